@@ -1,0 +1,211 @@
+/* ufg.h - C ABI of the GB300 (sm_103a) library for the unitary-Fermi-gas fermion matrix.
+ *
+ * The library applies the fermion matrix M[sigma] of Ten, Drut & Laehde, "Preconditioning the
+ * non-relativistic many-fermion problem" (arXiv:1008.3647), Sec. 1, Eq. (MatrixM):
+ *
+ *     (M x)_0     = x_0     + B_{N_tau-1} x_{N_tau-1}
+ *     (M x)_{t+1} = x_{t+1} - B_t x_t                       (t = 0 .. N_tau-2)
+ *     B_t = exp(-tau K) (1 + A sin sigma_t),   A = sqrt(2) sqrt(exp(tau g) - 1),
+ *     K diagonal in momentum space with E(k) = k^2/2 (hbar = m = 1), k_i = 2 pi n_i / N_x,
+ *
+ * matrix-free on the GPU, its transpose M^T (= M^dagger, M is real), the normal operator
+ * Q = M^T M (Eq. 1), and the paper's Krylov solvers and preconditioners: CG on Q x = b (Eq. 1),
+ * two-step BiCGStab M^T y = b, M x = y (Eq. 2), Chebyshev (Sec. 2), weak-coupling expansion with
+ * exact Fourier-accelerated M0^{-1} (Sec. 3) and strong coupling (Sec. 4), plus the HMC fermion
+ * force (Sec. 1).
+ *
+ * Conventions.
+ *   - Vectors are contiguous arrays in the order [t][z][y][x] (time slice slowest), t = 0-based
+ *     (the paper's 1-based slice j is t + 1).  S = N_x^3 N_tau sites.
+ *   - Vector pointers are DEVICE pointers unless a function says otherwise, 16-byte aligned, not
+ *     aliased with each other, owned by the caller.  FP64 entries are double, FP32 entries float.
+ *   - Handles (lattice, field, solver) and their workspace are owned by the library; all device
+ *     memory is allocated at creation, none inside applies or solve loops.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Applies are
+ *     asynchronous on it; solves and the force return after the result is complete.
+ *   - No function throws or aborts; every failure returns a status and leaves a thread-local
+ *     message for ufg_last_error().
+ */
+#ifndef UFG_H
+#define UFG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  UFG_OK = 0,
+  UFG_INVALID_ARG = 1,   /* bad size, pointer, alignment or parameter */
+  UFG_NOT_CONVERGED = 2, /* maxit reached before the residual target */
+  UFG_BREAKDOWN = 3,     /* BiCGStab breakdown persisted through all restarts */
+  UFG_NONFINITE = 4,     /* NaN or Inf in a residual or input */
+  UFG_TIMEOUT = 5,       /* a bounded device wait ran out */
+  UFG_CUDA_ERROR = 6,    /* a CUDA runtime call failed */
+  UFG_OOM = 7,           /* device allocation failed at handle creation */
+  UFG_INTERNAL = 8,      /* internal consistency check failed */
+  UFG_UNSUPPORTED = 9    /* valid input outside what this build implements (e.g. N_x) */
+} ufg_status;
+
+typedef enum { UFG_FP64 = 0, UFG_FP32 = 1, UFG_MIXED = 2 } ufg_precision;
+
+typedef enum { UFG_PC_NONE = 0, UFG_PC_CHEB = 1, UFG_PC_SCA = 2, UFG_PC_WCE = 3 } ufg_pc_kind;
+
+typedef struct ufg_lattice ufg_lattice;
+typedef struct ufg_field ufg_field;
+typedef struct ufg_solver ufg_solver;
+
+/* Preconditioner parameters (fields unused by a kind are ignored).
+ *   degree : Chebyshev degree d = 2n of P(z) ~ 1/z (Sec. 2, Eq. ChebInv); even, 2..64.
+ *   eps    : lower edge of [eps, 1] after normalisation; <= 0 selects (2 - 2 cos(pi/N_tau)) / scale.
+ *   scale  : spectrum normalisation s of M^T M (z = Q / s); <= 0 selects (2 + A)^2, a rigorous
+ *            bound on ||M||^2 since ||exp(-tau K)|| = 1 and |1 + A sin sigma| <= 1 + A.
+ *   alpha  : strong-coupling parameter alpha of D_t (Sec. 4); must be > 0.
+ *   order  : weak-coupling expansion order d (Sec. 3, Eq. WCE); 0..16.
+ *   euler  : nonzero selects Euler acceleration with p = 1/2 (Sec. 3.1, Eq. Euler). */
+typedef struct {
+  int degree;
+  double eps;
+  double scale;
+  double alpha;
+  int order;
+  int euler;
+} ufg_pc_params;
+
+/* Solve parameters.
+ *   tol       : target of the true relative residual ||b - M^T M x|| / ||b|| (Sec. 5 "reduction in
+ *               the norm of the residual"), recomputed in FP64 at exit.
+ *   maxit     : iteration cap of each Krylov solve.
+ *   precision : UFG_FP64, or UFG_MIXED (FP32 inner solves inside an FP64 defect-correction loop).
+ *   x0_given  : nonzero uses the content of x as the initial guess (else x0 = 0).
+ *   inner_tol : MIXED only, relative reduction asked of each FP32 inner solve (e.g. 1e-5).
+ *   check_every : Krylov iterations between host convergence checks (CUDA-graph replay length). */
+typedef struct {
+  double tol;
+  int maxit;
+  int precision;
+  int x0_given;
+  double inner_tol;
+  int check_every;
+} ufg_params;
+
+/* Solve statistics.  Apply counters count kernel applications of each operator (FP64 + FP32).
+ * mv_paper is the paper's MV-operation count for the iterations done (Sec. 5: CG + Chebyshev
+ * 2(d+1) per iteration, BiCGStab + WCE 2(d+1)(1+2 beta) with beta = 1, CG + SCA 3, none 2). */
+typedef struct {
+  int status;
+  int iterations;          /* Krylov iterations, summed over both steps and all inner solves */
+  int iterations_step[2];  /* two-step BiCGStab: step 1 (M^T y = b), step 2 (M x = y) */
+  int outer_iterations;    /* MIXED: defect-correction rounds */
+  int restarts;            /* BiCGStab restarts after near-breakdown */
+  long long n_M, n_Mdag, n_M1, n_M1T, n_M0inv, n_M0invT, n_sca;
+  double mv_paper;
+  double true_residual;    /* ||b - M^T M x|| / ||b|| in FP64 at exit */
+  double seconds;          /* wall time of the call */
+} ufg_stats;
+
+/* One independent problem of a batched solve.  sigma, b, x: device FP64 pointers of its own
+ * lattice size. */
+typedef struct {
+  int nx, ntau;
+  double tau, g;
+  const double* sigma;
+  const double* b;
+  double* x;
+} ufg_problem;
+
+/* Last error message of the calling thread ("" if none). */
+const char* ufg_last_error(void);
+
+/* Build version / supported lattice extents (comma-separated N_x list). */
+const char* ufg_version(void);
+const char* ufg_supported_nx(void);
+
+/* Lattice N_x^3 x N_tau with time step tau and coupling g (Sec. 1; the paper uses tau = 0.05,
+ * g in {2.5, 5, 7.5}).  dispersion 0: E(k) = k^2/2 (the paper's choice, hbar = m = 1);
+ * dispersion 1: E(k) = sum_i (1 - cos k_i), a Hubbard-type lattice dispersion (Sec. 6).
+ * N_x must be even and one of ufg_supported_nx(); N_tau >= 3 (<= 1024); tau > 0; g >= 0.
+ * Builds the FP64 line-operator tables on the host and the per-mode table exp(-tau E(k)) on the
+ * current device. */
+ufg_status ufg_lattice_create(int nx, int ntau, double tau, double g, int dispersion,
+                              ufg_lattice** out);
+void ufg_lattice_destroy(ufg_lattice* lat);
+/* Coupling A of the lattice (Sec. 1). */
+double ufg_lattice_coupling(const ufg_lattice* lat);
+
+/* Auxiliary field: copies sigma (device FP64, [N_tau][N_x]^3) and derives per site, in FP64 and
+ * FP32, w = 1 + A sin sigma (B_t), s = sin sigma (C_t of Eq. MatrixM_1), c = A cos sigma (force),
+ * calling CUDA's sin/cos.  Asynchronous on stream; sigma may be freed after the call returns
+ * only once the stream has passed it. */
+ufg_status ufg_field_create(const ufg_lattice* lat, const double* sigma, void* stream,
+                            ufg_field** out);
+/* Replaces sigma of an existing field (HMC step); same rules as ufg_field_create. */
+ufg_status ufg_field_update(ufg_field* f, const double* sigma, void* stream);
+void ufg_field_destroy(ufg_field* f);
+
+/* y = M x (Eq. MatrixM), y = M^T x, y = M^T M x (Eq. 1), y = M1 x and y = M1^T x (Eq. MatrixM_1),
+ * y = exp(-tau K) x on every slice, y = M0^{-1} x and y = M0^{-T} x (Sec. 3, exact: diagonal
+ * [1 - exp(-i omega - tau E(k))]^{-1} in frequency-momentum space, omega = (2n+1) pi / N_tau).
+ * precision UFG_FP64: x, y are double*; UFG_FP32: float*.  x and y must not overlap.  Q and
+ * M0^{-1}/M0^{-T} use library workspace of the field, so calls on one field must not overlap in
+ * time on different streams. */
+ufg_status ufg_apply_M(ufg_field* f, const void* x, void* y, int precision, void* stream);
+ufg_status ufg_apply_Mdag(ufg_field* f, const void* x, void* y, int precision, void* stream);
+ufg_status ufg_apply_Q(ufg_field* f, const void* x, void* y, int precision, void* stream);
+ufg_status ufg_apply_M1(ufg_field* f, const void* x, void* y, int precision, void* stream);
+ufg_status ufg_apply_M1T(ufg_field* f, const void* x, void* y, int precision, void* stream);
+ufg_status ufg_apply_kinetic(ufg_field* f, const void* x, void* y, int precision, void* stream);
+ufg_status ufg_apply_M0inv(ufg_field* f, const void* x, void* y, int precision, void* stream);
+ufg_status ufg_apply_M0invT(ufg_field* f, const void* x, void* y, int precision, void* stream);
+
+/* Solver workspace for one lattice (all vectors the solvers and preconditioners need, FP64 and
+ * FP32). */
+ufg_status ufg_solver_create(const ufg_lattice* lat, ufg_solver** out);
+void ufg_solver_destroy(ufg_solver* s);
+
+/* Selects the preconditioner of the following solves.  UFG_PC_CHEB and UFG_PC_SCA precondition
+ * Q = M^T M (CG); UFG_PC_WCE preconditions M and M^T separately (two-step BiCGStab). */
+ufg_status ufg_set_preconditioner(ufg_solver* s, int kind, const ufg_pc_params* p);
+
+/* z = P r with the current preconditioner: Chebyshev P(Q/s)/s ~ Q^{-1}; SCA (L^T D L)^{-1};
+ * WCE P_d ~ M^{-1} (transpose != 0: P_d^T ~ M^{-T}).  For tests and for callers composing their
+ * own solvers. */
+ufg_status ufg_apply_preconditioner(ufg_solver* s, ufg_field* f, const void* r, void* z,
+                                    int transpose, int precision, void* stream);
+
+/* Solves M^T M x = b by preconditioned CG (Eq. 1 with the left/SPD preconditioning of Eq. 3).
+ * b, x: FP64, device or host pointers (host buffers are staged through the workspace). */
+ufg_status ufg_solve_cg_normal(ufg_solver* s, ufg_field* f, const double* b, double* x,
+                               const ufg_params* p, ufg_stats* stats, void* stream);
+
+/* Solves M^T y = b, then M x = y (Eq. 2) by right-preconditioned BiCGStab (van der Vorst 1992),
+ * with P_d^T for the first and P_d for the second step when the WCE preconditioner is set.
+ * Step 1 runs to tol/2, step 2 to tol ||b|| / (2 (2 + A) ||y||); the composite residual
+ * ||b - M^T M x|| / ||b|| is checked at exit and one more correction round runs if needed. */
+ufg_status ufg_solve_bicgstab_two_step(ufg_solver* s, ufg_field* f, const double* b, double* x,
+                                       const ufg_params* p, ufg_stats* stats, void* stream);
+
+/* HMC force of the pseudofermion action S = phi^T (M^T M)^{-1} phi (Sec. 1): solves
+ * X = Q^{-1} phi with the two-step BiCGStab (WCE preconditioner if set) and returns
+ * dS/dsigma_t(r) = 2 A cos sigma_t(r) X_t(r) [exp(-tau K) Y~_{t+1}](r), Y = M X, Y~_{N_tau} = -Y_0
+ * (the paper's F with the opposite sign).  phi: device FP64.  dS (nullable: solve and action
+ * only), X_out (nullable): device FP64; S_out (nullable, host) receives S. */
+ufg_status ufg_hmc_force(ufg_solver* s, ufg_field* f, const double* phi, double* dS,
+                         double* X_out, double* S_out, const ufg_params* p, ufg_stats* stats,
+                         void* stream);
+/* dS = scale * dS/dsigma from a given solution X = Q^{-1} phi (device FP64): Y = M X is recomputed
+ * into solver workspace, then one fused slice kernel forms the force.  Asynchronous on stream. */
+ufg_status ufg_force_from_solution(ufg_solver* s, ufg_field* f, const double* X, double* dS,
+                                   double scale, void* stream);
+
+/* n independent problems of mixed lattice sizes, each solved by two-step BiCGStab with the
+ * preconditioner settings pc_kind/pc, all problems advanced together by batched kernels (one
+ * launch per phase for the whole batch) and the iteration body captured in a CUDA graph.
+ * stats: n entries (nullable). */
+ufg_status ufg_solve_batch(int n, const ufg_problem* probs, int pc_kind, const ufg_pc_params* pc,
+                           const ufg_params* p, ufg_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UFG_H */

@@ -317,11 +317,10 @@ def bit_reversed(n: int):
 
 
 def cheb_scale_eps(lat, sigma, eps=None):
-    """Spectrum normalisation of M^dagger M to [eps, 1] (Sec. 2): scale s = (1 + max|w|)^2 bounds
-    ||M||^2 because ||exp(-tau K)|| = 1; default eps = free-gas lowest eigenvalue
-    (2 - 2 cos(pi/N_tau)) / s."""
-    w, _, _ = potentials(lat, sigma)
-    s = (1.0 + np.max(np.abs(w))) ** 2
+    """Spectrum normalisation of M^dagger M to [eps, 1] (Sec. 2): scale s = (2 + A)^2 bounds
+    ||M||^2 because ||exp(-tau K)|| = 1 and |1 + A sin sigma| <= 1 + A; default eps = free-gas
+    lowest eigenvalue (2 - 2 cos(pi/N_tau)) / s."""
+    s = (2.0 + lat.A) ** 2
     if eps is None:
         eps = (2.0 - 2.0 * math.cos(math.pi / lat.ntau)) / s
     return s, eps
@@ -546,11 +545,10 @@ def solve_cg_normal(lat, sigma, b, tol=1e-10, maxit=20000, pc=None):
 def solve_bicgstab_two_step(lat, sigma, b, tol=1e-10, maxit=20000, pc=None):
     """M^dagger y = b then M x = y (Eq. 2) with right-preconditioned BiCGStab.
 
-    Tolerance split: step 1 to tol/2; step 2 to tol ||b|| / (2 (1 + max|w|) ||y||), since
-    ||b - M^dagger M x|| <= ||r_1|| + ||M^dagger|| ||r_2|| and ||M^dagger|| <= 1 + max|w|.
+    Tolerance split: step 1 to tol/2; step 2 to tol ||b|| / (2 (2 + A) ||y||), since
+    ||b - M^dagger M x|| <= ||r_1|| + ||M^dagger|| ||r_2|| and ||M^dagger|| <= 2 + A.
     """
     counter = Counter()
-    w, _, _ = potentials(lat, sigma)
 
     def mdag(u):
         counter.add("Mdag")
@@ -560,7 +558,7 @@ def solve_bicgstab_two_step(lat, sigma, b, tol=1e-10, maxit=20000, pc=None):
         counter.add("M")
         return apply_M(lat, sigma, u)
     y, it1, ok1 = bicgstab(mdag, b, 0.5 * tol, maxit, _make_pc(lat, sigma, pc, counter, True))
-    tol2 = tol * math.sqrt(_dot(b, b)) / (2.0 * (1.0 + np.max(np.abs(w))) * math.sqrt(_dot(y, y)))
+    tol2 = tol * math.sqrt(_dot(b, b)) / (2.0 * (2.0 + lat.A) * math.sqrt(_dot(y, y)))
     x, it2, ok2 = bicgstab(m, y, tol2, maxit, _make_pc(lat, sigma, pc, counter, False))
     return x, {"iterations": it1 + it2, "iterations_step": (it1, it2),
                "converged": ok1 and ok2, "counts": dict(counter)}

@@ -1,0 +1,26 @@
+// Runtime dispatch from the lattice extent N_x to the compiled slice-kernel instantiation.
+#include "slice_call.h"
+
+namespace ufg {
+
+bool slice_supported_n(int N) {
+  switch (N) {
+    case 4: case 6: case 8: case 10: case 12: case 16: case 32: return true;
+  }
+  return false;
+}
+
+cudaError_t slice_dispatch(int N, const SliceCall& c, cudaStream_t st) {
+  switch (N) {
+    case 4: return slice_launch<4>(c, st);
+    case 6: return slice_launch<6>(c, st);
+    case 8: return slice_launch<8>(c, st);
+    case 10: return slice_launch<10>(c, st);
+    case 12: return slice_launch<12>(c, st);
+    case 16: return slice_launch<16>(c, st);
+    case 32: return slice_launch<32>(c, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ufg

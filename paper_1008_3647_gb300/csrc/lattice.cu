@@ -1,0 +1,489 @@
+// Lattice and field handles, the host-side construction of the line-operator tables, and the
+// C-ABI operator applications (M, M^T, Q, M1, M1^T, kinetic, M0^{-1}, M0^{-T}).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "line_ops.cuh"
+#include "ufg_internal.h"
+
+namespace ufg {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+
+ufg_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s failed: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+  return UFG_CUDA_ERROR;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Line-operator tables (FP64 on the host).
+//
+// 1-D spectrum: frequency n (numpy-style order, k = 2 pi n'/N with n' = n for n < N/2 and n - N
+// otherwise, i.e. n' in -N/2..N/2-1, Sec. 1) has eigenvalue lam(n) = exp(-tau E1(k)),
+// E1 = k^2/2 (dispersion 0) or 1 - cos k (dispersion 1); exp(-tau E(k)) = prod_i lam(n_i).
+//
+// Real orthonormal basis F (columns = spectral slots): slot 0 constant, slots 1..H-1 cosines,
+// slot H the alternating vector, slots H+1..N-1 sines.  T = F diag(lam_slot) F^T is exp(-tau K)
+// along one axis, a real symmetric circulant.
+// ---------------------------------------------------------------------------------------------
+static double e1(double k, int dispersion) {
+  return dispersion == 0 ? 0.5 * k * k : 1.0 - std::cos(k);
+}
+
+static void basis(int N, std::vector<double>& F /*N x N, F[x*N+slot]*/, std::vector<int>& freq) {
+  const int H = N / 2;
+  F.assign((size_t)N * N, 0.0);
+  freq.assign(N, 0);
+  const double pi = 3.14159265358979323846;
+  for (int x = 0; x < N; ++x) {
+    F[x * N + 0] = 1.0 / std::sqrt((double)N);
+    F[x * N + H] = ((x & 1) ? -1.0 : 1.0) / std::sqrt((double)N);
+    for (int i = 1; i < H; ++i) {
+      F[x * N + i] = std::sqrt(2.0 / N) * std::cos(2.0 * pi * i * x / N);
+      F[x * N + H + i] = std::sqrt(2.0 / N) * std::sin(2.0 * pi * i * x / N);
+    }
+  }
+  freq[0] = 0;
+  freq[H] = H;
+  for (int i = 1; i < H; ++i) {
+    freq[i] = i;
+    freq[H + i] = i;
+  }
+}
+
+// Reduces a full N x N operator (y = A v) to its even/odd blocks for the given input/output
+// representations; returns false if the operator mixes even and odd parts.
+static bool reduce(int N, const std::vector<double>& A, bool in_spec, bool out_spec,
+                   std::vector<double>& ce, std::vector<double>& co) {
+  const int H = N / 2;
+  ce.assign((H + 1) * (H + 1), 0.0);
+  co.assign((H - 1) * (H - 1), 0.0);
+  double cross = 0.0, scale = 0.0;
+  auto to_out = [&](const std::vector<double>& y, std::vector<double>& E, std::vector<double>& O) {
+    E.assign(H + 1, 0.0);
+    O.assign(H + 1, 0.0);
+    if (out_spec) {
+      for (int i = 0; i <= H; ++i) E[i] = y[i];
+      for (int i = 1; i < H; ++i) O[i] = y[H + i];
+    } else {
+      E[0] = y[0];
+      E[H] = y[H];
+      for (int i = 1; i < H; ++i) {
+        E[i] = 0.5 * (y[i] + y[N - i]);
+        O[i] = 0.5 * (y[i] - y[N - i]);
+      }
+    }
+  };
+  for (int odd = 0; odd < 2; ++odd) {
+    const int jlo = odd ? 1 : 0, jhi = odd ? H - 1 : H;
+    for (int j = jlo; j <= jhi; ++j) {
+      std::vector<double> v(N, 0.0), y(N, 0.0), E, O;
+      if (in_spec) {
+        v[odd ? H + j : j] = 1.0;
+      } else if (!odd && (j == 0 || j == H)) {
+        v[j] = 1.0;
+      } else {
+        v[j] = 0.5;
+        v[N - j] = odd ? -0.5 : 0.5;
+      }
+      for (int i = 0; i < N; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < N; ++k) acc += A[(size_t)i * N + k] * v[k];
+        y[i] = acc;
+      }
+      to_out(y, E, O);
+      for (int i = 0; i <= H; ++i) scale = std::fmax(scale, std::fabs(E[i]) + std::fabs(O[i]));
+      if (!odd) {
+        for (int i = 0; i <= H; ++i) ce[i * (H + 1) + j] = E[i];
+        for (int i = 1; i < H; ++i) cross = std::fmax(cross, std::fabs(O[i]));
+      } else {
+        for (int i = 1; i < H; ++i) co[(i - 1) * (H - 1) + (j - 1)] = O[i];
+        for (int i = 0; i <= H; ++i) cross = std::fmax(cross, std::fabs(E[i]));
+      }
+    }
+  }
+  return cross <= 1e-13 * std::fmax(scale, 1.0);
+}
+
+template <typename R>
+static void pack(const std::vector<double>& ce, const std::vector<double>& co,
+                 std::vector<unsigned char>& out) {
+  std::vector<R> v;
+  v.reserve(ce.size() + co.size());
+  for (double d : ce) v.push_back((R)d);
+  for (double d : co) v.push_back((R)d);
+  out.resize(v.size() * sizeof(R));
+  std::memcpy(out.data(), v.data(), out.size());
+}
+
+static ufg_status build_tables(ufg_lattice* L) {
+  const int N = L->nx, H = N / 2;
+  const double pi = 3.14159265358979323846;
+  std::vector<double> F;
+  std::vector<int> freq;
+  basis(N, F, freq);
+  L->lam.assign(N, 0.0);
+  for (int s = 0; s < N; ++s) L->lam[s] = std::exp(-L->tau * e1(2.0 * pi * freq[s] / N, L->dispersion));
+  (void)H;
+  // T = F diag(lam) F^T; Ft = F^T; Finv = F.
+  std::vector<double> T((size_t)N * N, 0.0), Ft((size_t)N * N), Fi((size_t)N * N);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      double acc = 0.0;
+      for (int s = 0; s < N; ++s) acc += F[i * N + s] * L->lam[s] * F[j * N + s];
+      T[(size_t)i * N + j] = acc;
+      Ft[(size_t)i * N + j] = F[(size_t)j * N + i];
+      Fi[(size_t)i * N + j] = F[(size_t)i * N + j];
+    }
+  std::vector<double> ce, co;
+  struct Spec { const std::vector<double>* A; bool in_spec, out_spec; int fam; } specs[3] = {
+      {&T, false, false, FAM_KIN}, {&Ft, false, true, FAM_FWD}, {&Fi, true, false, FAM_INV}};
+  for (auto& sp : specs) {
+    if (!reduce(N, *sp.A, sp.in_spec, sp.out_spec, ce, co)) {
+      set_error("line operator of family %d does not split into even and odd parts", sp.fam);
+      return UFG_INTERNAL;
+    }
+    pack<double>(ce, co, L->coef[sp.fam][0]);
+    pack<float>(ce, co, L->coef[sp.fam][1]);
+  }
+  // per-mode table in spectral layout [sz][sy][sx]
+  std::vector<double> bk((size_t)L->V);
+  std::vector<float> bkf((size_t)L->V);
+  for (int z = 0; z < N; ++z)
+    for (int y = 0; y < N; ++y)
+      for (int x = 0; x < N; ++x) {
+        const size_t i = ((size_t)z * N + y) * N + x;
+        bk[i] = L->lam[z] * L->lam[y] * L->lam[x];
+        bkf[i] = (float)bk[i];
+      }
+  UFG_TRY(dev_alloc(&L->bk64, (size_t)L->V));
+  UFG_TRY(dev_alloc(&L->bk32, (size_t)L->V));
+  UFG_CUDA(cudaMemcpy(L->bk64, bk.data(), bk.size() * sizeof(double), cudaMemcpyHostToDevice));
+  UFG_CUDA(cudaMemcpy(L->bk32, bkf.data(), bkf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return UFG_OK;
+}
+
+// Default launch shape: ~32-70 KB of shared memory per CTA so that several CTAs share an SM.
+static void default_tuning(ufg_lattice* L) {
+  const int N = L->nx;
+  for (int prec = 0; prec < 2; ++prec) {
+    const size_t es = prec == 0 ? 8 : 4;
+    if (N >= 32) {
+      L->C[prec] = prec == 0 ? 4 : 2;
+      L->spc[prec] = 1;
+    } else {
+      L->C[prec] = 1;
+      const size_t slice = (size_t)N * N * (N + 1) * es;
+      int spc = 1;
+      while (spc < 8 && slice * (spc * 2) <= 48 * 1024 && L->ntau / (spc * 2) >= 152) spc *= 2;
+      L->spc[prec] = spc;
+    }
+  }
+}
+
+SliceCall base_call(const ufg_lattice* lat, int fam, int prec) {
+  SliceCall c;
+  c.fam = fam;
+  c.prec = prec;
+  c.coef = lat->coef[fam][prec].data();
+  c.ntau = lat->ntau;
+  c.spc = lat->spc[prec];
+  c.C = lat->C[prec];
+  return c;
+}
+
+const void* fld(const ufg_field* f, char which, int prec) {
+  switch (which) {
+    case 'w': return prec ? (const void*)f->w32 : (const void*)f->w64;
+    case 's': return prec ? (const void*)f->s32 : (const void*)f->s64;
+    case 'c': return prec ? (const void*)f->c32 : (const void*)f->c64;
+  }
+  return nullptr;
+}
+
+static ufg_status run(const ufg_lattice* lat, const SliceCall& c, cudaStream_t st) {
+  cudaError_t e = slice_dispatch(lat->nx, c, st);
+  if (e != cudaSuccess) return cuda_fail(e, "slice kernel launch");
+  return UFG_OK;
+}
+
+ufg_status op_M(const ufg_field* f, int prec, const void* x, void* y, cudaStream_t st) {
+  SliceCall c = base_call(f->lat, FAM_KIN, prec);
+  c.in = x;
+  c.pre = fld(f, 'w', prec);
+  c.id = x;
+  c.shift = -1;
+  c.out = y;
+  return run(f->lat, c, st);
+}
+
+ufg_status op_Mdag(const ufg_field* f, int prec, const void* x, void* y, cudaStream_t st) {
+  SliceCall c = base_call(f->lat, FAM_KIN, prec);
+  c.in = x;
+  c.post = fld(f, 'w', prec);
+  c.id = x;
+  c.shift = +1;
+  c.out = y;
+  return run(f->lat, c, st);
+}
+
+ufg_status op_M0inv(const ufg_field* f, int prec, const void* x, void* y, void* tmp, int transpose,
+                    cudaStream_t st) {
+  const ufg_lattice* lat = f->lat;
+  SliceCall fw = base_call(lat, FAM_FWD, prec);
+  fw.in = x;
+  fw.out = tmp;
+  UFG_TRY(run(lat, fw, st));
+  const void* bk = prec ? (const void*)lat->bk32 : (const void*)lat->bk64;
+  cudaError_t e = launch_recurrence(prec, tmp, tmp, bk, lat->V, lat->ntau, transpose, 1.0, nullptr,
+                                    0.0, 0, nullptr, st);
+  if (e != cudaSuccess) return cuda_fail(e, "recurrence kernel launch");
+  SliceCall iv = base_call(lat, FAM_INV, prec);
+  iv.in = tmp;
+  iv.out = y;
+  return run(lat, iv, st);
+}
+
+ufg_status ensure_sca(ufg_field* f, double alpha, cudaStream_t st) {
+  if (f->sca_alpha == alpha && f->L64 != nullptr) return UFG_OK;
+  const ufg_lattice* lat = f->lat;
+  if (f->L64 == nullptr) {
+    UFG_TRY(dev_alloc(&f->L64, (size_t)lat->S));
+    UFG_TRY(dev_alloc(&f->Di64, (size_t)lat->S));
+    UFG_TRY(dev_alloc(&f->L32, (size_t)lat->S));
+    UFG_TRY(dev_alloc(&f->Di32, (size_t)lat->S));
+  }
+  cudaError_t e = launch_sca_setup(f->w64, lat->V, lat->ntau, alpha, f->L64, f->Di64, f->L32,
+                                   f->Di32, st);
+  if (e != cudaSuccess) return cuda_fail(e, "SCA setup launch");
+  f->sca_alpha = alpha;
+  return UFG_OK;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static ufg_status check_vec(const ufg_field* f, const void* x, const void* y, int prec) {
+  if (f == nullptr || f->lat == nullptr) {
+    set_error("null field");
+    return UFG_INVALID_ARG;
+  }
+  if (x == nullptr || y == nullptr) {
+    set_error("null vector pointer");
+    return UFG_INVALID_ARG;
+  }
+  if (prec != UFG_FP64 && prec != UFG_FP32) {
+    set_error("apply precision must be UFG_FP64 or UFG_FP32");
+    return UFG_INVALID_ARG;
+  }
+  if (!aligned16(x) || !aligned16(y)) {
+    set_error("vector pointers must be 16-byte aligned");
+    return UFG_INVALID_ARG;
+  }
+  const size_t bytes = (size_t)f->lat->S * (prec ? 4 : 8);
+  const char* a = static_cast<const char*>(x);
+  const char* b = static_cast<const char*>(y);
+  if (a < b + bytes && b < a + bytes) {
+    set_error("x and y overlap");
+    return UFG_INVALID_ARG;
+  }
+  return UFG_OK;
+}
+
+}  // namespace ufg
+
+using namespace ufg;
+
+extern "C" {
+
+const char* ufg_last_error(void) { return g_err.c_str(); }
+const char* ufg_version(void) { return "ufg-gb300 0.1 (sm_103a)"; }
+const char* ufg_supported_nx(void) { return "4,6,8,10,12,16,32"; }
+
+ufg_status ufg_lattice_create(int nx, int ntau, double tau, double g, int dispersion,
+                              ufg_lattice** out) {
+  clear_error();
+  if (out == nullptr) {
+    set_error("out is null");
+    return UFG_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (nx < 2 || nx % 2 != 0 || ntau < 3 || ntau > 1024 || !(tau > 0) || !(g >= 0) ||
+      (dispersion != 0 && dispersion != 1) || !std::isfinite(tau) || !std::isfinite(g)) {
+    set_error("invalid lattice: need even N_x >= 2, 3 <= N_tau <= 1024, tau > 0, g >= 0, "
+              "dispersion 0 or 1 (got N_x=%d N_tau=%d tau=%g g=%g dispersion=%d)",
+              nx, ntau, tau, g, dispersion);
+    return UFG_INVALID_ARG;
+  }
+  if (!slice_supported_n(nx)) {
+    set_error("N_x=%d is not built; supported: %s", nx, ufg_supported_nx());
+    return UFG_UNSUPPORTED;
+  }
+  ufg_lattice* L = new ufg_lattice();
+  L->nx = nx;
+  L->ntau = ntau;
+  L->tau = tau;
+  L->g = g;
+  L->dispersion = dispersion;
+  L->A = std::sqrt(2.0) * std::sqrt(std::expm1(tau * g));
+  L->V = (long long)nx * nx * nx;
+  L->S = L->V * ntau;
+  cudaGetDevice(&L->device);
+  ufg_status s = build_tables(L);
+  if (s != UFG_OK) {
+    ufg_lattice_destroy(L);
+    return s;
+  }
+  default_tuning(L);
+  *out = L;
+  return UFG_OK;
+}
+
+void ufg_lattice_destroy(ufg_lattice* L) {
+  if (!L) return;
+  dev_free(L->bk64);
+  dev_free(L->bk32);
+  delete L;
+}
+
+double ufg_lattice_coupling(const ufg_lattice* L) { return L ? L->A : 0.0; }
+
+ufg_status ufg_field_update(ufg_field* f, const double* sigma, void* stream) {
+  clear_error();
+  if (f == nullptr || sigma == nullptr || !aligned16(sigma)) {
+    set_error("field_update: null field or null/misaligned sigma");
+    return UFG_INVALID_ARG;
+  }
+  const ufg_lattice* L = f->lat;
+  cudaStream_t st = as_stream(stream);
+  UFG_CUDA(cudaMemcpyAsync(f->sigma, sigma, (size_t)L->S * sizeof(double), cudaMemcpyDefault, st));
+  UFG_CUDA(launch_potentials(f->sigma, L->A, L->S, f->w64, f->s64, f->c64, f->w32, f->s32, f->c32,
+                             st));
+  f->sca_alpha = -1.0;
+  return UFG_OK;
+}
+
+ufg_status ufg_field_create(const ufg_lattice* L, const double* sigma, void* stream,
+                            ufg_field** out) {
+  clear_error();
+  if (L == nullptr || out == nullptr) {
+    set_error("null lattice or out");
+    return UFG_INVALID_ARG;
+  }
+  *out = nullptr;
+  ufg_field* f = new ufg_field();
+  f->lat = L;
+  const size_t S = (size_t)L->S;
+  ufg_status s = UFG_OK;
+  if ((s = dev_alloc(&f->sigma, S)) || (s = dev_alloc(&f->w64, S)) || (s = dev_alloc(&f->s64, S)) ||
+      (s = dev_alloc(&f->c64, S)) || (s = dev_alloc(&f->w32, S)) || (s = dev_alloc(&f->s32, S)) ||
+      (s = dev_alloc(&f->c32, S)) || (s = dev_alloc(&f->tmp64, S)) || (s = dev_alloc(&f->tmp32, S))) {
+    ufg_field_destroy(f);
+    return s;
+  }
+  s = ufg_field_update(f, sigma, stream);
+  if (s != UFG_OK) {
+    ufg_field_destroy(f);
+    return s;
+  }
+  *out = f;
+  return UFG_OK;
+}
+
+void ufg_field_destroy(ufg_field* f) {
+  if (!f) return;
+  dev_free(f->sigma);
+  dev_free(f->w64);
+  dev_free(f->s64);
+  dev_free(f->c64);
+  dev_free(f->w32);
+  dev_free(f->s32);
+  dev_free(f->c32);
+  dev_free(f->tmp64);
+  dev_free(f->tmp32);
+  dev_free(f->L64);
+  dev_free(f->Di64);
+  dev_free(f->L32);
+  dev_free(f->Di32);
+  delete f;
+}
+
+ufg_status ufg_apply_M(ufg_field* f, const void* x, void* y, int prec, void* stream) {
+  clear_error();
+  UFG_TRY(check_vec(f, x, y, prec));
+  return op_M(f, prec, x, y, as_stream(stream));
+}
+
+ufg_status ufg_apply_Mdag(ufg_field* f, const void* x, void* y, int prec, void* stream) {
+  clear_error();
+  UFG_TRY(check_vec(f, x, y, prec));
+  return op_Mdag(f, prec, x, y, as_stream(stream));
+}
+
+ufg_status ufg_apply_Q(ufg_field* f, const void* x, void* y, int prec, void* stream) {
+  clear_error();
+  UFG_TRY(check_vec(f, x, y, prec));
+  void* tmp = prec ? (void*)f->tmp32 : (void*)f->tmp64;
+  UFG_TRY(op_M(f, prec, x, tmp, as_stream(stream)));
+  return op_Mdag(f, prec, tmp, y, as_stream(stream));
+}
+
+ufg_status ufg_apply_M1(ufg_field* f, const void* x, void* y, int prec, void* stream) {
+  clear_error();
+  UFG_TRY(check_vec(f, x, y, prec));
+  SliceCall c = base_call(f->lat, FAM_KIN, prec);
+  c.in = x;
+  c.pre = fld(f, 's', prec);
+  c.shift = -1;
+  c.out = y;
+  return run(f->lat, c, as_stream(stream));
+}
+
+ufg_status ufg_apply_M1T(ufg_field* f, const void* x, void* y, int prec, void* stream) {
+  clear_error();
+  UFG_TRY(check_vec(f, x, y, prec));
+  SliceCall c = base_call(f->lat, FAM_KIN, prec);
+  c.in = x;
+  c.post = fld(f, 's', prec);
+  c.shift = +1;
+  c.out = y;
+  return run(f->lat, c, as_stream(stream));
+}
+
+ufg_status ufg_apply_kinetic(ufg_field* f, const void* x, void* y, int prec, void* stream) {
+  clear_error();
+  UFG_TRY(check_vec(f, x, y, prec));
+  SliceCall c = base_call(f->lat, FAM_KIN, prec);
+  c.in = x;
+  c.out = y;
+  return run(f->lat, c, as_stream(stream));
+}
+
+ufg_status ufg_apply_M0inv(ufg_field* f, const void* x, void* y, int prec, void* stream) {
+  clear_error();
+  UFG_TRY(check_vec(f, x, y, prec));
+  void* tmp = prec ? (void*)f->tmp32 : (void*)f->tmp64;
+  return op_M0inv(f, prec, x, y, tmp, 0, as_stream(stream));
+}
+
+ufg_status ufg_apply_M0invT(ufg_field* f, const void* x, void* y, int prec, void* stream) {
+  clear_error();
+  UFG_TRY(check_vec(f, x, y, prec));
+  void* tmp = prec ? (void*)f->tmp32 : (void*)f->tmp64;
+  return op_M0inv(f, prec, x, y, tmp, 1, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,226 @@
+// Time-direction kernels: the per-site potentials of a field, the exact M0^{-1} recurrence per
+// momentum mode (Sec. 3) and the strong-coupling factorisation and apply (Sec. 4).
+#include <cuda_runtime.h>
+
+#include "ufg_internal.h"
+
+namespace ufg {
+
+// ---- potentials: w = 1 + A sin sigma, s = sin sigma, c = A cos sigma (B_t, C_t, dB/dsigma) ----
+__global__ void potentials_kernel(const double* __restrict__ sigma, double A, long long S,
+                                  double* w64, double* s64, double* c64, float* w32, float* s32,
+                                  float* c32) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S;
+       i += (long long)gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincos(sigma[i], &sn, &cs);
+    const double w = 1.0 + A * sn;
+    w64[i] = w;
+    s64[i] = sn;
+    c64[i] = A * cs;
+    w32[i] = (float)w;
+    s32[i] = (float)sn;
+    c32[i] = (float)(A * cs);
+  }
+}
+
+cudaError_t launch_potentials(const double* sigma, double A, long long S, double* w64, double* s64,
+                              double* c64, float* w32, float* s32, float* c32, cudaStream_t st) {
+  const int nt = 256;
+  long long blocks = (S + nt - 1) / nt;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  potentials_kernel<<<(unsigned)blocks, nt, 0, st>>>(sigma, A, S, w64, s64, c64, w32, s32, c32);
+  return cudaGetLastError();
+}
+
+// ---- exact M0^{-1} per momentum mode ------------------------------------------------------
+// In the spatial eigenbasis of exp(-tau K) (eigenvalue b per mode) M0 acts on one mode as
+//   (M0 x)_t = x_t - b x_{t-1},  x_{-1} = -x_{N_tau-1}  (antiperiodic, Eq. MatrixM at sigma = 0),
+// so M0^{-1} is the first-order recurrence x_t = y_t + b x_{t-1} closed by
+//   x_{N_tau-1} = sum_t b^{N_tau-1-t} y_t / (1 + b^{N_tau}),
+// which is the frequency-space diagonal [1 - exp(-i omega - tau E(k))]^{-1} of Sec. 3 written in
+// imaginary time.  M0^{-T} runs the same recurrence backwards in t.
+//
+// Layout: block = 32 modes (lanes, coalesced) x nch time chunks (warps).  Each thread keeps its
+// chunk (<= LMAX slices) in registers: pass 1 forms the chunk's zero-start end value, one lane
+// per mode folds the chunks to the closed boundary value and each chunk's incoming state, pass 2
+// replays the chunk from registers and writes.  One HBM read and one write per element.
+template <typename R, int LMAX>
+__global__ void recurrence_kernel(const R* in, R* out, const R* __restrict__ bk, long long V,
+                                  int ntau, int len, int transpose, double out_scale, R* acc,
+                                  double acc_coef, int acc_mode, const int* done) {
+  __shared__ R Es[32][33];
+  __shared__ R Ps[32][33];
+  __shared__ R Is[32][33];
+  if (done != nullptr && *done) return;
+  const int lane = threadIdx.x;
+  const int ch = threadIdx.y;
+  const int nch = blockDim.y;
+  const long long mode = (long long)blockIdx.x * 32 + lane;
+  const bool active = mode < V;
+  const R b = active ? bk[mode] : R(0);
+  const int l0 = ch * len;
+  R y[LMAX];
+  R e = R(0), p = R(1);
+#pragma unroll
+  for (int i = 0; i < LMAX; ++i) {
+    const int l = l0 + i;
+    if (i < len && l < ntau && active) {
+      const int t = transpose ? ntau - 1 - l : l;
+      y[i] = in[(size_t)t * V + mode];
+      e = y[i] + b * e;
+      p = p * b;
+    } else {
+      y[i] = R(0);
+    }
+  }
+  Es[ch][lane] = e;
+  Ps[ch][lane] = p;
+  __syncthreads();
+  if (ch == 0) {
+    R Z = R(0), bN = R(1);
+    for (int c = 0; c < nch; ++c) {
+      Z = Es[c][lane] + Ps[c][lane] * Z;
+      bN = bN * Ps[c][lane];
+    }
+    const R xlast = Z / (R(1) + bN);
+    R state = -xlast;  // x_{-1} = -x_{N_tau-1}
+    for (int c = 0; c < nch; ++c) {
+      Is[c][lane] = state;
+      state = Es[c][lane] + Ps[c][lane] * state;
+    }
+  }
+  __syncthreads();
+  R x = Is[ch][lane];
+#pragma unroll
+  for (int i = 0; i < LMAX; ++i) {
+    const int l = l0 + i;
+    if (i < len && l < ntau && active) {
+      const int t = transpose ? ntau - 1 - l : l;
+      x = y[i] + b * x;
+      const size_t g = (size_t)t * V + mode;
+      if (acc_mode == 1) acc[g] = R(acc_coef) * x;
+      if (acc_mode == 2) acc[g] += R(acc_coef) * x;
+      if (out != nullptr) out[g] = R(out_scale) * x;
+    }
+  }
+}
+
+cudaError_t launch_recurrence(int prec, const void* in, void* out, const void* bk, long long V,
+                              int ntau, int transpose, double out_scale, void* acc,
+                              double acc_coef, int acc_mode, const int* done, cudaStream_t st) {
+  const int lmax = ntau <= 512 ? 16 : 32;
+  const int nch = (ntau + lmax - 1) / lmax;
+  if (nch > 32) return cudaErrorInvalidValue;
+  const int len = (ntau + nch - 1) / nch;
+  dim3 block(32, nch);
+  dim3 grid((unsigned)((V + 31) / 32));
+  if (prec == 0) {
+    if (lmax == 16)
+      recurrence_kernel<double, 16><<<grid, block, 0, st>>>(
+          (const double*)in, (double*)out, (const double*)bk, V, ntau, len, transpose, out_scale,
+          (double*)acc, acc_coef, acc_mode, done);
+    else
+      recurrence_kernel<double, 32><<<grid, block, 0, st>>>(
+          (const double*)in, (double*)out, (const double*)bk, V, ntau, len, transpose, out_scale,
+          (double*)acc, acc_coef, acc_mode, done);
+  } else {
+    if (lmax == 16)
+      recurrence_kernel<float, 16><<<grid, block, 0, st>>>(
+          (const float*)in, (float*)out, (const float*)bk, V, ntau, len, transpose, out_scale,
+          (float*)acc, acc_coef, acc_mode, done);
+    else
+      recurrence_kernel<float, 32><<<grid, block, 0, st>>>(
+          (const float*)in, (float*)out, (const float*)bk, V, ntau, len, transpose, out_scale,
+          (float*)acc, acc_coef, acc_mode, done);
+  }
+  return cudaGetLastError();
+}
+
+// ---- strong-coupling approximation (Sec. 4) -----------------------------------------------
+// Per site r, with w_t = 1 + A sin sigma_t (B_{0,t}) and 0-based t (paper's j = t + 1):
+//   D_0 = alpha + w_0^2,  D_t = alpha + w_t^2 - w_{t-1}^2 / D_{t-1}  (1 <= t <= N-2),
+//   D_{N-1} = alpha + w_{N-1}^2 - w_{N-2}^2 / D_{N-2} - w_{N-1}^2 / D_0,
+//   L_t = w_t / D_t (t < N-1),  L_{N-1} = w_{N-1} / D_0.
+// Stored: L and 1/D, FP64 and FP32.
+__global__ void sca_setup_kernel(const double* __restrict__ w, long long V, int ntau, double alpha,
+                                 double* L64, double* Di64, float* L32, float* Di32) {
+  const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= V) return;
+  const double w0 = w[r];
+  const double D0 = alpha + w0 * w0;
+  double Dprev = D0, wprev = w0;
+  auto put = [&](int t, double L, double D) {
+    const size_t g = (size_t)t * V + r;
+    L64[g] = L;
+    Di64[g] = 1.0 / D;
+    L32[g] = (float)L;
+    Di32[g] = (float)(1.0 / D);
+  };
+  put(0, w0 / D0, D0);
+  for (int t = 1; t < ntau - 1; ++t) {
+    const double wt = w[(size_t)t * V + r];
+    const double Dt = alpha + wt * wt - wprev * wprev / Dprev;
+    put(t, wt / Dt, Dt);
+    Dprev = Dt;
+    wprev = wt;
+  }
+  const double wl = w[(size_t)(ntau - 1) * V + r];
+  const double Dl = alpha + wl * wl - wprev * wprev / Dprev - wl * wl / D0;
+  put(ntau - 1, wl / D0, Dl);
+}
+
+cudaError_t launch_sca_setup(const double* w64, long long V, int ntau, double alpha, double* L64,
+                             double* Di64, float* L32, float* Di32, cudaStream_t st) {
+  sca_setup_kernel<<<(unsigned)((V + 127) / 128), 128, 0, st>>>(w64, V, ntau, alpha, L64, Di64, L32,
+                                                                 Di32);
+  return cudaGetLastError();
+}
+
+// z = (L^T D L)^{-1} y: forward solve with the lower factor (the recursion printed in Sec. 4),
+// pointwise 1/D, backward solve with the upper factor.  One thread per site, coalesced in r.
+template <typename R>
+__global__ void sca_apply_kernel(const R* __restrict__ L, const R* __restrict__ Di, const R* y,
+                                 R* z, long long V, int ntau, const int* done) {
+  if (done != nullptr && *done) return;
+  const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= V) return;
+  const int N = ntau;
+  const R x0 = y[r];
+  R xp = x0;
+  // forward: x_t = y_t + L_{t-1} x_{t-1}; x_{N-1} -= L_{N-1} x_0; store u = x / D into z
+  z[r] = x0 * Di[r];
+  for (int t = 1; t < N; ++t) {
+    const size_t g = (size_t)t * V + r;
+    R xt = y[g] + L[g - V] * xp;
+    if (t == N - 1) xt -= L[g] * x0;
+    z[g] = xt * Di[g];
+    xp = xt;
+  }
+  // backward: z_{N-1} = u_{N-1}; z_t = u_t + L_t z_{t+1} (t = N-2..1);
+  // z_0 = u_0 + L_0 z_1 - L_{N-1} z_{N-1}
+  const size_t gl = (size_t)(N - 1) * V + r;
+  const R zl = z[gl];
+  R zn = zl;
+  for (int t = N - 2; t >= 1; --t) {
+    const size_t g = (size_t)t * V + r;
+    const R zt = z[g] + L[g] * zn;
+    z[g] = zt;
+    zn = zt;
+  }
+  z[r] = z[r] + L[r] * zn - L[gl] * zl;
+}
+
+cudaError_t launch_sca_apply(int prec, const void* L, const void* Di, const void* y, void* z,
+                             long long V, int ntau, const int* done, cudaStream_t st) {
+  const unsigned grid = (unsigned)((V + 127) / 128);
+  if (prec == 0)
+    sca_apply_kernel<double><<<grid, 128, 0, st>>>((const double*)L, (const double*)Di,
+                                                   (const double*)y, (double*)z, V, ntau, done);
+  else
+    sca_apply_kernel<float><<<grid, 128, 0, st>>>((const float*)L, (const float*)Di,
+                                                  (const float*)y, (float*)z, V, ntau, done);
+  return cudaGetLastError();
+}
+
+}  // namespace ufg

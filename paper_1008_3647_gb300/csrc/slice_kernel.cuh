@@ -1,0 +1,308 @@
+// The fused per-time-slice kernel behind every apply of the fermion matrix family.
+//
+// One CTA (or one thread-block cluster of C CTAs for the largest slices) owns `spc` consecutive
+// output time slices.  For each it
+//   1. streams the input slice t_in (t_out-1 for M-type, t_out+1 for M^T-type, t_out otherwise)
+//      from HBM into shared memory, multiplied on the fly by a per-site field (w = 1 + A sin sigma,
+//      s = sin sigma) and/or a per-mode table,
+//   2. applies the separable line operator along x and along y in shared memory (in place,
+//      padded rows of N+1 elements keep the three access patterns free of bank conflicts),
+//   3. applies it along z column by column (a cluster reads the other CTAs' planes through
+//      distributed shared memory) and finishes every output site in registers: antiperiodic
+//      time-shift sign, post-multiplication, identity term, linear-combination epilogue and
+//      FP64 dot-product partials, one coalesced HBM write.
+//
+// Operator families (line operator along all three axes):
+//   KIN: T = exp(-tau K) restricted to one axis (REAL -> REAL)      -> M, M^T, M1, M1^T, force
+//   FWD: F^T, the real orthonormal Fourier basis (REAL -> SPEC)     -> momentum space
+//   INV: F (SPEC -> REAL)                                           -> back to real space
+//
+// Epilogue for an output site g of slice t_out (sgn = +1 for the antiperiodic wrap, -1 for the
+// other shifted slices, +1 without shift):
+//   base = sgn * op(...)[g] * bkpost[mode] * post[g] * post2[g] + id[g]      (absent factors = 1/0)
+//   out[g] = a * base + bU * U[g] + cV * V[g];  partials += (out*dotP, out*out) in FP64.
+#pragma once
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "line_ops.cuh"
+#include "slice_call.h"
+
+namespace ufg {
+
+namespace cg = cooperative_groups;
+
+template <int N, typename R>
+struct SliceArgs {
+  LineCoef<N, R> coef;
+  const R* in;
+  const R* pre;
+  const R* bkpre;
+  const R* bkpost;
+  R* out;
+  const R* id;
+  const R* post;
+  const R* post2;
+  const R* U;
+  const R* V;
+  const R* dotP;
+  double a, bU, cV;
+  double* partials;
+  int want_dotP, want_self;
+  const int* done;
+  int ntau, shift, spc;
+};
+
+template <typename R> struct Vec16;
+template <> struct Vec16<float> { using T = float4; static constexpr int W = 4; };
+template <> struct Vec16<double> { using T = double2; static constexpr int W = 2; };
+
+template <typename R>
+__device__ __forceinline__ void ld16(const R* p, R (&o)[Vec16<R>::W]) {
+  typename Vec16<R>::T v = __ldg(reinterpret_cast<const typename Vec16<R>::T*>(p));
+  if constexpr (Vec16<R>::W == 4) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+  else { o[0] = v.x; o[1] = v.y; }
+}
+
+constexpr int SLICE_NT = 256;
+
+template <int N, typename R, int C, int FAM>
+__global__ void __launch_bounds__(SLICE_NT)
+slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
+  constexpr int NP = N / C;          // z-planes of one slice held by this CTA
+  constexpr int PITCH = N + 1;       // padded row
+  constexpr int PLANE = N * PITCH;   // shared-memory elements per plane
+  constexpr int NN = N * N;
+  constexpr int VOL = N * N * N;
+  constexpr int CHUNK = NP * NN;     // HBM elements per slice per CTA
+  constexpr int VW = Vec16<R>::W;
+  constexpr bool IN_SPEC = (FAM == FAM_INV);
+  constexpr bool OUT_SPEC = (FAM == FAM_FWD);
+  static_assert(CHUNK % VW == 0, "chunk must be a whole number of 16-byte vectors");
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sm = reinterpret_cast<R*>(smem_raw);
+  __shared__ double red[SLICE_NT / 32][2];
+
+  if (A.done != nullptr && *A.done) return;  // same value in every CTA of the grid
+
+  int rank = 0;
+  if constexpr (C > 1) rank = (int)cg::this_cluster().block_rank();
+  const int unit = blockIdx.x / C;
+  const int t0 = unit * A.spc;
+  const int nsl = min(A.spc, A.ntau - t0);
+  const int tid = threadIdx.x;
+
+  // ---- 1. load (with per-site / per-mode multipliers) ----
+  for (int s = 0; s < nsl; ++s) {
+    const int t_out = t0 + s;
+    int t_in = t_out;
+    if (A.shift < 0) t_in = (t_out == 0) ? A.ntau - 1 : t_out - 1;
+    if (A.shift > 0) t_in = (t_out == A.ntau - 1) ? 0 : t_out + 1;
+    const size_t gbase = (size_t)t_in * VOL + (size_t)rank * CHUNK;
+    R* dst = sm + s * NP * PLANE;
+    for (int e = tid * VW; e < CHUNK; e += SLICE_NT * VW) {
+      R v[VW];
+      ld16(A.in + gbase + e, v);
+      if (A.pre != nullptr) {
+        R w[VW];
+        ld16(A.pre + gbase + e, w);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) v[k] *= w[k];
+      }
+      if (A.bkpre != nullptr) {
+        R w[VW];
+        ld16(A.bkpre + (size_t)rank * CHUNK + e, w);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) v[k] *= w[k];
+      }
+#pragma unroll
+      for (int k = 0; k < VW; ++k) {
+        const int idx = e + k;
+        const int p = idx / NN;
+        const int rem = idx - p * NN;
+        const int row = rem / N;
+        const int col = rem - row * N;
+        dst[p * PLANE + row * PITCH + col] = v[k];
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- 2. x-pass and y-pass, in place ----
+  const int nlines = nsl * NP * N;
+  for (int l = tid; l < nlines; l += SLICE_NT) {
+    const int pl = l / N, r = l - (l / N) * N;
+    R* base = sm + pl * PLANE + r * PITCH;
+    R v[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = base[j];
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef, [&](int i, R val) { base[i] = val; });
+  }
+  __syncthreads();
+  for (int l = tid; l < nlines; l += SLICE_NT) {
+    const int pl = l / N, x = l - (l / N) * N;
+    R* base = sm + pl * PLANE + x;
+    R v[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = base[j * PITCH];
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef, [&](int i, R val) { base[i * PITCH] = val; });
+  }
+  if constexpr (C > 1) {
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+
+  // ---- 3. z-pass + epilogue ----
+  const R* owner[C];
+#pragma unroll
+  for (int o = 0; o < C; ++o) {
+    if constexpr (C > 1) {
+      owner[o] = (o == rank) ? sm : cg::this_cluster().map_shared_rank(sm, o);
+    } else {
+      owner[o] = sm;
+    }
+  }
+  constexpr int COLS = NN / C;
+  double acc_dot = 0.0, acc_self = 0.0;
+  const int ncols = nsl * COLS;
+  for (int l = tid; l < ncols; l += SLICE_NT) {
+    const int s = l / COLS;
+    const int q = rank * COLS + (l - s * COLS);
+    const int y = q / N, x = q - (q / N) * N;
+    const int t_out = t0 + s;
+    R sgn = R(1);
+    if (A.shift < 0 && t_out != 0) sgn = R(-1);
+    if (A.shift > 0 && t_out != A.ntau - 1) sgn = R(-1);
+    R v[N];
+#pragma unroll
+    for (int z = 0; z < N; ++z) {
+      v[z] = owner[z / NP][(s * NP + (z % NP)) * PLANE + y * PITCH + x];
+    }
+    const size_t obase = (size_t)t_out * VOL + q;
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef, [&](int zp, R val) {
+      const size_t g = obase + (size_t)zp * NN;
+      R b = sgn * val;
+      if (A.bkpost != nullptr) b *= A.bkpost[zp * NN + q];
+      if (A.post != nullptr) b *= A.post[g];
+      if (A.post2 != nullptr) b *= A.post2[g];
+      if (A.id != nullptr) b += A.id[g];
+      R o = R(A.a) * b;
+      if (A.U != nullptr) o += R(A.bU) * A.U[g];
+      if (A.V != nullptr) o += R(A.cV) * A.V[g];
+      A.out[g] = o;
+      if (A.want_dotP) acc_dot += (double)o * (double)A.dotP[g];
+      if (A.want_self) acc_self += (double)o * (double)o;
+    });
+  }
+
+  if (A.want_dotP || A.want_self) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc_dot += __shfl_xor_sync(0xffffffffu, acc_dot, off);
+      acc_self += __shfl_xor_sync(0xffffffffu, acc_self, off);
+    }
+    if ((tid & 31) == 0) {
+      red[tid >> 5][0] = acc_dot;
+      red[tid >> 5][1] = acc_self;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double d = 0.0, q2 = 0.0;
+      for (int w = 0; w < SLICE_NT / 32; ++w) {
+        d += red[w][0];
+        q2 += red[w][1];
+      }
+      A.partials[2 * blockIdx.x] = d;
+      A.partials[2 * blockIdx.x + 1] = q2;
+    }
+  }
+  if constexpr (C > 1) cg::this_cluster().sync();  // peers may still read this CTA's planes
+}
+
+template <int N, typename R>
+inline void fill_args(SliceArgs<N, R>& a, const SliceCall& c) {
+  a.coef = *reinterpret_cast<const LineCoef<N, R>*>(c.coef);
+  a.in = static_cast<const R*>(c.in);
+  a.pre = static_cast<const R*>(c.pre);
+  a.bkpre = static_cast<const R*>(c.bkpre);
+  a.bkpost = static_cast<const R*>(c.bkpost);
+  a.out = static_cast<R*>(c.out);
+  a.id = static_cast<const R*>(c.id);
+  a.post = static_cast<const R*>(c.post);
+  a.post2 = static_cast<const R*>(c.post2);
+  a.U = static_cast<const R*>(c.U);
+  a.V = static_cast<const R*>(c.V);
+  a.dotP = static_cast<const R*>(c.dotP);
+  a.a = c.a;
+  a.bU = c.bU;
+  a.cV = c.cV;
+  a.partials = c.partials;
+  a.want_dotP = c.want_dotP;
+  a.want_self = c.want_self;
+  a.done = c.done;
+  a.ntau = c.ntau;
+  a.shift = c.shift;
+  a.spc = c.spc;
+}
+
+template <int N, typename R, int C, int FAM>
+inline cudaError_t launch_one(const SliceCall& c, cudaStream_t st) {
+  SliceArgs<N, R> a;
+  fill_args<N, R>(a, c);
+  constexpr int PLANE = N * (N + 1);
+  const size_t smem = (size_t)c.spc * (N / C) * PLANE * sizeof(R);
+  auto kern = slice_kernel<N, R, C, FAM>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int units = (c.ntau + c.spc - 1) / c.spc;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(units * C);
+  cfg.blockDim = dim3(SLICE_NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (C > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <int N, typename R, int FAM>
+inline cudaError_t launch_C(const SliceCall& c, cudaStream_t st) {
+  if constexpr (N >= 16) {
+    if (c.C == 4) return launch_one<N, R, 4, FAM>(c, st);
+    if (c.C == 2) return launch_one<N, R, 2, FAM>(c, st);
+  }
+  if (c.C == 1) {
+    // an FP64 32^3 slice (270 KB padded) exceeds one CTA's shared memory
+    if constexpr (N < 32 || sizeof(R) == 4) return launch_one<N, R, 1, FAM>(c, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int N>
+cudaError_t slice_launch(const SliceCall& c, cudaStream_t st) {
+  if (c.prec == 0) {
+    switch (c.fam) {
+      case FAM_KIN: return launch_C<N, double, FAM_KIN>(c, st);
+      case FAM_FWD: return launch_C<N, double, FAM_FWD>(c, st);
+      case FAM_INV: return launch_C<N, double, FAM_INV>(c, st);
+    }
+  } else {
+    switch (c.fam) {
+      case FAM_KIN: return launch_C<N, float, FAM_KIN>(c, st);
+      case FAM_FWD: return launch_C<N, float, FAM_FWD>(c, st);
+      case FAM_INV: return launch_C<N, float, FAM_INV>(c, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ufg

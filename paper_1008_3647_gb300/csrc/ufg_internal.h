@@ -1,0 +1,114 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "slice_call.h"
+#include "ufg.h"
+
+namespace ufg {
+
+// ---- errors -------------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+ufg_status cuda_fail(cudaError_t e, const char* what);
+
+#define UFG_CUDA(call)                                              \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return ::ufg::cuda_fail(e_, #call);      \
+  } while (0)
+
+#define UFG_TRY(call)                                               \
+  do {                                                              \
+    ufg_status s_ = (call);                                         \
+    if (s_ != UFG_OK) return s_;                                    \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---- small device buffers -----------------------------------------------------------------
+template <typename T>
+ufg_status dev_alloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return UFG_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    set_error("cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+    return UFG_OOM;
+  }
+  return UFG_OK;
+}
+template <typename T>
+void dev_free(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+// ---- kernels living in other translation units --------------------------------------------
+// Per-site potentials from sigma (FP64 in, FP64 + FP32 out).
+cudaError_t launch_potentials(const double* sigma, double A, long long S, double* w64, double* s64,
+                              double* c64, float* w32, float* s32, float* c32, cudaStream_t st);
+// Exact M0^{-1} (transpose = 0) or M0^{-T} time recurrence per momentum mode, in place allowed.
+// out (nullable) = out_scale * x; acc_mode 0: none, 1: acc = acc_coef * x, 2: acc += acc_coef * x.
+cudaError_t launch_recurrence(int prec, const void* in, void* out, const void* bk, long long V,
+                              int ntau, int transpose, double out_scale, void* acc,
+                              double acc_coef, int acc_mode, const int* done, cudaStream_t st);
+// Strong-coupling factors (per site, sequential in t) and apply.
+cudaError_t launch_sca_setup(const double* w64, long long V, int ntau, double alpha, double* L64,
+                             double* Di64, float* L32, float* Di32, cudaStream_t st);
+cudaError_t launch_sca_apply(int prec, const void* L, const void* Di, const void* y, void* z,
+                             long long V, int ntau, const int* done, cudaStream_t st);
+
+}  // namespace ufg
+
+// ---- handles ------------------------------------------------------------------------------
+struct ufg_lattice {
+  int nx = 0, ntau = 0, dispersion = 0;
+  double tau = 0, g = 0, A = 0;
+  long long V = 0, S = 0;
+  std::vector<double> lam;                 // exp(-tau E1) per 1-D spectral slot
+  std::vector<unsigned char> coef[3][2];   // reduced line matrices [family][0 FP64 / 1 FP32]
+  double* bk64 = nullptr;                  // per-mode exp(-tau E(k)), spectral layout [V]
+  float* bk32 = nullptr;
+  int spc[2] = {1, 1};                     // slices per CTA (KIN family) per precision
+  int C[2] = {1, 1};                       // cluster size per precision
+  int device = 0;
+};
+
+struct ufg_field {
+  const ufg_lattice* lat = nullptr;
+  double* sigma = nullptr;
+  double* w64 = nullptr;
+  double* s64 = nullptr;
+  double* c64 = nullptr;
+  float* w32 = nullptr;
+  float* s32 = nullptr;
+  float* c32 = nullptr;
+  double* tmp64 = nullptr;  // apply workspace (Q intermediate, momentum-space temp)
+  float* tmp32 = nullptr;
+  double sca_alpha = -1.0;  // alpha the SCA tables were built for (< 0: none)
+  double* L64 = nullptr;
+  double* Di64 = nullptr;
+  float* L32 = nullptr;
+  float* Di32 = nullptr;
+};
+
+namespace ufg {
+
+// Generic slice-kernel call prefilled for a field/lattice and precision.
+SliceCall base_call(const ufg_lattice* lat, int fam, int prec);
+// Operator applications used by the C ABI and by the solvers (vectors in precision prec).
+ufg_status op_M(const ufg_field* f, int prec, const void* x, void* y, cudaStream_t st);
+ufg_status op_Mdag(const ufg_field* f, int prec, const void* x, void* y, cudaStream_t st);
+ufg_status op_M0inv(const ufg_field* f, int prec, const void* x, void* y, void* tmp, int transpose,
+                    cudaStream_t st);
+ufg_status ensure_sca(ufg_field* f, double alpha, cudaStream_t st);
+const void* fld(const ufg_field* f, char which, int prec);  // 'w', 's', 'c'
+
+}  // namespace ufg
