@@ -87,6 +87,8 @@ vec_kernel(long long n, const DevScalars* __restrict__ sc, R* a, R* b, R* c, R* 
     for (long long i = i0; i < n; i += stride) a[i] = b[i];
   } else if constexpr (OP == V_ZERO) {
     for (long long i = i0; i < n; i += stride) a[i] = R(0);
+  } else if constexpr (OP == V_ADD) {
+    for (long long i = i0; i < n; i += stride) a[i] += b[i];
   }
   if (part != nullptr) block_pair_store(d1, d2, part);
 }
@@ -107,6 +109,7 @@ static cudaError_t vec_dispatch(int op, long long n, const DevScalars* sc, R* a,
     CASE(V_DOT)
     CASE(V_COPY)
     CASE(V_ZERO)
+    CASE(V_ADD)
 #undef CASE
     default:
       return cudaErrorInvalidValue;

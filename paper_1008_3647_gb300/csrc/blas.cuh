@@ -54,6 +54,7 @@ enum VecOp {
   V_DOT,            // part = (a.b, c.d)
   V_COPY,           // a <- b
   V_ZERO,           // a <- 0
+  V_ADD,            // a += b
 };
 cudaError_t launch_vec(int prec, int op, long long n, const DevScalars* sc, void* a, void* b,
                        void* c, void* d, void* e, void* f, double* part, int* nparts,

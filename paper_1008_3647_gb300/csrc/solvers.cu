@@ -1,0 +1,1075 @@
+// Krylov solvers on the fused operators: CG on M^T M x = b (Eq. 1), two-step BiCGStab
+// M^T y = b, M x = y (Eq. 2), the Chebyshev (Sec. 2), strong-coupling (Sec. 4) and weak-coupling
+// (Sec. 3) preconditioners, the FP32-inner / FP64-outer defect-correction loop, and the HMC force.
+//
+// Each Krylov iteration is a fixed sequence of kernels whose scalars live in device memory
+// (blas.cuh), so the host captures `check_every` iterations into a CUDA graph once and replays it,
+// reading back the convergence flag between replays.  The solver runs on its own non-blocking
+// stream ordered after/before the caller's stream by events.
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "blas.cuh"
+#include "ufg_internal.h"
+
+using namespace ufg;
+
+namespace {
+
+enum Slot { P_SLICE1 = 0, P_SLICE2, P_VEC1, P_VEC2, P_DOT, P_PC, P_RES, NSLOT };
+enum OpKind { OPK_M = 0, OPK_MDAG = 1, OPK_Q = 2 };
+
+struct VecSet {
+  void *r = nullptr, *rhat = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr,
+       *y = nullptr, *z = nullptr, *q = nullptr, *tmp = nullptr, *u = nullptr, *acc = nullptr,
+       *spec = nullptr, *wr = nullptr, *x = nullptr, *rhs = nullptr;
+};
+
+struct Counts {
+  long long M = 0, Mdag = 0, M1 = 0, M1T = 0, M0inv = 0, M0invT = 0, sca = 0;
+};
+
+}  // namespace
+
+struct ufg_solver {
+  const ufg_lattice* lat = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  int pc_kind = UFG_PC_NONE;
+  ufg_pc_params pc = {};
+  VecSet vs[2];
+  double* x64 = nullptr;    // FP64 solution accumulator (outer loops, host staging)
+  double* b64 = nullptr;    // FP64 right-hand side staging
+  double* r64 = nullptr;    // FP64 residual (outer loops, true residual)
+  double* y64 = nullptr;    // FP64 intermediate of the two-step solve
+  double* rc64 = nullptr;   // FP64 composite residual of the correction round
+  double* xs64 = nullptr;   // FP64 solution saved across the correction round
+  double* xf64 = nullptr;   // FP64 X of the force when the caller does not keep it
+  double* parts = nullptr;  // NSLOT x [MAX_PARTIAL_CTAS][2]
+  DevScalars* sc = nullptr;
+  DevScalars* sc_host = nullptr;  // pinned
+  double* red_dev = nullptr;      // scratch scalar for host-visible reductions
+  double* red_host = nullptr;     // pinned
+  std::map<std::string, cudaGraphExec_t> graphs;
+  Counts counts;
+};
+
+namespace {
+
+double* slot(ufg_solver* S, int k) { return S->parts + (size_t)k * 2 * MAX_PARTIAL_CTAS; }
+
+int slice_grid(const ufg_lattice* L, int prec) {
+  const int units = (L->ntau + L->spc[prec] - 1) / L->spc[prec];
+  return units * L->C[prec];
+}
+
+// ---- operator applications with epilogues --------------------------------------------------
+// out = a * (A in) + bU * U   with partials (out . dotP, out . out) into `part` when requested.
+ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const void* in, void* out,
+                    double a, const void* U, double bU, const void* dotP, bool self, double* part,
+                    int* nparts) {
+  const ufg_lattice* L = f->lat;
+  const int* done = &S->sc->done;
+  if (op == OPK_Q) {
+    void* t1 = S->vs[prec].tmp;
+    SliceCall c = base_call(L, FAM_KIN, prec);
+    c.in = in;
+    c.pre = fld(f, 'w', prec);
+    c.id = in;
+    c.shift = -1;
+    c.out = t1;
+    c.done = done;
+    cudaError_t e = slice_dispatch(L->nx, c, S->st);
+    if (e != cudaSuccess) return cuda_fail(e, "slice kernel (M of Q)");
+    in = t1;
+    op = OPK_MDAG;
+    S->counts.M++;
+  }
+  SliceCall c = base_call(L, FAM_KIN, prec);
+  c.in = in;
+  c.id = in;
+  if (op == OPK_M) {
+    c.pre = fld(f, 'w', prec);
+    c.shift = -1;
+    S->counts.M++;
+  } else {
+    c.post = fld(f, 'w', prec);
+    c.shift = +1;
+    S->counts.Mdag++;
+  }
+  c.out = out;
+  c.a = a;
+  c.U = U;
+  c.bU = bU;
+  c.dotP = dotP;
+  c.want_dotP = dotP != nullptr;
+  c.want_self = self;
+  c.partials = part;
+  c.done = done;
+  if (nparts) *nparts = slice_grid(L, prec);
+  cudaError_t e = slice_dispatch(L->nx, c, S->st);
+  if (e != cudaSuccess) return cuda_fail(e, "slice kernel");
+  return UFG_OK;
+}
+
+#define VEC(prec, op, n, a, b, c, d, e, f, part, np)                                         \
+  do {                                                                                        \
+    cudaError_t err_ = launch_vec(prec, op, n, S->sc, (void*)(a), (void*)(b), (void*)(c),     \
+                                  (void*)(d), (void*)(e), (void*)(f), part, np, S->st);       \
+    if (err_ != cudaSuccess) return cuda_fail(err_, "vector kernel");                         \
+  } while (0)
+
+#define VEC_NODONE(prec, op, n, a, b, c, d, e, f, part, np)                                  \
+  do {                                                                                        \
+    cudaError_t err_ = launch_vec(prec, op, n, nullptr, (void*)(a), (void*)(b), (void*)(c),   \
+                                  (void*)(d), (void*)(e), (void*)(f), part, np, S->st);       \
+    if (err_ != cudaSuccess) return cuda_fail(err_, "vector kernel");                         \
+  } while (0)
+
+#define SCALAR(op, part, np, part2, np2)                                                      \
+  do {                                                                                        \
+    cudaError_t err_ = launch_scalar(op, S->sc, part, np, part2, np2, S->st);                 \
+    if (err_ != cudaSuccess) return cuda_fail(err_, "scalar kernel");                         \
+  } while (0)
+
+// ---- preconditioners (z = P r in precision prec) -------------------------------------------
+ufg_status pc_cheb(ufg_solver* S, const ufg_field* f, int prec, const void* r, void* z) {
+  const ufg_lattice* L = f->lat;
+  const int d = S->pc.degree, n = d / 2;
+  const double s = S->pc.scale > 0 ? S->pc.scale : (2.0 + L->A) * (2.0 + L->A);
+  const double eps = S->pc.eps > 0 ? S->pc.eps
+                                   : (2.0 - 2.0 * std::cos(3.14159265358979323846 / L->ntau)) / s;
+  const double z0 = 0.5 * (1.0 + eps);
+  // conjugate root pairs k = 1..n: a_k = z0 (1 - cos th), b_k = sqrt(eps) sin th, th = 2 pi k/(2n+1)
+  std::vector<double> ak(n), bk2(n), nk(n);
+  for (int k = 0; k < n; ++k) {
+    const double th = 2.0 * 3.14159265358979323846 * (k + 1) / (2 * n + 1);
+    ak[k] = z0 * (1.0 - std::cos(th));
+    const double bb = std::sqrt(eps) * std::sin(th);
+    bk2[k] = bb * bb;
+    nk[k] = (z0 - ak[k]) * (z0 - ak[k]) + bk2[k];
+  }
+  // bit-reversed order of the n factors
+  int bits = 0;
+  while ((1 << bits) < n) ++bits;
+  if (bits == 0) bits = 1;
+  std::vector<int> order;
+  for (int i = 0; i < (1 << bits); ++i) {
+    int rv = 0;
+    for (int b = 0; b < bits; ++b)
+      if (i & (1 << b)) rv |= 1 << (bits - 1 - b);
+    if (rv < n) order.push_back(rv);
+  }
+  VecSet& V = S->vs[prec];
+  const void* cur = r;
+  for (size_t j = 0; j < order.size(); ++j) {
+    const int k = order[j];
+    const bool last = (j + 1 == order.size());
+    const double fin = last ? 1.0 / (z0 * s) : 1.0;
+    // u = Q cur / s - a_k cur
+    UFG_TRY(apply_op(S, f, prec, OPK_Q, cur, V.u, 1.0 / s, cur, -ak[k], nullptr, false, nullptr,
+                     nullptr));
+    // z = [Q u / s - a_k u + b_k^2 cur] / norm_k (* 1/(z0 s) for the last factor)
+    void* t1 = V.tmp;
+    SliceCall c = base_call(L, FAM_KIN, prec);
+    c.in = V.u;
+    c.pre = fld(f, 'w', prec);
+    c.id = V.u;
+    c.shift = -1;
+    c.out = t1;
+    c.done = &S->sc->done;
+    cudaError_t e = slice_dispatch(L->nx, c, S->st);
+    if (e != cudaSuccess) return cuda_fail(e, "slice kernel (Chebyshev)");
+    S->counts.M++;
+    SliceCall c2 = base_call(L, FAM_KIN, prec);
+    c2.in = t1;
+    c2.post = fld(f, 'w', prec);
+    c2.id = t1;
+    c2.shift = +1;
+    c2.out = z;
+    c2.a = fin / (s * nk[k]);
+    c2.U = V.u;
+    c2.bU = -fin * ak[k] / nk[k];
+    c2.V = cur;
+    c2.cV = fin * bk2[k] / nk[k];
+    c2.done = &S->sc->done;
+    e = slice_dispatch(L->nx, c2, S->st);
+    if (e != cudaSuccess) return cuda_fail(e, "slice kernel (Chebyshev)");
+    S->counts.Mdag++;
+    cur = z;
+  }
+  return UFG_OK;
+}
+
+// Euler p = 1/2 weights c_n = 2^-d sum_{k=n}^{d} C(d, k): the result of applying the Euler
+// recursion S_{j+1,k} = (S_{j,k} + S_{j,k+1}) / 2 d times to the partial sums (Sec. 3.1).
+std::vector<double> wce_weights(int d, bool euler) {
+  std::vector<double> c(d + 1, 1.0);
+  if (!euler || d == 0) return c;
+  std::vector<double> binom(d + 1, 0.0);
+  binom[0] = 1.0;
+  for (int i = 1; i <= d; ++i)
+    for (int k = i; k >= 1; --k) binom[k] += binom[k - 1];
+  for (int nn = 0; nn <= d; ++nn) {
+    double acc = 0.0;
+    for (int k = nn; k <= d; ++k) acc += binom[k];
+    c[nn] = acc / std::ldexp(1.0, d);
+  }
+  return c;
+}
+
+// P_d r = sum_n c_n (-A)^n (M0^{-1} M1)^n M0^{-1} r (transpose: its exact transpose), evaluated in
+// momentum space: every M0^{-1} is the per-mode recurrence, M1 / M1^T are fused with the
+// transforms (F^T M1 w = sgn exp(-tau E) F^T(s w_shifted), M1^T F x = sgn s F(exp(-tau E) x_shifted)).
+ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, void* z, bool tr) {
+  const ufg_lattice* L = f->lat;
+  const int d = S->pc.order;
+  const std::vector<double> cw = wce_weights(d, S->pc.euler != 0);
+  VecSet& V = S->vs[prec];
+  const void* bk = prec ? (const void*)L->bk32 : (const void*)L->bk64;
+  const int* done = &S->sc->done;
+  auto rec = [&](double coef, int acc_mode, bool write_out) -> ufg_status {
+    cudaError_t e = launch_recurrence(prec, V.spec, write_out ? V.spec : nullptr, bk, L->V,
+                                      L->ntau, tr ? 1 : 0, 1.0, V.acc, coef, acc_mode, done,
+                                      S->st);
+    if (e != cudaSuccess) return cuda_fail(e, "recurrence kernel");
+    if (tr) S->counts.M0invT++; else S->counts.M0inv++;
+    return UFG_OK;
+  };
+  SliceCall fw = base_call(L, FAM_FWD, prec);
+  fw.in = r;
+  fw.out = V.spec;
+  fw.done = done;
+  cudaError_t e = slice_dispatch(L->nx, fw, S->st);
+  if (e != cudaSuccess) return cuda_fail(e, "forward transform");
+  UFG_TRY(rec(cw[0], 1, d > 0));
+  for (int nn = 1; nn <= d; ++nn) {
+    if (!tr) {
+      SliceCall iv = base_call(L, FAM_INV, prec);  // w = F spec
+      iv.in = V.spec;
+      iv.out = V.wr;
+      iv.done = done;
+      e = slice_dispatch(L->nx, iv, S->st);
+      if (e != cudaSuccess) return cuda_fail(e, "inverse transform");
+      SliceCall m1 = base_call(L, FAM_FWD, prec);  // spec = -A F^T (M1 w)
+      m1.in = V.wr;
+      m1.pre = fld(f, 's', prec);
+      m1.bkpost = bk;
+      m1.shift = -1;
+      m1.a = -L->A;
+      m1.out = V.spec;
+      m1.done = done;
+      e = slice_dispatch(L->nx, m1, S->st);
+      if (e != cudaSuccess) return cuda_fail(e, "M1 + forward transform");
+      S->counts.M1++;
+    } else {
+      SliceCall m1t = base_call(L, FAM_INV, prec);  // u = -A M1^T (F spec)
+      m1t.in = V.spec;
+      m1t.bkpre = bk;
+      m1t.post = fld(f, 's', prec);
+      m1t.shift = +1;
+      m1t.a = -L->A;
+      m1t.out = V.wr;
+      m1t.done = done;
+      e = slice_dispatch(L->nx, m1t, S->st);
+      if (e != cudaSuccess) return cuda_fail(e, "M1^T + inverse transform");
+      SliceCall fw2 = base_call(L, FAM_FWD, prec);
+      fw2.in = V.wr;
+      fw2.out = V.spec;
+      fw2.done = done;
+      e = slice_dispatch(L->nx, fw2, S->st);
+      if (e != cudaSuccess) return cuda_fail(e, "forward transform");
+      S->counts.M1T++;
+    }
+    UFG_TRY(rec(cw[nn], 2, nn < d));
+  }
+  SliceCall iv = base_call(L, FAM_INV, prec);
+  iv.in = V.acc;
+  iv.out = z;
+  iv.done = done;
+  e = slice_dispatch(L->nx, iv, S->st);
+  if (e != cudaSuccess) return cuda_fail(e, "inverse transform");
+  return UFG_OK;
+}
+
+// Per-field preconditioner set-up that allocates or launches once (kept out of captured graphs).
+ufg_status pc_prepare(ufg_solver* S, ufg_field* f) {
+  if (S->pc_kind == UFG_PC_SCA) return ensure_sca(f, S->pc.alpha, S->st);
+  return UFG_OK;
+}
+
+ufg_status pc_apply(ufg_solver* S, ufg_field* f, int prec, const void* r, void* z, bool tr) {
+  switch (S->pc_kind) {
+    case UFG_PC_CHEB:
+      return pc_cheb(S, f, prec, r, z);
+    case UFG_PC_SCA: {
+      if (f->sca_alpha != S->pc.alpha || f->L64 == nullptr) {
+        set_error("SCA tables not prepared");
+        return UFG_INTERNAL;
+      }
+      const void* Lt = prec ? (const void*)f->L32 : (const void*)f->L64;
+      const void* Di = prec ? (const void*)f->Di32 : (const void*)f->Di64;
+      cudaError_t e = launch_sca_apply(prec, Lt, Di, r, z, f->lat->V, f->lat->ntau, &S->sc->done,
+                                       S->st);
+      if (e != cudaSuccess) return cuda_fail(e, "SCA apply");
+      S->counts.sca++;
+      return UFG_OK;
+    }
+    case UFG_PC_WCE:
+      return pc_wce(S, f, prec, r, z, tr);
+  }
+  set_error("no preconditioner selected");
+  return UFG_INVALID_ARG;
+}
+
+// ---- graph replay ---------------------------------------------------------------------------
+bool graphs_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("UFG_NO_GRAPH");
+    v = (e && e[0] == '1') ? 0 : 1;
+  }
+  return v == 1;
+}
+
+template <class Body>
+ufg_status run_body(ufg_solver* S, const std::string& key, int reps, Body&& body) {
+  if (!graphs_enabled()) {
+    for (int i = 0; i < reps; ++i) UFG_TRY(body());
+    return UFG_OK;
+  }
+  auto it = S->graphs.find(key);
+  if (it == S->graphs.end()) {
+    if (S->graphs.size() > 64) {
+      for (auto& kv : S->graphs) cudaGraphExecDestroy(kv.second);
+      S->graphs.clear();
+    }
+    const Counts saved = S->counts;
+    UFG_CUDA(cudaStreamBeginCapture(S->st, cudaStreamCaptureModeThreadLocal));
+    ufg_status s = UFG_OK;
+    for (int i = 0; i < reps && s == UFG_OK; ++i) s = body();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(S->st, &g);
+    S->counts = saved;
+    if (s != UFG_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    it = S->graphs.emplace(key, ex).first;
+  }
+  UFG_CUDA(cudaGraphLaunch(it->second, S->st));
+  return UFG_OK;
+}
+
+ufg_status read_scalars(ufg_solver* S) {
+  UFG_CUDA(cudaMemcpyAsync(S->sc_host, S->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, S->st));
+  UFG_CUDA(cudaStreamSynchronize(S->st));
+  return UFG_OK;
+}
+
+ufg_status write_scalars(ufg_solver* S, double tol, int maxit) {
+  std::memset(S->sc_host, 0, sizeof(DevScalars));
+  S->sc_host->tol = tol;
+  S->sc_host->maxit = maxit;
+  S->sc_host->restart_cos = 1e-12;
+  S->sc_host->rho_old = S->sc_host->alpha = S->sc_host->omega = 1.0;
+  UFG_CUDA(cudaMemcpyAsync(S->sc, S->sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice, S->st));
+  return UFG_OK;
+}
+
+std::string key_of(const char* kind, ufg_solver* S, const ufg_field* f, int prec, int op,
+                   int reps) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s|%p|%d|%d|%d|%d|%d|%g|%g|%g|%d|%d", kind, (const void*)f, prec, op,
+           reps, S->pc_kind, S->pc.degree, S->pc.eps, S->pc.scale, S->pc.alpha, S->pc.order,
+           S->pc.euler);
+  return buf;
+}
+
+struct KrylovResult {
+  int iters = 0;
+  int restarts = 0;
+  int done = 0;
+};
+
+// ---- CG on Q x = rhs (vectors of precision prec; rhs, x live in the VecSet) ----------------
+ufg_status run_cg(ufg_solver* S, ufg_field* f, int prec, double tol, int maxit, int check_every,
+                  bool x0, KrylovResult* res) {
+  VecSet& V = S->vs[prec];
+  const long long n = f->lat->S;
+  const bool pc = S->pc_kind == UFG_PC_CHEB || S->pc_kind == UFG_PC_SCA;
+  UFG_TRY(write_scalars(S, tol, maxit));
+  int np = 0, npd = 0, nps = 0;
+  if (x0) {
+    UFG_TRY(apply_op(S, f, prec, OPK_Q, V.x, V.r, -1.0, V.rhs, 1.0, nullptr, false, nullptr,
+                     nullptr));
+  } else {
+    VEC_NODONE(prec, V_COPY, n, V.r, V.rhs, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    VEC_NODONE(prec, V_ZERO, n, V.x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+  }
+  void* z = pc ? V.z : V.r;
+  if (pc) UFG_TRY(pc_apply(S, f, prec, V.r, V.z, false));
+  VEC_NODONE(prec, V_DOT, n, V.r, z, V.r, V.r, nullptr, nullptr, slot(S, P_DOT), &npd);
+  VEC_NODONE(prec, V_DOT, n, nullptr, nullptr, V.rhs, V.rhs, nullptr, nullptr, slot(S, P_RES), &nps);
+  SCALAR(OP_CG_INIT, slot(S, P_DOT), npd, slot(S, P_RES), nps);
+  VEC_NODONE(prec, V_COPY, n, V.p, z, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+  auto body = [&]() -> ufg_status {
+    int nq = 0, nv = 0, npc = 0;
+    UFG_TRY(apply_op(S, f, prec, OPK_Q, V.p, V.q, 1.0, nullptr, 0.0, V.p, false, slot(S, P_SLICE1),
+                     &nq));
+    SCALAR(OP_CG_ALPHA, slot(S, P_SLICE1), nq, nullptr, 0);
+    VEC(prec, V_CG_UPDATE, n, V.x, V.p, V.r, V.q, nullptr, nullptr, slot(S, P_VEC1), &nv);
+    SCALAR(OP_CG_CHECK, slot(S, P_VEC1), nv, nullptr, 0);
+    if (pc) {
+      UFG_TRY(pc_apply(S, f, prec, V.r, V.z, false));
+      VEC(prec, V_DOT, n, V.r, V.z, nullptr, nullptr, nullptr, nullptr, slot(S, P_PC), &npc);
+      SCALAR(OP_CG_BETA, slot(S, P_PC), npc, nullptr, 0);
+    } else {
+      SCALAR(OP_CG_BETA, nullptr, 0, slot(S, P_VEC1), nv);
+    }
+    VEC(prec, V_CG_P, n, V.p, z, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    return UFG_OK;
+  };
+  (void)np;
+  const Counts c0 = S->counts;
+  const std::string key = key_of("cg", S, f, prec, 0, check_every);
+  while (true) {
+    UFG_TRY(read_scalars(S));
+    const DevScalars& h = *S->sc_host;
+    if (h.done != 0) break;
+    UFG_TRY(run_body(S, key, check_every, body));
+    S->counts = c0;
+  }
+  res->iters = S->sc_host->iters;
+  res->done = S->sc_host->done;
+  // applies per iteration: Q (one M, one M^T) plus the preconditioner (Chebyshev: d Q applies,
+  // SCA: one sweep); the initial preconditioner application adds one more
+  const long long it = res->iters, it_pc = res->iters + 1;
+  S->counts.M += it + (x0 ? 1 : 0);
+  S->counts.Mdag += it + (x0 ? 1 : 0);
+  if (S->pc_kind == UFG_PC_CHEB) {
+    S->counts.M += (long long)S->pc.degree * it_pc;
+    S->counts.Mdag += (long long)S->pc.degree * it_pc;
+  }
+  if (S->pc_kind == UFG_PC_SCA) S->counts.sca += it_pc;
+  return UFG_OK;
+}
+
+// ---- BiCGStab on A x = rhs, A = M or M^T, right preconditioner P_d or P_d^T -----------------
+ufg_status run_bicgstab(ufg_solver* S, ufg_field* f, int prec, int op, double tol, int maxit,
+                        int check_every, bool x0, KrylovResult* res) {
+  VecSet& V = S->vs[prec];
+  const long long n = f->lat->S;
+  const bool pc = S->pc_kind == UFG_PC_WCE;
+  const bool tr = (op == OPK_MDAG);
+  UFG_TRY(write_scalars(S, tol, maxit));
+  auto restart = [&](bool have_x) -> ufg_status {
+    int n1 = 0, n2 = 0;
+    if (have_x) {
+      UFG_TRY(apply_op(S, f, prec, op, V.x, V.r, -1.0, V.rhs, 1.0, nullptr, false, nullptr,
+                       nullptr));
+    } else {
+      VEC_NODONE(prec, V_COPY, n, V.r, V.rhs, nullptr, nullptr, nullptr, nullptr, nullptr,
+                 nullptr);
+      VEC_NODONE(prec, V_ZERO, n, V.x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                 nullptr);
+    }
+    VEC_NODONE(prec, V_COPY, n, V.rhat, V.r, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    VEC_NODONE(prec, V_ZERO, n, V.v, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    VEC_NODONE(prec, V_ZERO, n, V.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    VEC_NODONE(prec, V_DOT, n, V.rhat, V.r, V.r, V.r, nullptr, nullptr, slot(S, P_VEC2), &n1);
+    VEC_NODONE(prec, V_DOT, n, V.rhat, V.rhat, V.rhs, V.rhs, nullptr, nullptr, slot(S, P_DOT), &n2);
+    SCALAR(OP_BI_INIT, slot(S, P_VEC2), n1, slot(S, P_DOT), n2);
+    return UFG_OK;
+  };
+  UFG_TRY(restart(x0));
+  const int nv_grid = vec_grid(n);
+  auto body = [&]() -> ufg_status {
+    int nsv = 0, nst = 0, nv = 0;
+    SCALAR(OP_BI_RHO, slot(S, P_VEC2), nv_grid, nullptr, 0);
+    VEC(prec, V_BI_P, n, V.p, V.r, V.v, nullptr, nullptr, nullptr, nullptr, nullptr);
+    void* y = V.p;
+    if (pc) {
+      UFG_TRY(pc_apply(S, f, prec, V.p, V.y, tr));
+      y = V.y;
+    }
+    UFG_TRY(apply_op(S, f, prec, op, y, V.v, 1.0, nullptr, 0.0, V.rhat, false, slot(S, P_SLICE1),
+                     &nsv));
+    SCALAR(OP_BI_ALPHA, slot(S, P_SLICE1), nsv, nullptr, 0);
+    VEC(prec, V_BI_S, n, V.s, V.r, V.v, V.x, y, nullptr, slot(S, P_VEC1), &nv);
+    SCALAR(OP_BI_SCHECK, slot(S, P_VEC1), nv, nullptr, 0);
+    void* z = V.s;
+    if (pc) {
+      UFG_TRY(pc_apply(S, f, prec, V.s, V.z, tr));
+      z = V.z;
+    }
+    UFG_TRY(apply_op(S, f, prec, op, z, V.t, 1.0, nullptr, 0.0, V.s, true, slot(S, P_SLICE2),
+                     &nst));
+    SCALAR(OP_BI_OMEGA, slot(S, P_SLICE2), nst, nullptr, 0);
+    VEC(prec, V_BI_X, n, V.x, z, V.r, V.s, V.t, V.rhat, slot(S, P_VEC2), &nv);
+    SCALAR(OP_BI_RCHECK, slot(S, P_VEC2), nv, nullptr, 0);
+    return UFG_OK;
+  };
+  const Counts c0 = S->counts;
+  const std::string key = key_of(tr ? "bicg_t" : "bicg", S, f, prec, op, check_every);
+  int restarts = 0;
+  while (true) {
+    UFG_TRY(read_scalars(S));
+    const DevScalars& h = *S->sc_host;
+    if (h.done == 2) {  // near-breakdown: restart from the true residual, keep the count
+      if (restarts >= 100) break;
+      ++restarts;
+      UFG_TRY(restart(true));
+      continue;
+    }
+    if (h.done != 0) break;
+    UFG_TRY(run_body(S, key, check_every, body));
+    S->counts = c0;
+  }
+  res->iters = S->sc_host->iters;
+  res->restarts = restarts;
+  res->done = S->sc_host->done == 2 ? 3 : S->sc_host->done;
+  // applies per iteration: two of A, two preconditioner applications (WCE order d: d+1 exact
+  // M0^{-1} and d M1 each); every restart or initial guess adds one A for the true residual
+  const long long it = res->iters, extra = restarts + (x0 ? 1 : 0);
+  const int d = pc ? S->pc.order : -1;
+  if (tr) {
+    S->counts.Mdag += 2 * it + extra;
+    if (pc) { S->counts.M0invT += 2 * it * (d + 1); S->counts.M1T += 2 * it * d; }
+  } else {
+    S->counts.M += 2 * it + extra;
+    if (pc) { S->counts.M0inv += 2 * it * (d + 1); S->counts.M1 += 2 * it * d; }
+  }
+  return UFG_OK;
+}
+
+// ---- helpers on FP64 user vectors ---------------------------------------------------------
+ufg_status norm64(ufg_solver* S, const double* v, long long n, double* out) {
+  int np = 0;
+  VEC_NODONE(0, V_DOT, n, v, v, nullptr, nullptr, nullptr, nullptr, slot(S, P_RES), &np);
+  cudaError_t e = launch_reduce_to(slot(S, P_RES), np, 0, S->red_dev, S->st);
+  if (e != cudaSuccess) return cuda_fail(e, "reduce");
+  UFG_CUDA(cudaMemcpyAsync(S->red_host, S->red_dev, sizeof(double), cudaMemcpyDeviceToHost, S->st));
+  UFG_CUDA(cudaStreamSynchronize(S->st));
+  *out = std::sqrt(*S->red_host);
+  return UFG_OK;
+}
+
+// r64 = rhs - A x (FP64), returns ||r64||.
+ufg_status residual64(ufg_solver* S, ufg_field* f, int op, const double* x, const double* rhs,
+                      double* r, double* rn) {
+  UFG_TRY(write_scalars(S, 0.0, 0));  // clears `done` so the slice kernels run
+  int np = 0;
+  UFG_TRY(apply_op(S, f, 0, op, x, r, -1.0, rhs, 1.0, nullptr, true, slot(S, P_RES), &np));
+  cudaError_t e = launch_reduce_to(slot(S, P_RES), np, 1, S->red_dev, S->st);
+  if (e != cudaSuccess) return cuda_fail(e, "reduce");
+  UFG_CUDA(cudaMemcpyAsync(S->red_host, S->red_dev, sizeof(double), cudaMemcpyDeviceToHost, S->st));
+  UFG_CUDA(cudaStreamSynchronize(S->st));
+  *rn = std::sqrt(*S->red_host);
+  return UFG_OK;
+}
+
+struct SolveOut {
+  int iters = 0;
+  int outer = 0;
+  int restarts = 0;
+  int done = 0;
+};
+
+ufg_status status_of(int done) {
+  switch (done) {
+    case 1: return UFG_OK;
+    case 3: set_error("BiCGStab breakdown persisted through 100 restarts"); return UFG_BREAKDOWN;
+    case 4: set_error("non-finite value in the Krylov recursion"); return UFG_NONFINITE;
+    case 5: set_error("iteration limit reached"); return UFG_NOT_CONVERGED;
+  }
+  set_error("solver stopped in state %d", done);
+  return UFG_INTERNAL;
+}
+
+// Solves A x = rhs (A = M, M^T or Q) to relative tolerance tol, FP64 result in x64 (which holds
+// the initial guess if x0).  prec 0: FP64 Krylov; prec 2 (mixed): FP64 defect correction around
+// FP32 Krylov solves to inner_tol.
+ufg_status solve_system(ufg_solver* S, ufg_field* f, int op, const double* rhs, double* x64,
+                        bool x0, double tol, const ufg_params* p, SolveOut* out) {
+  const long long n = f->lat->S;
+  const int ce = p->check_every > 0 ? p->check_every : 8;
+  auto krylov = [&](int prec, double t, bool guess, KrylovResult* kr) -> ufg_status {
+    if (op == OPK_Q) return run_cg(S, f, prec, t, p->maxit, ce, guess, kr);
+    return run_bicgstab(S, f, prec, op, t, p->maxit, ce, guess, kr);
+  };
+  if (p->precision != UFG_MIXED) {
+    VecSet& V = S->vs[0];
+    UFG_CUDA(cudaMemcpyAsync(V.rhs, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, S->st));
+    if (x0) UFG_CUDA(cudaMemcpyAsync(V.x, x64, n * sizeof(double), cudaMemcpyDeviceToDevice, S->st));
+    KrylovResult kr;
+    UFG_TRY(krylov(0, tol, x0, &kr));
+    UFG_CUDA(cudaMemcpyAsync(x64, V.x, n * sizeof(double), cudaMemcpyDeviceToDevice, S->st));
+    out->iters += kr.iters;
+    out->restarts += kr.restarts;
+    out->done = kr.done;
+    return UFG_OK;
+  }
+  // mixed precision: x64 += ||r|| e32 with Q e32 = r / ||r|| solved in FP32
+  double bn = 0.0;
+  UFG_TRY(norm64(S, rhs, n, &bn));
+  if (!x0) UFG_CUDA(cudaMemsetAsync(x64, 0, n * sizeof(double), S->st));
+  VecSet& V = S->vs[1];
+  const double inner = p->inner_tol > 0 ? p->inner_tol : 1e-5;
+  out->done = 5;
+  for (int outer = 0; outer < 60; ++outer) {
+    double rn = 0.0;
+    if (outer == 0 && !x0) {
+      UFG_CUDA(cudaMemcpyAsync(S->r64, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, S->st));
+      rn = bn;
+    } else {
+      UFG_TRY(residual64(S, f, op, x64, rhs, S->r64, &rn));
+    }
+    if (!std::isfinite(rn)) {
+      out->done = 4;
+      return UFG_OK;
+    }
+    if (rn <= tol * bn || bn == 0.0) {
+      out->done = 1;
+      return UFG_OK;
+    }
+    if (out->iters >= p->maxit) {
+      out->done = 5;
+      return UFG_OK;
+    }
+    out->outer += 1;
+    cudaError_t e = launch_to_f32(S->r64, 1.0 / rn, (float*)V.rhs, n, S->st);
+    if (e != cudaSuccess) return cuda_fail(e, "to_f32");
+    // the inner solve asks at least what the outer target still needs
+    const double t_in = std::fmax(inner, 0.5 * tol * bn / rn);
+    KrylovResult kr;
+    UFG_TRY(krylov(1, t_in, false, &kr));
+    out->iters += kr.iters;
+    out->restarts += kr.restarts;
+    if (kr.done == 4) {
+      out->done = 4;
+      return UFG_OK;
+    }
+    e = launch_axpy_f32_to_f64(x64, (const float*)V.x, rn, n, S->st);
+    if (e != cudaSuccess) return cuda_fail(e, "axpy mixed");
+  }
+  return UFG_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct CallGuard {  // orders the solver stream after the caller's stream and back
+  ufg_solver* S;
+  cudaStream_t user;
+  CallGuard(ufg_solver* s, cudaStream_t u) : S(s), user(u) {
+    cudaEventRecord(S->ev, user);
+    cudaStreamWaitEvent(S->st, S->ev, 0);
+  }
+  ~CallGuard() {
+    cudaEventRecord(S->ev, S->st);
+    cudaStreamWaitEvent(user, S->ev, 0);
+  }
+};
+
+double paper_mv(const ufg_solver* S, int iters, bool bicg) {
+  if (bicg) {
+    if (S->pc_kind == UFG_PC_WCE) return iters * 2.0 * (S->pc.order + 1) * 3.0;
+    return iters * 2.0;
+  }
+  if (S->pc_kind == UFG_PC_CHEB) return iters * 2.0 * (S->pc.degree + 1);
+  if (S->pc_kind == UFG_PC_SCA) return iters * 3.0;
+  return iters * 2.0;
+}
+
+void fill_stats(ufg_stats* st, ufg_solver* S, const SolveOut& o, double rel, double secs,
+                bool bicg, ufg_status status) {
+  if (!st) return;
+  st->status = status;
+  st->iterations = o.iters;
+  st->outer_iterations = o.outer;
+  st->restarts = o.restarts;
+  st->n_M = S->counts.M;
+  st->n_Mdag = S->counts.Mdag;
+  st->n_M1 = S->counts.M1;
+  st->n_M1T = S->counts.M1T;
+  st->n_M0inv = S->counts.M0inv;
+  st->n_M0invT = S->counts.M0invT;
+  st->n_sca = S->counts.sca;
+  st->mv_paper = paper_mv(S, o.iters, bicg);
+  st->true_residual = rel;
+  st->seconds = secs;
+}
+
+ufg_status check_solve_args(ufg_solver* S, ufg_field* f, const void* b, const void* x,
+                            const ufg_params* p) {
+  if (!S || !f || !b || !x || !p) {
+    set_error("null argument");
+    return UFG_INVALID_ARG;
+  }
+  if (f->lat != S->lat && (f->lat->nx != S->lat->nx || f->lat->ntau != S->lat->ntau)) {
+    set_error("field and solver belong to different lattices");
+    return UFG_INVALID_ARG;
+  }
+  if (!(p->tol > 0) || p->maxit <= 0 ||
+      (p->precision != UFG_FP64 && p->precision != UFG_MIXED)) {
+    set_error("invalid params: need tol > 0, maxit > 0, precision UFG_FP64 or UFG_MIXED");
+    return UFG_INVALID_ARG;
+  }
+  return UFG_OK;
+}
+
+// Stages b (and x0) into FP64 device workspace; returns device pointers.
+ufg_status stage_in(ufg_solver* S, const double* b, double* x, bool x0, const double** bd,
+                    double** xd, bool* host_x) {
+  const size_t bytes = (size_t)S->lat->S * sizeof(double);
+  if (is_device_ptr(b)) {
+    *bd = b;
+  } else {
+    UFG_CUDA(cudaMemcpyAsync(S->b64, b, bytes, cudaMemcpyHostToDevice, S->st));
+    *bd = S->b64;
+  }
+  *host_x = !is_device_ptr(x);
+  *xd = S->x64;
+  if (x0) UFG_CUDA(cudaMemcpyAsync(S->x64, x, bytes, cudaMemcpyDefault, S->st));
+  return UFG_OK;
+}
+
+ufg_status stage_out(ufg_solver* S, double* x) {
+  const size_t bytes = (size_t)S->lat->S * sizeof(double);
+  UFG_CUDA(cudaMemcpyAsync(x, S->x64, bytes, cudaMemcpyDefault, S->st));
+  UFG_CUDA(cudaStreamSynchronize(S->st));
+  return UFG_OK;
+}
+
+ufg_status two_step(ufg_solver* S, ufg_field* f, const double* b, double* x, bool x0, double tol,
+                    const ufg_params* p, SolveOut* o1, SolveOut* o2) {
+  // step 1: M^T y = b to tol/2
+  double bn = 0.0, yn = 0.0;
+  UFG_TRY(norm64(S, b, S->lat->S, &bn));
+  if (bn == 0.0) {
+    UFG_CUDA(cudaMemsetAsync(x, 0, S->lat->S * sizeof(double), S->st));
+    o1->done = o2->done = 1;
+    return UFG_OK;
+  }
+  UFG_TRY(solve_system(S, f, OPK_MDAG, b, S->y64, false, 0.5 * tol, p, o1));
+  if (o1->done != 1) return UFG_OK;
+  UFG_TRY(norm64(S, S->y64, S->lat->S, &yn));
+  const double tol2 = tol * bn / (2.0 * (2.0 + S->lat->A) * yn);
+  UFG_TRY(solve_system(S, f, OPK_M, S->y64, x, x0, tol2, p, o2));
+  return UFG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ufg_status ufg_solver_create(const ufg_lattice* L, ufg_solver** out) {
+  clear_error();
+  if (!L || !out) {
+    set_error("null lattice or out");
+    return UFG_INVALID_ARG;
+  }
+  *out = nullptr;
+  ufg_solver* S = new ufg_solver();
+  S->lat = L;
+  S->pc.degree = 16;
+  S->pc.alpha = 2.0;
+  S->pc.order = 2;
+  const size_t n = (size_t)L->S;
+  ufg_status s = UFG_OK;
+  auto fail = [&](ufg_status st) {
+    ufg_solver_destroy(S);
+    return st;
+  };
+  if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming) != cudaSuccess) {
+    set_error("stream/event creation failed");
+    return fail(UFG_CUDA_ERROR);
+  }
+  for (int prec = 0; prec < 2; ++prec) {
+    VecSet& V = S->vs[prec];
+    void** all[] = {&V.r, &V.rhat, &V.p, &V.v, &V.s, &V.t, &V.y, &V.z, &V.q, &V.tmp, &V.u,
+                    &V.acc, &V.spec, &V.wr, &V.x, &V.rhs};
+    for (void** pp : all) {
+      if (prec == 0) s = dev_alloc((double**)pp, n);
+      else s = dev_alloc((float**)pp, n);
+      if (s != UFG_OK) return fail(s);
+    }
+  }
+  if ((s = dev_alloc(&S->x64, n)) || (s = dev_alloc(&S->b64, n)) || (s = dev_alloc(&S->r64, n)) ||
+      (s = dev_alloc(&S->y64, n)) || (s = dev_alloc(&S->rc64, n)) ||
+      (s = dev_alloc(&S->xs64, n)) || (s = dev_alloc(&S->xf64, n)) ||
+      (s = dev_alloc(&S->parts, (size_t)NSLOT * 2 * MAX_PARTIAL_CTAS)) ||
+      (s = dev_alloc(&S->sc, 1)) || (s = dev_alloc(&S->red_dev, 1)))
+    return fail(s);
+  if (cudaMallocHost(&S->sc_host, sizeof(DevScalars)) != cudaSuccess ||
+      cudaMallocHost(&S->red_host, sizeof(double)) != cudaSuccess) {
+    set_error("pinned host allocation failed");
+    return fail(UFG_OOM);
+  }
+  if (cudaMemset(S->parts, 0, (size_t)NSLOT * 2 * MAX_PARTIAL_CTAS * sizeof(double)) !=
+      cudaSuccess) {
+    set_error("memset failed");
+    return fail(UFG_CUDA_ERROR);
+  }
+  *out = S;
+  return UFG_OK;
+}
+
+void ufg_solver_destroy(ufg_solver* S) {
+  if (!S) return;
+  if (S->st) cudaStreamSynchronize(S->st);
+  for (auto& kv : S->graphs) cudaGraphExecDestroy(kv.second);
+  for (int prec = 0; prec < 2; ++prec) {
+    VecSet& V = S->vs[prec];
+    void** all[] = {&V.r, &V.rhat, &V.p, &V.v, &V.s, &V.t, &V.y, &V.z, &V.q, &V.tmp, &V.u,
+                    &V.acc, &V.spec, &V.wr, &V.x, &V.rhs};
+    for (void** pp : all)
+      if (*pp) cudaFree(*pp);
+  }
+  dev_free(S->x64);
+  dev_free(S->b64);
+  dev_free(S->r64);
+  dev_free(S->y64);
+  dev_free(S->rc64);
+  dev_free(S->xs64);
+  dev_free(S->xf64);
+  dev_free(S->parts);
+  dev_free(S->sc);
+  dev_free(S->red_dev);
+  if (S->sc_host) cudaFreeHost(S->sc_host);
+  if (S->red_host) cudaFreeHost(S->red_host);
+  if (S->ev) cudaEventDestroy(S->ev);
+  if (S->st) cudaStreamDestroy(S->st);
+  delete S;
+}
+
+ufg_status ufg_set_preconditioner(ufg_solver* S, int kind, const ufg_pc_params* p) {
+  clear_error();
+  if (!S) {
+    set_error("null solver");
+    return UFG_INVALID_ARG;
+  }
+  if (kind == UFG_PC_NONE) {
+    S->pc_kind = kind;
+    return UFG_OK;
+  }
+  if (!p) {
+    set_error("null preconditioner parameters");
+    return UFG_INVALID_ARG;
+  }
+  if (kind == UFG_PC_CHEB && (p->degree < 2 || p->degree > 64 || p->degree % 2 ||
+                              p->eps >= 1.0 || !(std::isfinite(p->scale)))) {
+    set_error("Chebyshev: need an even degree in 2..64 and eps < 1");
+    return UFG_INVALID_ARG;
+  }
+  if (kind == UFG_PC_SCA && !(p->alpha > 0)) {
+    set_error("SCA: alpha must be > 0");
+    return UFG_INVALID_ARG;
+  }
+  if (kind == UFG_PC_WCE && (p->order < 0 || p->order > 16)) {
+    set_error("WCE: order must be in 0..16");
+    return UFG_INVALID_ARG;
+  }
+  if (kind < UFG_PC_NONE || kind > UFG_PC_WCE) {
+    set_error("unknown preconditioner kind %d", kind);
+    return UFG_INVALID_ARG;
+  }
+  S->pc_kind = kind;
+  S->pc = *p;
+  return UFG_OK;
+}
+
+ufg_status ufg_apply_preconditioner(ufg_solver* S, ufg_field* f, const void* r, void* z,
+                                    int transpose, int precision, void* stream) {
+  clear_error();
+  if (!S || !f || !r || !z || (precision != UFG_FP64 && precision != UFG_FP32) ||
+      S->pc_kind == UFG_PC_NONE) {
+    set_error("apply_preconditioner: null argument, bad precision or no preconditioner set");
+    return UFG_INVALID_ARG;
+  }
+  CallGuard g(S, as_stream(stream));
+  UFG_TRY(write_scalars(S, 0.0, 0));
+  UFG_TRY(pc_prepare(S, f));
+  return pc_apply(S, f, precision, r, z, transpose != 0);
+}
+
+ufg_status ufg_solve_cg_normal(ufg_solver* S, ufg_field* f, const double* b, double* x,
+                               const ufg_params* p, ufg_stats* stats, void* stream) {
+  clear_error();
+  UFG_TRY(check_solve_args(S, f, b, x, p));
+  if (S->pc_kind == UFG_PC_WCE) {
+    set_error("CG on the normal equations takes the Chebyshev or SCA preconditioner");
+    return UFG_INVALID_ARG;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  CallGuard g(S, as_stream(stream));
+  S->counts = Counts();
+  const double* bd = nullptr;
+  double* xd = nullptr;
+  bool host_x = false;
+  UFG_TRY(stage_in(S, b, x, p->x0_given != 0, &bd, &xd, &host_x));
+  UFG_TRY(pc_prepare(S, f));
+  SolveOut o;
+  UFG_TRY(solve_system(S, f, OPK_Q, bd, xd, p->x0_given != 0, p->tol, p, &o));
+  double bn = 0, rn = 0;
+  UFG_TRY(norm64(S, bd, S->lat->S, &bn));
+  UFG_TRY(residual64(S, f, OPK_Q, xd, bd, S->r64, &rn));
+  const double rel = bn > 0 ? rn / bn : 0.0;
+  UFG_TRY(stage_out(S, x));
+  ufg_status st = status_of(o.done);
+  if (st == UFG_OK && rel > p->tol) {
+    set_error("recursive residual converged but the true residual %.3e exceeds tol", rel);
+    st = UFG_NOT_CONVERGED;
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  fill_stats(stats, S, o, rel, secs, false, st);
+  if (stats) stats->iterations_step[0] = o.iters, stats->iterations_step[1] = 0;
+  return st;
+}
+
+ufg_status ufg_solve_bicgstab_two_step(ufg_solver* S, ufg_field* f, const double* b, double* x,
+                                       const ufg_params* p, ufg_stats* stats, void* stream) {
+  clear_error();
+  UFG_TRY(check_solve_args(S, f, b, x, p));
+  if (S->pc_kind == UFG_PC_CHEB || S->pc_kind == UFG_PC_SCA) {
+    set_error("two-step BiCGStab takes the weak-coupling preconditioner (or none)");
+    return UFG_INVALID_ARG;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  CallGuard g(S, as_stream(stream));
+  S->counts = Counts();
+  const double* bd = nullptr;
+  double* xd = nullptr;
+  bool host_x = false;
+  UFG_TRY(stage_in(S, b, x, p->x0_given != 0, &bd, &xd, &host_x));
+  UFG_TRY(pc_prepare(S, f));
+  SolveOut o1, o2;
+  UFG_TRY(two_step(S, f, bd, xd, p->x0_given != 0, p->tol, p, &o1, &o2));
+  double bn = 0, rn = 0;
+  UFG_TRY(norm64(S, bd, S->lat->S, &bn));
+  UFG_TRY(residual64(S, f, OPK_Q, xd, bd, S->r64, &rn));
+  double rel = bn > 0 ? rn / bn : 0.0;
+  int extra = 0;
+  if (o1.done == 1 && o2.done == 1 && rel > p->tol) {
+    // one defect-correction round on the composite residual: x += two_step(b - Q x)
+    ++extra;
+    const size_t bytes = (size_t)S->lat->S * sizeof(double);
+    UFG_CUDA(cudaMemcpyAsync(S->rc64, S->r64, bytes, cudaMemcpyDeviceToDevice, S->st));
+    UFG_CUDA(cudaMemcpyAsync(S->xs64, xd, bytes, cudaMemcpyDeviceToDevice, S->st));
+    SolveOut c1, c2;
+    UFG_TRY(two_step(S, f, S->rc64, xd, false, p->tol * bn / rn, p, &c1, &c2));
+    cudaError_t e = launch_vec(0, V_ADD, S->lat->S, nullptr, xd, S->xs64, nullptr, nullptr,
+                               nullptr, nullptr, nullptr, nullptr, S->st);
+    if (e != cudaSuccess) return cuda_fail(e, "vector kernel");
+    o1.iters += c1.iters;
+    o2.iters += c2.iters;
+    o1.restarts += c1.restarts;
+    o2.restarts += c2.restarts;
+    o1.outer += c1.outer;
+    o2.outer += c2.outer;
+    if (c1.done != 1) o1.done = c1.done;
+    if (c2.done != 1) o2.done = c2.done;
+    UFG_TRY(residual64(S, f, OPK_Q, xd, bd, S->r64, &rn));
+    rel = rn / bn;
+  }
+  UFG_TRY(stage_out(S, x));
+  SolveOut o;
+  o.iters = o1.iters + o2.iters;
+  o.outer = o1.outer + o2.outer;
+  o.restarts = o1.restarts + o2.restarts;
+  o.done = (o1.done == 1 && o2.done == 1) ? 1 : (o1.done != 1 ? o1.done : o2.done);
+  ufg_status st = status_of(o.done);
+  if (st == UFG_OK && rel > p->tol) {
+    set_error("two-step solve: composite residual %.3e exceeds tol after %d correction(s)", rel,
+              extra);
+    st = UFG_NOT_CONVERGED;
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  fill_stats(stats, S, o, rel, secs, true, st);
+  if (stats) {
+    stats->iterations_step[0] = o1.iters;
+    stats->iterations_step[1] = o2.iters;
+  }
+  return st;
+}
+
+ufg_status ufg_force_from_solution(ufg_solver* S, ufg_field* f, const double* X, double* dS,
+                                   double scale, void* stream) {
+  clear_error();
+  if (!S || !f || !X || !dS) {
+    set_error("null argument");
+    return UFG_INVALID_ARG;
+  }
+  CallGuard g(S, as_stream(stream));
+  UFG_TRY(write_scalars(S, 0.0, 0));
+  const ufg_lattice* L = f->lat;
+  double* Y = (double*)S->vs[0].tmp;
+  SliceCall c = base_call(L, FAM_KIN, 0);  // Y = M X
+  c.in = X;
+  c.pre = f->w64;
+  c.id = X;
+  c.shift = -1;
+  c.out = Y;
+  cudaError_t e = slice_dispatch(L->nx, c, S->st);
+  if (e != cudaSuccess) return cuda_fail(e, "slice kernel (Y = M X)");
+  // dS/dsigma_t = 2 A cos sigma_t X_t [exp(-tau K) Y~_{t+1}], Y~_{N_tau} = -Y_0:
+  // base = sgn * K(Y_{t_in}) * c_t * X_t with sgn = -1 except at the wrap, out = -2 * scale * base
+  SliceCall fc = base_call(L, FAM_KIN, 0);
+  fc.in = Y;
+  fc.post = f->c64;
+  fc.post2 = X;
+  fc.shift = +1;
+  fc.a = -2.0 * scale;
+  fc.out = dS;
+  e = slice_dispatch(L->nx, fc, S->st);
+  if (e != cudaSuccess) return cuda_fail(e, "slice kernel (force)");
+  return UFG_OK;
+}
+
+ufg_status ufg_hmc_force(ufg_solver* S, ufg_field* f, const double* phi, double* dS,
+                         double* X_out, double* S_out, const ufg_params* p, ufg_stats* stats,
+                         void* stream) {
+  clear_error();
+  if (!S || !f || !phi || !p) {
+    set_error("null argument");
+    return UFG_INVALID_ARG;
+  }
+  double* X = X_out ? X_out : S->xf64;
+  ufg_status st = ufg_solve_bicgstab_two_step(S, f, phi, X, p, stats, stream);
+  if (st != UFG_OK && st != UFG_NOT_CONVERGED) return st;
+  if (S_out) {
+    CallGuard g(S, as_stream(stream));
+    int np = 0;
+    cudaError_t e = launch_vec(0, V_DOT, S->lat->S, nullptr, (void*)phi, (void*)X, nullptr,
+                               nullptr, nullptr, nullptr, slot(S, P_RES), &np, S->st);
+    if (e != cudaSuccess) return cuda_fail(e, "dot");
+    e = launch_reduce_to(slot(S, P_RES), np, 0, S->red_dev, S->st);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce");
+    UFG_CUDA(cudaMemcpyAsync(S->red_host, S->red_dev, sizeof(double), cudaMemcpyDeviceToHost,
+                             S->st));
+    UFG_CUDA(cudaStreamSynchronize(S->st));
+    *S_out = *S->red_host;
+  }
+  if (dS) UFG_TRY(ufg_force_from_solution(S, f, X, dS, 1.0, stream));
+  return st;
+}
+
+}  // extern "C"

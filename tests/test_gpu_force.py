@@ -1,0 +1,93 @@
+"""HMC force dS/dsigma of S = phi^T (M^T M)^{-1} phi on the GPU: kernel parity with the oracle's
+force formula for the same X (1e-12), agreement with central finite differences of S computed by
+GPU solves (relative 1e-6), the heat-bath identity S = |eta|^2, and the autograd wrapper."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1008_3647_gb300.inputs import field_and_source, sample_sites
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ufg():
+    from paper_1008_3647_gb300 import ufg as u
+    u.load()
+    return u
+
+
+@pytest.mark.parametrize("nx,ntau", [(4, 8), (8, 32), (32, 6)])
+def test_force_kernel_parity(ufg, nx, ntau):
+    sigma, X = field_and_source(nx, ntau, 31)
+    lat = ufg.Lattice(nx, ntau)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    solver = ufg.Solver(lat)
+    dS = solver.ufg_force_from_solution(field, torch.from_numpy(X).cuda()).cpu().numpy()
+    ref = O.force_dS_dsigma(O.Lattice(nx, ntau), sigma, X)
+    assert float(np.abs(dS - ref).max() / np.abs(ref).max()) < 1e-12
+
+
+def _action(ufg, lat, solver, sigma, phi):
+    field = ufg.Field(lat, sigma)
+    S, X, st = solver.ufg_pseudofermion_action(field, phi, tol=1e-13)
+    assert st["status"] == ufg.UFG_OK, st
+    return S, X
+
+
+@pytest.mark.parametrize("nx,ntau,nsites", [(8, 32, 12)])
+def test_force_matches_central_differences(ufg, nx, ntau, nsites):
+    sigma, eta = field_and_source(nx, ntau, 41)
+    lat = ufg.Lattice(nx, ntau)
+    solver = ufg.Solver(lat)
+    solver.ufg_set_preconditioner("wce", order=2)
+    sig = torch.from_numpy(sigma).cuda()
+    field = ufg.Field(lat, sig)
+    phi = ufg.ufg_apply_Mdag(field, torch.from_numpy(eta).cuda())
+    dS, X, S0, st = solver.ufg_hmc_force(field, phi, tol=1e-13)
+    assert st["status"] == ufg.UFG_OK
+    assert S0 == pytest.approx(float(np.sum(eta * eta)), rel=1e-9)  # phi = M^T eta => S = |eta|^2
+    h = 1e-4
+    dS = dS.cpu().numpy().ravel()
+    for i in sample_sites(lat.shape, nsites, 5):
+        sp = sig.clone().view(-1)
+        sp[i] += h
+        sm = sig.clone().view(-1)
+        sm[i] -= h
+        Sp, _ = _action(ufg, lat, solver, sp.view(lat.shape), phi)
+        Sm, _ = _action(ufg, lat, solver, sm.view(lat.shape), phi)
+        fd = (Sp - Sm) / (2 * h)
+        assert dS[i] == pytest.approx(fd, rel=1e-6, abs=1e-8 * abs(S0))
+
+
+def test_force_matches_oracle_gradient_8cubed(ufg):
+    # GPU solve + GPU force against the oracle's solve + oracle force on an 8^3 lattice
+    nx, ntau = 8, 16
+    sigma, eta = field_and_source(nx, ntau, 43)
+    olat = O.Lattice(nx, ntau)
+    phi = O.apply_Mdag(olat, sigma, eta)
+    Xo, _ = O.solve_cg_normal(olat, sigma, phi, tol=1e-13)
+    ref = O.force_dS_dsigma(olat, sigma, Xo)
+    lat = ufg.Lattice(nx, ntau)
+    solver = ufg.Solver(lat)
+    solver.ufg_set_preconditioner("wce", order=2)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    dS, X, S, st = solver.ufg_hmc_force(field, torch.from_numpy(phi).cuda(), tol=1e-12)
+    assert float(np.abs(dS.cpu().numpy() - ref).max() / np.abs(ref).max()) < 1e-8
+
+
+def test_autograd_backward_is_force(ufg):
+    nx, ntau = 6, 10
+    sigma, eta = field_and_source(nx, ntau, 44)
+    lat = ufg.Lattice(nx, ntau)
+    solver = ufg.Solver(lat)
+    solver.ufg_set_preconditioner("wce", order=1)
+    sig = torch.from_numpy(sigma).cuda().requires_grad_(True)
+    field = ufg.Field(lat, sig.detach())
+    phi = ufg.ufg_apply_Mdag(field, torch.from_numpy(eta).cuda())
+    S = ufg.PseudofermionAction.apply(sig, phi, solver, {"tol": 1e-12})
+    S.backward()
+    dS, _, S2, _ = solver.ufg_hmc_force(field, phi, tol=1e-12)
+    assert float(S) == pytest.approx(S2, rel=1e-10)
+    assert torch.allclose(sig.grad, dS, rtol=1e-8, atol=1e-10 * float(dS.abs().max()))

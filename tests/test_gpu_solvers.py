@@ -1,0 +1,175 @@
+"""GPU solvers through the C ABI: every solve reaches ||b - M^T M x|| / ||b|| <= 1e-10 recomputed
+by the FP64 oracle, and FP64 iteration counts agree with the oracle's (stored by
+tests/golden/make_oracle_counts.py) to within 2 % or 2 iterations."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1008_3647_gb300.inputs import field_and_source
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_counts_8x64.json")
+
+
+@pytest.fixture(scope="module")
+def ufg():
+    from paper_1008_3647_gb300 import ufg as u
+    u.load()
+    return u
+
+
+def _true_rel(olat, sigma, b, x):
+    r = b - O.apply_Q(olat, sigma, x)
+    return float(np.linalg.norm(r) / np.linalg.norm(b))
+
+
+def _counts_close(a, b):
+    return abs(a - b) <= max(2, 0.02 * b)
+
+
+def test_plain_fp64_cg_4x16(ufg):
+    nx, ntau = 4, 16
+    sigma, b = field_and_source(nx, ntau, 0)
+    lat = ufg.Lattice(nx, ntau)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    solver = ufg.Solver(lat)
+    x, st = solver.ufg_solve_cg_normal(field, torch.from_numpy(b).cuda(), tol=1e-10)
+    olat = O.Lattice(nx, ntau)
+    assert st["status"] == ufg.UFG_OK, st
+    assert _true_rel(olat, sigma, b, x.cpu().numpy()) <= 1e-10
+    _, info = O.solve_cg_normal(olat, sigma, b, 1e-10)
+    assert _counts_close(st["iterations"], info["iterations"]), (st["iterations"], info)
+    assert st["n_M"] >= st["iterations"] and st["mv_paper"] == 2 * st["iterations"]
+
+
+METHODS = {
+    "cg_none": ("cg", "none", {}),
+    "cg_cheb8": ("cg", "cheb", {"degree": 8}),
+    "cg_cheb16": ("cg", "cheb", {"degree": 16}),
+    "cg_cheb32": ("cg", "cheb", {"degree": 32}),
+    "cg_sca2": ("cg", "sca", {"alpha": 2.0}),
+    "bicg_none": ("bicg", "none", {}),
+    "bicg_wce0": ("bicg", "wce", {"order": 0}),
+    "bicg_wce1": ("bicg", "wce", {"order": 1}),
+    "bicg_wce2": ("bicg", "wce", {"order": 2}),
+    "bicg_wce4": ("bicg", "wce", {"order": 4}),
+    "bicg_wce2_euler": ("bicg", "wce", {"order": 2, "euler": True}),
+    "bicg_wce4_euler": ("bicg", "wce", {"order": 4, "euler": True}),
+}
+
+
+@pytest.mark.parametrize("method", list(METHODS))
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_8x64_fp64_matches_oracle(ufg, method, seed):
+    gold = json.load(open(GOLD))
+    ref = gold["runs"]["%s/%d" % (method, seed)]
+    nx, ntau = gold["nx"], gold["ntau"]
+    sigma, b = field_and_source(nx, ntau, seed)
+    lat = ufg.Lattice(nx, ntau)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    solver = ufg.Solver(lat)
+    kind, pc, kw = METHODS[method]
+    solver.ufg_set_preconditioner(pc, **kw)
+    fn = solver.ufg_solve_cg_normal if kind == "cg" else solver.ufg_solve_bicgstab_two_step
+    x, st = fn(field, torch.from_numpy(b).cuda(), tol=1e-10)
+    assert st["status"] == ufg.UFG_OK, st
+    rel = _true_rel(O.Lattice(nx, ntau), sigma, b, x.cpu().numpy())
+    assert rel <= 1e-10
+    assert _counts_close(st["iterations"], ref["iterations"]), (st["iterations"], ref)
+
+
+@pytest.mark.parametrize("kind,pc,kw", [("cg", "cheb", {"degree": 16}), ("bicg", "wce", {"order": 2})])
+def test_mixed_precision_16x256(ufg, kind, pc, kw):
+    nx, ntau = 16, 256
+    sigma, b = field_and_source(nx, ntau, 0)
+    lat = ufg.Lattice(nx, ntau)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    solver = ufg.Solver(lat)
+    solver.ufg_set_preconditioner(pc, **kw)
+    fn = solver.ufg_solve_cg_normal if kind == "cg" else solver.ufg_solve_bicgstab_two_step
+    bd = torch.from_numpy(b).cuda()
+    x, st = fn(field, bd, tol=1e-10, precision=ufg.UFG_MIXED, inner_tol=1e-5)
+    assert st["status"] == ufg.UFG_OK, st
+    assert st["outer_iterations"] >= 1
+    assert _true_rel(O.Lattice(nx, ntau), sigma, b, x.cpu().numpy()) <= 1e-10
+    x64, st64 = fn(field, bd, tol=1e-10)
+    assert st64["status"] == ufg.UFG_OK
+    err = float((x - x64).norm() / x64.norm())
+    assert err < 1e-6  # both solutions within the 1e-10 residual ball of the same system
+
+
+def test_host_buffers_match_device_buffers(ufg):
+    nx, ntau = 8, 16
+    sigma, b = field_and_source(nx, ntau, 9)
+    lat = ufg.Lattice(nx, ntau)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    solver = ufg.Solver(lat)
+    solver.ufg_set_preconditioner("wce", order=2)
+    xd, st = solver.ufg_solve_bicgstab_two_step(field, torch.from_numpy(b).cuda(), tol=1e-10)
+    bh = torch.from_numpy(b.copy())
+    xh = torch.zeros_like(bh)
+    xh, sth = solver.ufg_solve_bicgstab_two_step(field, bh, xh, tol=1e-10)
+    assert sth["status"] == ufg.UFG_OK
+    assert torch.equal(xh, xd.cpu())  # same kernels, same order: bit-identical
+
+
+def test_initial_guess_is_used(ufg):
+    nx, ntau = 6, 12
+    sigma, b = field_and_source(nx, ntau, 2)
+    lat = ufg.Lattice(nx, ntau)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    solver = ufg.Solver(lat)
+    bd = torch.from_numpy(b).cuda()
+    x, st = solver.ufg_solve_cg_normal(field, bd, tol=1e-10)
+    x2, st2 = solver.ufg_solve_cg_normal(field, bd, x.clone(), tol=1e-10, x0_given=True)
+    assert st2["status"] == ufg.UFG_OK and st2["iterations"] <= 1
+
+
+def test_maxit_reports_not_converged(ufg):
+    nx, ntau = 8, 32
+    sigma, b = field_and_source(nx, ntau, 1)
+    lat = ufg.Lattice(nx, ntau)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    solver = ufg.Solver(lat)
+    x, st = solver.ufg_solve_cg_normal(field, torch.from_numpy(b).cuda(), tol=1e-10, maxit=5)
+    assert st["status"] == ufg.UFG_NOT_CONVERGED
+    assert st["iterations"] == 5
+
+
+def test_nonfinite_rhs_reports_nonfinite(ufg):
+    nx, ntau = 4, 8
+    sigma, b = field_and_source(nx, ntau, 1)
+    b[2, 1, 1, 1] = np.nan  # the failure is made on the host
+    lat = ufg.Lattice(nx, ntau)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    solver = ufg.Solver(lat)
+    for fn in (solver.ufg_solve_cg_normal, solver.ufg_solve_bicgstab_two_step):
+        x, st = fn(field, torch.from_numpy(b).cuda(), tol=1e-10)
+        assert st["status"] == ufg.UFG_NONFINITE
+
+
+def test_zero_rhs_gives_zero(ufg):
+    lat = ufg.Lattice(4, 8)
+    sigma, _ = field_and_source(4, 8, 0)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    solver = ufg.Solver(lat)
+    b = torch.zeros(lat.shape, dtype=torch.float64, device="cuda")
+    for fn in (solver.ufg_solve_cg_normal, solver.ufg_solve_bicgstab_two_step):
+        x, st = fn(field, b, tol=1e-10)
+        assert st["status"] == ufg.UFG_OK and float(x.abs().max()) == 0.0
+
+
+def test_wrong_preconditioner_for_solver_rejected(ufg):
+    lat = ufg.Lattice(4, 8)
+    sigma, b = field_and_source(4, 8, 0)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    solver = ufg.Solver(lat)
+    solver.ufg_set_preconditioner("wce", order=1)
+    with pytest.raises(ufg.UfgError):
+        solver.ufg_solve_cg_normal(field, torch.from_numpy(b).cuda())
+    with pytest.raises(ufg.UfgError):
+        solver.ufg_set_preconditioner("cheb", degree=7)
