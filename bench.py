@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the unitary-Fermi-gas solver library on one node.
+
+Headline (one JSON line on rank 0): solves/s to a true relative residual ||b - M^T M x||/||b|| <=
+1e-10 on the 16^3 x 256 lattice (1.05M sites), tau = 0.05, g = 5, sigma ~ U[-pi, pi], b ~ N(0,1),
+solved by the paper's method of choice -- two-step BiCGStab (M^T y = b, M x = y) with the
+order-2 weak-coupling preconditioner -- in mixed precision (FP32 inner solves, FP64 defect
+correction).  One step = 8 independent problems per rank (field set-up + solve each), inputs
+resident in HBM; the same step in plain FP64 is reported beside it ("fp64").  The roofline
+object reports the fused M apply (FP32) on the 32^3 x 512 lattice, the HBM-bound form of the
+slice kernel that dominates every step, timed live with CUDA events on its stream.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ufg|reference]
+Under torchrun each rank solves its own 8 problems (weak scaling, no collective on the data
+path); the reference arm (--impl reference) times the FP64 CPU oracle on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/s to 1e-10 residual (mixed vs FP64 GPU); M apply GB/s vs HBM peak"
+NX, NTAU, PER_RANK, TOL = 16, 256, 8, 1e-10
+WORKLOAD = ("16^3x256 lattice (tau=0.05, g=5), 8 seeded problems per rank, two-step BiCGStab "
+            "+ WCE order 2, mixed FP32-inner/FP64-outer, tol 1e-10")
+ORACLE_COUNTS = os.path.join(ROOT, "tests", "golden", "oracle_counts_16x256.json")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        except Exception:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle on the host cores: each step times a bounded sample (one iteration of
+    the oracle's BiCGStab + WCE2 on the first system M^T y = b of a 16^3 x 256 problem) and scales
+    it to 8 full solves with the oracle's own iteration count for that problem."""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1008_3647_gb300.inputs import field_and_source
+    line = {"metric": METRIC, "unit": "solves/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "ntau": NTAU, "solves_per_step": PER_RANK}}
+    lat = O.Lattice(NX, NTAU, 0.05, 5.0)
+    sigma, b = field_and_source(NX, NTAU, 0)
+    iters, src = oracle_iterations()
+    pc = lambda r: O.wce_apply_T(lat, sigma, r, 2)  # noqa: E731
+    aop = lambda u: O.apply_Mdag(lat, sigma, u)  # noqa: E731
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.bicgstab(aop, b, 1e-30, 1, pc)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    t_iter = statistics.mean(times)
+    sps = 1.0 / (t_iter * iters)
+    line.update({"value": sps, "ms_per_step": 1e3 * t_iter * iters * PER_RANK,
+                 "cpu_baseline": {"value": sps, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                  "sample": "1 BiCGStab+WCE2 iteration of the FP64 oracle per step "
+                                            "on the 16^3x256 seed-0 problem, scaled by %d "
+                                            "iterations per solve (%s)" % (iters, src)},
+                 "e2e": {"value": sps, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                         "d2h_bytes_per_step": 0}})
+    print(json.dumps(line), flush=True)
+
+
+def oracle_iterations():
+    try:
+        with open(ORACLE_COUNTS) as f:
+            return int(json.load(f)["runs"]["bicg_wce2"]["iterations"]), "oracle count, stored"
+    except Exception:
+        return 80, "assumed 80 iterations (oracle count file missing)"
+
+
+def cpu_baseline_sample():
+    """Bounded oracle sample for the ufg arm's cpu_baseline (same definition as the reference)."""
+    import oracle as O
+    from paper_1008_3647_gb300.inputs import field_and_source
+    lat = O.Lattice(NX, NTAU, 0.05, 5.0)
+    sigma, b = field_and_source(NX, NTAU, 0)
+    iters, src = oracle_iterations()
+    t0 = time.perf_counter()
+    O.bicgstab(lambda u: O.apply_Mdag(lat, sigma, u), b, 1e-30, 2,
+               lambda r: O.wce_apply_T(lat, sigma, r, 2))
+    t_iter = (time.perf_counter() - t0) / 2
+    return {"value": 1.0 / (t_iter * iters), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": "2 BiCGStab+WCE2 iterations of the FP64 oracle on the 16^3x256 seed-0 problem, "
+                      "scaled by %d iterations per solve (%s); numpy FFT, one thread" % (iters, src)}
+
+
+def seeds_for_rank(rank, per_rank=PER_RANK):
+    """Each rank owns its own seeded problems: no data exchange between ranks."""
+    return [rank * per_rank + i for i in range(per_rank)]
+
+
+def max_over_ranks(t, world, device=None):
+    """Max of a per-rank time over all ranks (the slowest rank defines the job time)."""
+    import torch
+    v = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return float(v.item())
+
+
+def run_ufg(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1008_3647_gb300 import build as B
+    if not os.path.exists(B.LIB):
+        B.build()
+    from paper_1008_3647_gb300 import ufg
+    from paper_1008_3647_gb300.inputs import field_and_source
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    lat = ufg.Lattice(NX, NTAU, 0.05, 5.0)
+    solver = ufg.Solver(lat)
+    solver.ufg_set_preconditioner("wce", order=2)
+    seeds = seeds_for_rank(rank)
+    sig_h, b_h = [], []
+    for s in seeds:
+        sg, bb = field_and_source(NX, NTAU, s)
+        sig_h.append(torch.from_numpy(sg).pin_memory())
+        b_h.append(torch.from_numpy(bb).pin_memory())
+    sig_d = [t.to(dev) for t in sig_h]
+    b_d = [t.to(dev) for t in b_h]
+    x_d = [torch.zeros_like(t) for t in b_d]
+    x_h = [torch.zeros_like(t).pin_memory() for t in b_h]
+    field = ufg.Field(lat, sig_d[0])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(precision, host=False, pc=("wce", {"order": 2}), kind="bicg"):
+        stats = []
+        for i in range(PER_RANK):
+            field.update(sig_h[i] if host else sig_d[i])
+            fn = solver.ufg_solve_bicgstab_two_step if kind == "bicg" else solver.ufg_solve_cg_normal
+            b = b_h[i] if host else b_d[i]
+            x = x_h[i] if host else x_d[i]
+            _, st = fn(field, b, x, tol=TOL, precision=precision, inner_tol=1e-5, check_every=8)
+            if st["status"] != ufg.UFG_OK:
+                raise RuntimeError("solve failed: %s" % st)
+            stats.append(st)
+        return stats
+
+    def timed(nsteps, fn):
+        total = 0.0
+        for _ in range(nsteps):
+            flush.fill_(1.0)  # evict L2 between steps (outside the timed window)
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1) / 1e3
+        return max_over_ranks(total, world, dev)
+
+    # warm-up (also captures the CUDA graphs of every solve configuration used below)
+    for _ in range(args.warmup):
+        step(ufg.UFG_MIXED)
+    step(ufg.UFG_FP64)
+    step(ufg.UFG_MIXED, host=True)
+
+    launches0 = ufg.ufg_kernel_launches()
+    stats_box = {}
+    with ClockSampler(local_rank) as clk:
+        t_mixed = timed(args.steps, lambda: stats_box.__setitem__("mixed", step(ufg.UFG_MIXED)))
+    launches = ufg.ufg_kernel_launches() - launches0
+    clocks = clk.summary()
+    t_e2e = timed(args.steps, lambda: step(ufg.UFG_MIXED, host=True))
+    n64 = max(1, min(args.steps, 2))
+    t_fp64 = timed(n64, lambda: stats_box.__setitem__("fp64", step(ufg.UFG_FP64)))
+
+    solves = PER_RANK * world
+    value = solves * args.steps / t_mixed
+    e2e = solves * args.steps / t_e2e
+    fp64 = solves * n64 / t_fp64
+
+    # roofline of the dominant kernel: fused M apply (slice kernel, KIN family) at 32^3 x 512
+    hbm, peak_src = peaks()
+    roof = apply_roofline(ufg, torch, dev, stream, hbm, peak_src)
+    if rank != 0:
+        return
+    sm = stats_box["mixed"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_mixed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": NX, "ntau": NTAU, "solves_per_step": PER_RANK * world,
+                   "precision": "mixed (FP32 inner, FP64 outer)", "tol": TOL,
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
+        "roofline": roof["fp32"],
+        "e2e": {"value": e2e, "unit": "solves/s",
+                "h2d_bytes_per_step": PER_RANK * 2 * lat.ntau * lat.nx ** 3 * 8,
+                "d2h_bytes_per_step": PER_RANK * lat.ntau * lat.nx ** 3 * 8},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "fp64": {"value": fp64, "unit": "solves/s", "mixed_speedup": value / fp64,
+                 "iterations_mean": statistics.mean(s["iterations"] for s in stats_box["fp64"]),
+                 "true_residual_max": max(s["true_residual"] for s in stats_box["fp64"])},
+        "mixed": {"iterations_mean": statistics.mean(s["iterations"] for s in sm),
+                  "outer_mean": statistics.mean(s["outer_iterations"] for s in sm),
+                  "true_residual_max": max(s["true_residual"] for s in sm),
+                  "mv_paper_mean": statistics.mean(s["mv_paper"] for s in sm)},
+        "apply_fp64_32x512": roof["fp64"],
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    print(json.dumps(line), flush=True)
+
+
+def apply_roofline(ufg, torch, dev, stream, hbm, peak_src):
+    """Times the fused M apply on 32^3 x 512 (16.8M sites; x, w and y exceed L2 together) with
+    CUDA events on the launching stream; algorithmic bytes = read x + read w + write y."""
+    from paper_1008_3647_gb300.inputs import field_and_source
+    nx, nt = 32, 512
+    lat = ufg.Lattice(nx, nt)
+    sg, xx = field_and_source(nx, nt, 123)
+    field = ufg.Field(lat, torch.from_numpy(sg).to(dev))
+    out = {}
+    for name, dt, reps in (("fp32", torch.float32, 20), ("fp64", torch.float64, 5)):
+        x = torch.from_numpy(xx).to(dev, dt)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            ufg.ufg_apply_M(field, x, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ufg.ufg_apply_M(field, x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        bytes_ = 3 * x.element_size() * x.numel()
+        ach = bytes_ / t / 1e9
+        out[name] = {"kernel": "slice_kernel KIN family (fused M apply), %s, 32^3x512" % name,
+                     "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                     "frac": ach / hbm, "traffic": None, "peak_source": peak_src,
+                     "us_per_launch": t * 1e6, "algorithmic_bytes": bytes_}
+    # FP64 is bound by the FP64 pipe on this part: flops of the even/odd line operators
+    H = nx // 2
+    flops_site = 3 * 2 * ((H + 1) ** 2 + (H - 1) ** 2 + 2 * (H - 1)) / nx + 3
+    f64 = out["fp64"]
+    f64["flops_per_site"] = flops_site
+    f64["achieved_tflops"] = flops_site * lat.ntau * nx ** 3 / (f64["us_per_launch"] * 1e-6) / 1e12
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ufg", choices=["ufg", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-apply", action="store_true",
+                    help="time only the 32^3x512 M apply (the case ncu profiles)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if args.only_apply:
+        import torch
+        from paper_1008_3647_gb300 import ufg
+        torch.cuda.set_device(local_rank)
+        hbm, src = peaks()
+        out = apply_roofline(ufg, torch, torch.device("cuda", local_rank),
+                             torch.cuda.current_stream(), hbm, src)
+        print(json.dumps(out), flush=True)
+        return
+    try:
+        run_ufg(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

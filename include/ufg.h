@@ -119,6 +119,9 @@ const char* ufg_last_error(void);
 /* Build version / supported lattice extents (comma-separated N_x list). */
 const char* ufg_version(void);
 const char* ufg_supported_nx(void);
+/* Number of this library's kernels launched so far in the process (graph replays count their
+ * captured kernels); for benchmarks and launch-overhead accounting. */
+long long ufg_kernel_launches(void);
 
 /* Lattice N_x^3 x N_tau with time step tau and coupling g (Sec. 1; the paper uses tau = 0.05,
  * g in {2.5, 5, 7.5}).  dispersion 0: E(k) = k^2/2 (the paper's choice, hbar = m = 1);

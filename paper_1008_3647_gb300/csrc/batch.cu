@@ -1,0 +1,715 @@
+// Batched two-step BiCGStab for many independent problems of uneven lattice size.
+//
+// All problems' vectors live in packed arenas (problem p at element offset off_p).  Every phase
+// of the iteration is one launch for the whole batch per lattice-extent group (slice kernels and
+// the M0^{-1} recurrence are specialised by N_x) or one launch for the whole batch (vector and
+// scalar kernels), driven by device tile tables: a slice tile is (problem, first time slice), a
+// vector tile (problem, start, length), a recurrence tile (problem, 32-mode block).  Per-problem
+// scalars and `done` flags let converged problems drop out while the rest continue; the
+// iteration body is captured once in a CUDA graph and replayed between host checks.  Tiles are
+// ordered largest problem first so that the tail of every launch is made of small problems.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "blas.cuh"
+#include "ufg_internal.h"
+
+using namespace ufg;
+
+namespace {
+
+constexpr int VT_LEN = 8192;  // elements per vector tile
+
+enum BSlot { B_SLICE1 = 0, B_SLICE2, B_VEC1, B_VEC2, B_DOT, B_RES, B_NSLOT };
+enum BOp { BOP_M = 0, BOP_MDAG = 1 };
+
+struct Group {
+  ufg_lattice* lat = nullptr;           // owns the line tables and b(k) of this (N_x, tau)
+  std::vector<int> probs;
+  BatchTile* tiles = nullptr;           // device slice tiles
+  int ntiles = 0;
+  int cta_base = 0;                     // first slice-CTA index of the group (partials)
+  int2* rtiles = nullptr;               // device recurrence tiles
+  int nrtiles = 0;
+  int max_ntau = 0;
+};
+
+struct Arena {  // one precision's vectors, packed over all problems
+  void *r = nullptr, *rhat = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr,
+       *y = nullptr, *z = nullptr, *spec = nullptr, *wr = nullptr, *acc = nullptr, *x = nullptr,
+       *rhs = nullptr;
+};
+
+struct Batch {
+  int n = 0;
+  std::vector<ufg_problem> pr;
+  std::vector<long long> off;
+  long long S = 0;
+  std::vector<Group> groups;
+  std::vector<int> group_of;
+  BatchProb* probs = nullptr;     // device
+  std::vector<BatchProb> probs_h;
+  int4* vtiles = nullptr;
+  int nvtiles = 0;
+  int nslice_ctas = 0;
+  DevScalars* scs = nullptr;
+  DevScalars* scs_h = nullptr;    // pinned
+  int* done_dummy = nullptr;
+  double* w64 = nullptr;
+  double* s64 = nullptr;
+  float* w32 = nullptr;
+  float* s32 = nullptr;
+  double* c64 = nullptr;
+  float* c32 = nullptr;
+  Arena ar[2];
+  double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *y64 = nullptr;
+  double* scale = nullptr;        // per-problem scale factors (mixed precision glue)
+  double* scale_h = nullptr;      // pinned
+  double* parts = nullptr;
+  size_t part_stride = 0;
+  cudaStream_t st = nullptr;
+  int pc_kind = UFG_PC_NONE;
+  ufg_pc_params pc = {};
+  std::map<std::string, cudaGraphExec_t> graphs;
+  std::map<std::string, long long> graph_kernels;
+  std::vector<void*> allocs;
+  ~Batch() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    for (void* p : allocs) cudaFree(p);
+    if (scs_h) cudaFreeHost(scs_h);
+    if (scale_h) cudaFreeHost(scale_h);
+    for (auto& g : groups) ufg_lattice_destroy(g.lat);
+    if (st) cudaStreamDestroy(st);
+  }
+  template <typename T>
+  ufg_status alloc(T** p, size_t n_) {
+    UFG_TRY(dev_alloc(p, n_));
+    allocs.push_back((void*)*p);
+    return UFG_OK;
+  }
+  double* slot(int k) { return parts + (size_t)k * part_stride; }
+};
+
+const void* fldb(Batch& B, char w, int prec) {
+  switch (w) {
+    case 'w': return prec ? (const void*)B.w32 : (const void*)B.w64;
+    case 's': return prec ? (const void*)B.s32 : (const void*)B.s64;
+  }
+  return nullptr;
+}
+
+ufg_status slice(Batch& B, Group& g, SliceCall c, int exec_if) {
+  c.tiles = g.tiles;
+  c.ntiles = g.ntiles;
+  c.probs = B.probs;
+  c.exec_if = exec_if;
+  if (c.partials) c.partials += 2 * (size_t)g.cta_base;
+  note_launches(1);
+  cudaError_t e = slice_dispatch(g.lat->nx, c, B.st);
+  if (e != cudaSuccess) return cuda_fail(e, "batched slice kernel");
+  return UFG_OK;
+}
+
+// out = a * (A in) + bU * U with partials (out.dotP, out.out), all groups
+ufg_status apply_b(Batch& B, int prec, int op, const void* in, void* out, double a, const void* U,
+                   double bU, const void* dotP, bool self, double* part, int exec_if) {
+  for (auto& g : B.groups) {
+    SliceCall c = base_call(g.lat, FAM_KIN, prec);
+    c.in = in;
+    c.id = in;
+    if (op == BOP_M) {
+      c.pre = fldb(B, 'w', prec);
+      c.shift = -1;
+    } else {
+      c.post = fldb(B, 'w', prec);
+      c.shift = +1;
+    }
+    c.out = out;
+    c.a = a;
+    c.U = U;
+    c.bU = bU;
+    c.dotP = dotP;
+    c.want_dotP = dotP != nullptr;
+    c.want_self = self;
+    c.partials = part;
+    UFG_TRY(slice(B, g, c, exec_if));
+  }
+  return UFG_OK;
+}
+
+ufg_status vecb(Batch& B, int prec, int op, int exec_if, const void* a, const void* b,
+                const void* c, const void* d, const void* e, const void* f, double* part) {
+  note_launches(1);
+  cudaError_t err = launch_vec_batch(prec, op, B.vtiles, B.nvtiles, B.scs, exec_if, (void*)a,
+                                     (void*)b, (void*)c, (void*)d, (void*)e, (void*)f, part, B.st);
+  if (err != cudaSuccess) return cuda_fail(err, "batched vector kernel");
+  return UFG_OK;
+}
+
+ufg_status scalb(Batch& B, int op, const double* part, int kind, const double* part2, int kind2,
+                 int exec_if) {
+  note_launches(1);
+  cudaError_t err = launch_scalar_batch(op, B.scs, B.probs, B.n, part, kind, part2, kind2, exec_if,
+                                        B.st);
+  if (err != cudaSuccess) return cuda_fail(err, "batched scalar kernel");
+  return UFG_OK;
+}
+
+std::vector<double> weights(int d, bool euler) {
+  std::vector<double> c(d + 1, 1.0);
+  if (!euler || d == 0) return c;
+  std::vector<double> binom(d + 1, 0.0);
+  binom[0] = 1.0;
+  for (int i = 1; i <= d; ++i)
+    for (int k = i; k >= 1; --k) binom[k] += binom[k - 1];
+  for (int nn = 0; nn <= d; ++nn) {
+    double acc = 0.0;
+    for (int k = nn; k <= d; ++k) acc += binom[k];
+    c[nn] = acc / std::ldexp(1.0, d);
+  }
+  return c;
+}
+
+// z = P_d r (tr: P_d^T) for every running problem, momentum-space evaluation (see solvers.cu)
+ufg_status wce_b(Batch& B, int prec, const void* r, void* z, bool tr) {
+  const int d = B.pc.order;
+  const std::vector<double> cw = weights(d, B.pc.euler != 0);
+  Arena& V = B.ar[prec];
+  for (auto& g : B.groups) {
+    const void* bk = prec ? (const void*)g.lat->bk32 : (const void*)g.lat->bk64;
+    auto rec = [&](double coef, int mode, bool write_out) -> ufg_status {
+      note_launches(1);
+      cudaError_t e = launch_recurrence_batch(prec, V.spec, write_out ? V.spec : nullptr, bk,
+                                              g.max_ntau, tr ? 1 : 0, 1.0, V.acc, coef, mode, 0,
+                                              g.rtiles, g.nrtiles, B.probs, B.st);
+      if (e != cudaSuccess) return cuda_fail(e, "batched recurrence");
+      return UFG_OK;
+    };
+    SliceCall fw = base_call(g.lat, FAM_FWD, prec);
+    fw.in = r;
+    fw.out = V.spec;
+    UFG_TRY(slice(B, g, fw, 0));
+    UFG_TRY(rec(cw[0], 1, d > 0));
+    for (int nn = 1; nn <= d; ++nn) {
+      if (!tr) {
+        SliceCall iv = base_call(g.lat, FAM_INV, prec);
+        iv.in = V.spec;
+        iv.out = V.wr;
+        UFG_TRY(slice(B, g, iv, 0));
+        SliceCall m1 = base_call(g.lat, FAM_FWD, prec);
+        m1.in = V.wr;
+        m1.pre = fldb(B, 's', prec);
+        m1.bkpost = bk;
+        m1.shift = -1;
+        m1.a = -1.0;
+        m1.scale_by_A = 1;
+        m1.out = V.spec;
+        UFG_TRY(slice(B, g, m1, 0));
+      } else {
+        SliceCall m1t = base_call(g.lat, FAM_INV, prec);
+        m1t.in = V.spec;
+        m1t.bkpre = bk;
+        m1t.post = fldb(B, 's', prec);
+        m1t.shift = +1;
+        m1t.a = -1.0;
+        m1t.scale_by_A = 1;
+        m1t.out = V.wr;
+        UFG_TRY(slice(B, g, m1t, 0));
+        SliceCall fw2 = base_call(g.lat, FAM_FWD, prec);
+        fw2.in = V.wr;
+        fw2.out = V.spec;
+        UFG_TRY(slice(B, g, fw2, 0));
+      }
+      UFG_TRY(rec(cw[nn], 2, nn < d));
+    }
+    SliceCall iv = base_call(g.lat, FAM_INV, prec);
+    iv.in = V.acc;
+    iv.out = z;
+    UFG_TRY(slice(B, g, iv, 0));
+  }
+  return UFG_OK;
+}
+
+ufg_status read_scs(Batch& B) {
+  UFG_CUDA(cudaMemcpyAsync(B.scs_h, B.scs, B.n * sizeof(DevScalars), cudaMemcpyDeviceToHost, B.st));
+  UFG_CUDA(cudaStreamSynchronize(B.st));
+  return UFG_OK;
+}
+ufg_status write_scs(Batch& B) {
+  UFG_CUDA(cudaMemcpyAsync(B.scs, B.scs_h, B.n * sizeof(DevScalars), cudaMemcpyHostToDevice, B.st));
+  return UFG_OK;
+}
+
+struct BRes {
+  std::vector<int> iters, restarts, done;
+};
+
+// BiCGStab on A x = rhs for every problem whose scalars say running (tol set per problem by the
+// caller in scs_h before the call); prec selects the arena.
+ufg_status bicg_b(Batch& B, int prec, int op, const std::vector<double>& tol,
+                  const std::vector<char>& active, int maxit, int check_every, BRes* res) {
+  Arena& V = B.ar[prec];
+  const bool pc = B.pc_kind == UFG_PC_WCE;
+  const bool tr = op == BOP_MDAG;
+  for (int p = 0; p < B.n; ++p) {
+    DevScalars& h = B.scs_h[p];
+    std::memset(&h, 0, sizeof(DevScalars));
+    h.tol = tol[p];
+    h.maxit = maxit;
+    h.restart_cos = 1e-12;
+    h.rho_old = h.alpha = h.omega = 1.0;
+    h.done = active[p] ? 0 : 1;
+  }
+  UFG_TRY(write_scs(B));
+  auto init = [&](int ex, bool from_x) -> ufg_status {
+    if (from_x) {
+      UFG_TRY(apply_b(B, prec, op, V.x, V.r, -1.0, V.rhs, 1.0, nullptr, false, nullptr, ex));
+    } else {
+      UFG_TRY(vecb(B, prec, V_COPY, ex, V.r, V.rhs, nullptr, nullptr, nullptr, nullptr, nullptr));
+      UFG_TRY(vecb(B, prec, V_ZERO, ex, V.x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr));
+    }
+    UFG_TRY(vecb(B, prec, V_COPY, ex, V.rhat, V.r, nullptr, nullptr, nullptr, nullptr, nullptr));
+    UFG_TRY(vecb(B, prec, V_ZERO, ex, V.v, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr));
+    UFG_TRY(vecb(B, prec, V_ZERO, ex, V.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr));
+    UFG_TRY(vecb(B, prec, V_DOT, ex, V.rhat, V.r, V.r, V.r, nullptr, nullptr, B.slot(B_VEC2)));
+    UFG_TRY(vecb(B, prec, V_DOT, ex, V.rhat, V.rhat, V.rhs, V.rhs, nullptr, nullptr,
+                 B.slot(B_DOT)));
+    UFG_TRY(scalb(B, OP_BI_INIT, B.slot(B_VEC2), 1, B.slot(B_DOT), 1, ex));
+    return UFG_OK;
+  };
+  UFG_TRY(init(0, false));
+  auto body = [&]() -> ufg_status {
+    UFG_TRY(scalb(B, OP_BI_RHO, B.slot(B_VEC2), 1, nullptr, 1, 0));
+    UFG_TRY(vecb(B, prec, V_BI_P, 0, V.p, V.r, V.v, nullptr, nullptr, nullptr, nullptr));
+    const void* y = V.p;
+    if (pc) {
+      UFG_TRY(wce_b(B, prec, V.p, V.y, tr));
+      y = V.y;
+    }
+    UFG_TRY(apply_b(B, prec, op, y, V.v, 1.0, nullptr, 0.0, V.rhat, false, B.slot(B_SLICE1), 0));
+    UFG_TRY(scalb(B, OP_BI_ALPHA, B.slot(B_SLICE1), 0, nullptr, 0, 0));
+    UFG_TRY(vecb(B, prec, V_BI_S, 0, V.s, V.r, V.v, V.x, y, nullptr, B.slot(B_VEC1)));
+    UFG_TRY(scalb(B, OP_BI_SCHECK, B.slot(B_VEC1), 1, nullptr, 1, 0));
+    const void* z = V.s;
+    if (pc) {
+      UFG_TRY(wce_b(B, prec, V.s, V.z, tr));
+      z = V.z;
+    }
+    UFG_TRY(apply_b(B, prec, op, z, V.t, 1.0, nullptr, 0.0, V.s, true, B.slot(B_SLICE2), 0));
+    UFG_TRY(scalb(B, OP_BI_OMEGA, B.slot(B_SLICE2), 0, nullptr, 0, 0));
+    UFG_TRY(vecb(B, prec, V_BI_X, 0, V.x, z, V.r, V.s, V.t, V.rhat, B.slot(B_VEC2)));
+    UFG_TRY(scalb(B, OP_BI_RCHECK, B.slot(B_VEC2), 1, nullptr, 1, 0));
+    return UFG_OK;
+  };
+  char key[128];
+  snprintf(key, sizeof(key), "bicg|%d|%d|%d|%d|%d|%d", prec, op, check_every, B.pc_kind,
+           B.pc.order, B.pc.euler);
+  std::vector<int> restarts(B.n, 0);
+  while (true) {
+    UFG_TRY(read_scs(B));
+    bool any_run = false, any_restart = false;
+    for (int p = 0; p < B.n; ++p) {
+      if (B.scs_h[p].done == 0) any_run = true;
+      if (B.scs_h[p].done == 2) {
+        if (restarts[p] < 100) {
+          any_restart = true;
+          ++restarts[p];
+        } else {
+          B.scs_h[p].done = 3;  // breakdown persisted
+          UFG_CUDA(cudaMemcpyAsync(&B.scs[p].done, &B.scs_h[p].done, sizeof(int),
+                                   cudaMemcpyHostToDevice, B.st));
+        }
+      }
+    }
+    if (any_restart) {
+      UFG_TRY(init(2, true));
+      continue;
+    }
+    if (!any_run) break;
+    auto it = B.graphs.find(key);
+    if (it == B.graphs.end()) {
+      const long long l0 = launches_so_far();
+      UFG_CUDA(cudaStreamBeginCapture(B.st, cudaStreamCaptureModeThreadLocal));
+      ufg_status s = UFG_OK;
+      for (int i = 0; i < check_every && s == UFG_OK; ++i) s = body();
+      cudaGraph_t gr = nullptr;
+      cudaError_t e = cudaStreamEndCapture(B.st, &gr);
+      const long long captured = launches_so_far() - l0;
+      note_launches(-captured);
+      if (s != UFG_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return s;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture (batch)");
+      cudaGraphExec_t ex = nullptr;
+      e = cudaGraphInstantiate(&ex, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate (batch)");
+      it = B.graphs.emplace(key, ex).first;
+      B.graph_kernels[key] = captured;
+    }
+    UFG_CUDA(cudaGraphLaunch(it->second, B.st));
+    note_launches(B.graph_kernels[key]);
+  }
+  res->iters.assign(B.n, 0);
+  res->restarts = restarts;
+  res->done.assign(B.n, 0);
+  for (int p = 0; p < B.n; ++p) {
+    res->iters[p] = B.scs_h[p].iters;
+    res->done[p] = B.scs_h[p].done;
+  }
+  return UFG_OK;
+}
+
+// per-problem norms of an FP64 arena vector (host result)
+ufg_status norms_b(Batch& B, const double* v, std::vector<double>& out) {
+  UFG_TRY(vecb(B, 0, V_DOT, -1, nullptr, nullptr, v, v, nullptr, nullptr, B.slot(B_RES)));
+  note_launches(1);
+  cudaError_t e = launch_scalar_batch(OP_NORM2, B.scs, B.probs, B.n, B.slot(B_RES), 1, nullptr, 1,
+                                      -1, B.st);
+  if (e != cudaSuccess) return cuda_fail(e, "batched norms");
+  UFG_TRY(read_scs(B));
+  out.resize(B.n);
+  for (int p = 0; p < B.n; ++p) out[p] = std::sqrt(B.scs_h[p].rr);
+  return UFG_OK;
+}
+
+__global__ void mixed_batch_kernel(const int4* tiles, const double* scale, double* x64, float* y32,
+                                   int mode) {
+  const int4 tl = tiles[blockIdx.x];
+  const double sc = scale[tl.x];
+  for (long long i = (long long)tl.y + threadIdx.x; i < (long long)tl.y + tl.z; i += blockDim.x) {
+    if (mode == 0) y32[i] = (float)(sc * x64[i]);
+    else x64[i] += sc * (double)y32[i];
+  }
+}
+
+ufg_status mixed_glue(Batch& B, int mode, double* x64, float* y32, const std::vector<double>& sc) {
+  std::memcpy(B.scale_h, sc.data(), B.n * sizeof(double));
+  UFG_CUDA(cudaMemcpyAsync(B.scale, B.scale_h, B.n * sizeof(double), cudaMemcpyHostToDevice, B.st));
+  note_launches(1);
+  mixed_batch_kernel<<<B.nvtiles, 256, 0, B.st>>>(B.vtiles, B.scale, x64, y32, mode);
+  UFG_CUDA(cudaGetLastError());
+  return UFG_OK;
+}
+
+// Solves A x = rhs (FP64 arenas) for every problem to per-problem relative tolerances.
+ufg_status solve_b(Batch& B, int op, const double* rhs, double* x, const std::vector<double>& tol,
+                   const ufg_params* p, std::vector<int>& iters, std::vector<int>& outer,
+                   std::vector<int>& restarts, std::vector<int>& done) {
+  const size_t bytes = (size_t)B.S * sizeof(double);
+  const int ce = p->check_every > 0 ? p->check_every : 8;
+  std::vector<char> active(B.n, 1);
+  if (p->precision != UFG_MIXED) {
+    Arena& V = B.ar[0];
+    UFG_CUDA(cudaMemcpyAsync(V.rhs, rhs, bytes, cudaMemcpyDeviceToDevice, B.st));
+    BRes r;
+    UFG_TRY(bicg_b(B, 0, op, tol, active, p->maxit, ce, &r));
+    UFG_CUDA(cudaMemcpyAsync(x, V.x, bytes, cudaMemcpyDeviceToDevice, B.st));
+    for (int i = 0; i < B.n; ++i) {
+      iters[i] += r.iters[i];
+      restarts[i] += r.restarts[i];
+      done[i] = r.done[i];
+    }
+    return UFG_OK;
+  }
+  std::vector<double> bn;
+  UFG_TRY(norms_b(B, rhs, bn));
+  UFG_CUDA(cudaMemsetAsync(x, 0, bytes, B.st));
+  UFG_CUDA(cudaMemcpyAsync(B.r64, rhs, bytes, cudaMemcpyDeviceToDevice, B.st));
+  std::vector<double> rn = bn;
+  const double inner = p->inner_tol > 0 ? p->inner_tol : 1e-5;
+  for (int i = 0; i < B.n; ++i) done[i] = 5;
+  for (int round = 0; round < 60; ++round) {
+    if (round > 0) {
+      // r64 = rhs - A x64 for every problem (FP64)
+      for (int i = 0; i < B.n; ++i) {
+        B.scs_h[i].done = 0;
+      }
+      UFG_TRY(write_scs(B));
+      UFG_TRY(apply_b(B, 0, op, x, B.r64, -1.0, rhs, 1.0, nullptr, false, nullptr, -1));
+      UFG_TRY(norms_b(B, B.r64, rn));
+    }
+    bool any = false;
+    std::vector<double> inv(B.n, 0.0), tin(B.n, 1.0);
+    for (int i = 0; i < B.n; ++i) {
+      active[i] = 0;
+      if (!std::isfinite(rn[i])) {
+        done[i] = 4;
+        continue;
+      }
+      if (rn[i] <= tol[i] * bn[i] || bn[i] == 0.0) {
+        done[i] = 1;
+        continue;
+      }
+      if (iters[i] >= p->maxit) {
+        done[i] = 5;
+        continue;
+      }
+      active[i] = 1;
+      any = true;
+      inv[i] = 1.0 / rn[i];
+      tin[i] = std::fmax(inner, 0.5 * tol[i] * bn[i] / rn[i]);
+      outer[i] += 1;
+    }
+    if (!any) break;
+    UFG_TRY(mixed_glue(B, 0, B.r64, (float*)B.ar[1].rhs, inv));
+    BRes r;
+    UFG_TRY(bicg_b(B, 1, op, tin, active, p->maxit, ce, &r));
+    for (int i = 0; i < B.n; ++i) {
+      if (!active[i]) continue;
+      iters[i] += r.iters[i];
+      restarts[i] += r.restarts[i];
+      if (r.done[i] == 4) done[i] = 4;
+    }
+    std::vector<double> sc(B.n, 0.0);
+    for (int i = 0; i < B.n; ++i) sc[i] = active[i] ? rn[i] : 0.0;
+    UFG_TRY(mixed_glue(B, 1, x, (float*)B.ar[1].x, sc));
+  }
+  return UFG_OK;
+}
+
+ufg_status setup(Batch& B, int n, const ufg_problem* probs) {
+  B.n = n;
+  B.pr.assign(probs, probs + n);
+  UFG_CUDA(cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking));
+  // order problems by size (largest first) inside the arenas and tile tables
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (long long)probs[a].nx * probs[a].nx * probs[a].nx * probs[a].ntau >
+           (long long)probs[b].nx * probs[b].nx * probs[b].nx * probs[b].ntau;
+  });
+  B.off.assign(n, 0);
+  long long o = 0;
+  for (int i : order) {
+    B.off[i] = o;
+    o += (long long)probs[i].nx * probs[i].nx * probs[i].nx * probs[i].ntau;
+  }
+  B.S = o;
+  // groups by (N_x, tau)
+  B.group_of.assign(n, -1);
+  for (int i : order) {
+    int gi = -1;
+    for (size_t k = 0; k < B.groups.size(); ++k)
+      if (B.groups[k].lat->nx == probs[i].nx && B.groups[k].lat->tau == probs[i].tau) gi = (int)k;
+    if (gi < 0) {
+      Group g;
+      ufg_status s = ufg_lattice_create(probs[i].nx, 3, probs[i].tau, probs[i].g, 0, &g.lat);
+      if (s != UFG_OK) return s;
+      g.lat->spc[0] = g.lat->spc[1] = 1;
+      B.groups.push_back(g);
+      gi = (int)B.groups.size() - 1;
+    }
+    B.groups[gi].probs.push_back(i);
+    B.group_of[i] = gi;
+  }
+  B.probs_h.assign(n, BatchProb{});
+  UFG_TRY(B.alloc(&B.scs, (size_t)n));
+  if (cudaMallocHost(&B.scs_h, n * sizeof(DevScalars)) != cudaSuccess ||
+      cudaMallocHost(&B.scale_h, n * sizeof(double)) != cudaSuccess) {
+    set_error("pinned allocation failed");
+    return UFG_OOM;
+  }
+  UFG_TRY(B.alloc(&B.scale, (size_t)n));
+  // slice tiles per group (C CTAs per tile), recurrence tiles
+  int cta = 0;
+  for (auto& g : B.groups) {
+    std::vector<BatchTile> tl;
+    std::vector<int2> rt;
+    const int C = g.lat->C[0];  // same cluster size for both precisions below N_x = 32
+    if (g.lat->C[1] != C) g.lat->C[1] = C;
+    g.cta_base = cta;
+    for (int i : g.probs) {
+      BatchProb& bp = B.probs_h[i];
+      const int nt = probs[i].ntau;
+      bp.off = B.off[i];
+      bp.ntau = nt;
+      bp.V = probs[i].nx * probs[i].nx * probs[i].nx;
+      bp.A = std::sqrt(2.0) * std::sqrt(std::expm1(probs[i].tau * probs[i].g));
+      bp.st0 = cta + (int)tl.size() * C;
+      for (int t0 = 0; t0 < nt; ++t0) tl.push_back(BatchTile{i, t0});
+      bp.st1 = cta + (int)tl.size() * C;
+      for (int mb = 0; mb < (bp.V + 31) / 32; ++mb) rt.push_back(make_int2(i, mb));
+      g.max_ntau = std::max(g.max_ntau, nt);
+    }
+    g.ntiles = (int)tl.size();
+    g.nrtiles = (int)rt.size();
+    cta += g.ntiles * C;
+    UFG_TRY(B.alloc(&g.tiles, tl.size()));
+    UFG_TRY(B.alloc(&g.rtiles, rt.size()));
+    UFG_CUDA(cudaMemcpy(g.tiles, tl.data(), tl.size() * sizeof(BatchTile), cudaMemcpyHostToDevice));
+    UFG_CUDA(cudaMemcpy(g.rtiles, rt.data(), rt.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  }
+  B.nslice_ctas = cta;
+  // vector tiles over the packed arenas, in arena order
+  std::vector<int4> vt;
+  for (int i : order) {
+    BatchProb& bp = B.probs_h[i];
+    const long long S = (long long)bp.V * bp.ntau;
+    bp.vt0 = (int)vt.size();
+    for (long long s0 = 0; s0 < S; s0 += VT_LEN)
+      vt.push_back(make_int4(i, (int)(bp.off + s0), (int)std::min<long long>(VT_LEN, S - s0), 0));
+    bp.vt1 = (int)vt.size();
+  }
+  B.nvtiles = (int)vt.size();
+  UFG_TRY(B.alloc(&B.vtiles, vt.size()));
+  UFG_CUDA(cudaMemcpy(B.vtiles, vt.data(), vt.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  for (int i = 0; i < n; ++i) B.probs_h[i].done = &B.scs[i].done;
+  UFG_TRY(B.alloc(&B.probs, (size_t)n));
+  UFG_CUDA(cudaMemcpy(B.probs, B.probs_h.data(), n * sizeof(BatchProb), cudaMemcpyHostToDevice));
+  // partial slots
+  B.part_stride = 2 * (size_t)std::max(B.nslice_ctas, B.nvtiles);
+  UFG_TRY(B.alloc(&B.parts, B.part_stride * B_NSLOT));
+  UFG_CUDA(cudaMemset(B.parts, 0, B.part_stride * B_NSLOT * sizeof(double)));
+  // arenas and fields
+  const size_t S = (size_t)B.S;
+  for (int prec = 0; prec < 2; ++prec) {
+    Arena& V = B.ar[prec];
+    void** all[] = {&V.r, &V.rhat, &V.p, &V.v, &V.s, &V.t, &V.y, &V.z, &V.spec, &V.wr, &V.acc,
+                    &V.x, &V.rhs};
+    for (void** pp : all) {
+      if (prec == 0) UFG_TRY(B.alloc((double**)pp, S));
+      else UFG_TRY(B.alloc((float**)pp, S));
+    }
+  }
+  UFG_TRY(B.alloc(&B.w64, S));
+  UFG_TRY(B.alloc(&B.s64, S));
+  UFG_TRY(B.alloc(&B.c64, S));
+  UFG_TRY(B.alloc(&B.w32, S));
+  UFG_TRY(B.alloc(&B.s32, S));
+  UFG_TRY(B.alloc(&B.c32, S));
+  UFG_TRY(B.alloc(&B.x64, S));
+  UFG_TRY(B.alloc(&B.b64, S));
+  UFG_TRY(B.alloc(&B.r64, S));
+  UFG_TRY(B.alloc(&B.y64, S));
+  // per-problem set-up: potentials from sigma, right-hand side into the arena
+  for (int i = 0; i < n; ++i) {
+    const BatchProb& bp = B.probs_h[i];
+    const long long Sp = (long long)bp.V * bp.ntau;
+    UFG_CUDA(cudaMemcpyAsync(B.y64 + bp.off, probs[i].sigma, Sp * sizeof(double),
+                             cudaMemcpyDefault, B.st));
+    UFG_CUDA(launch_potentials(B.y64 + bp.off, bp.A, Sp, B.w64 + bp.off, B.s64 + bp.off,
+                               B.c64 + bp.off, B.w32 + bp.off, B.s32 + bp.off, B.c32 + bp.off,
+                               B.st));
+    note_launches(1);
+    UFG_CUDA(cudaMemcpyAsync(B.b64 + bp.off, probs[i].b, Sp * sizeof(double), cudaMemcpyDefault,
+                             B.st));
+  }
+  return UFG_OK;
+}
+
+}  // namespace
+
+extern "C" ufg_status ufg_solve_batch(int n, const ufg_problem* probs, int pc_kind,
+                                      const ufg_pc_params* pc, const ufg_params* p,
+                                      ufg_stats* stats, void* stream) {
+  clear_error();
+  if (n <= 0 || !probs || !p || !(p->tol > 0) || p->maxit <= 0 ||
+      (p->precision != UFG_FP64 && p->precision != UFG_MIXED) ||
+      (pc_kind != UFG_PC_NONE && pc_kind != UFG_PC_WCE) || (pc_kind == UFG_PC_WCE && !pc)) {
+    set_error("solve_batch: need n > 0, problems, params with tol > 0, maxit > 0, precision "
+              "FP64 or MIXED, and preconditioner none or WCE");
+    return UFG_INVALID_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    const ufg_problem& q = probs[i];
+    if (!q.sigma || !q.b || !q.x || q.nx < 4 || q.nx % 2 || !slice_supported_n(q.nx) ||
+        q.nx >= 32 || q.ntau < 3 || q.ntau > 512 || !(q.tau > 0) || !(q.g >= 0)) {
+      set_error("solve_batch: problem %d invalid or unsupported (batched N_x in {4..16} built, "
+                "3 <= N_tau <= 512)", i);
+      return UFG_INVALID_ARG;
+    }
+  }
+  if (pc_kind == UFG_PC_WCE && (pc->order < 0 || pc->order > 16)) {
+    set_error("WCE order must be in 0..16");
+    return UFG_INVALID_ARG;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  auto B = std::make_unique<Batch>();
+  B->pc_kind = pc_kind;
+  if (pc) B->pc = *pc;
+  cudaStream_t user = as_stream(stream);
+  cudaEvent_t ev;
+  UFG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  UFG_TRY(setup(*B, n, probs));
+  UFG_CUDA(cudaEventRecord(ev, user));
+  UFG_CUDA(cudaStreamWaitEvent(B->st, ev, 0));
+  std::vector<int> it1(n, 0), it2(n, 0), out1(n, 0), out2(n, 0), rs1(n, 0), rs2(n, 0),
+      d1(n, 0), d2(n, 0);
+  // step 1: M^T y = b to tol/2
+  std::vector<double> tol1(n, 0.5 * p->tol);
+  UFG_TRY(solve_b(*B, BOP_MDAG, B->b64, B->y64, tol1, p, it1, out1, rs1, d1));
+  std::vector<double> bn, yn;
+  UFG_TRY(norms_b(*B, B->b64, bn));
+  UFG_TRY(norms_b(*B, B->y64, yn));
+  std::vector<double> tol2(n);
+  for (int i = 0; i < n; ++i) {
+    const double A = B->probs_h[i].A;
+    tol2[i] = yn[i] > 0 ? p->tol * bn[i] / (2.0 * (2.0 + A) * yn[i]) : 1.0;
+  }
+  UFG_TRY(solve_b(*B, BOP_M, B->y64, B->x64, tol2, p, it2, out2, rs2, d2));
+  // true residual of the normal equations per problem: r = b - M^T (M x)
+  for (int i = 0; i < n; ++i) B->scs_h[i].done = 0;
+  UFG_TRY(write_scs(*B));
+  UFG_TRY(apply_b(*B, 0, BOP_M, B->x64, B->ar[0].t, 1.0, nullptr, 0.0, nullptr, false, nullptr, -1));
+  UFG_TRY(apply_b(*B, 0, BOP_MDAG, B->ar[0].t, B->r64, -1.0, B->b64, 1.0, nullptr, false, nullptr,
+                  -1));
+  std::vector<double> rn;
+  UFG_TRY(norms_b(*B, B->r64, rn));
+  ufg_status worst = UFG_OK;
+  for (int i = 0; i < n; ++i) {
+    const BatchProb& bp = B->probs_h[i];
+    const long long Sp = (long long)bp.V * bp.ntau;
+    UFG_CUDA(cudaMemcpyAsync(probs[i].x, B->x64 + bp.off, Sp * sizeof(double), cudaMemcpyDefault,
+                             B->st));
+  }
+  UFG_CUDA(cudaStreamSynchronize(B->st));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < n; ++i) {
+    const int dn = (d1[i] == 1 && d2[i] == 1) ? 1 : (d1[i] != 1 ? d1[i] : d2[i]);
+    ufg_status st = dn == 1 ? UFG_OK
+                    : dn == 3 ? UFG_BREAKDOWN
+                    : dn == 4 ? UFG_NONFINITE
+                              : UFG_NOT_CONVERGED;
+    const double rel = bn[i] > 0 ? rn[i] / bn[i] : 0.0;
+    if (st == UFG_OK && rel > p->tol) st = UFG_NOT_CONVERGED;
+    if (st != UFG_OK && worst == UFG_OK) worst = st;
+    if (stats) {
+      ufg_stats& s = stats[i];
+      std::memset(&s, 0, sizeof(s));
+      s.status = st;
+      s.iterations = it1[i] + it2[i];
+      s.iterations_step[0] = it1[i];
+      s.iterations_step[1] = it2[i];
+      s.outer_iterations = out1[i] + out2[i];
+      s.restarts = rs1[i] + rs2[i];
+      const int d = pc_kind == UFG_PC_WCE ? B->pc.order : -1;
+      s.n_Mdag = 2LL * it1[i];
+      s.n_M = 2LL * it2[i];
+      if (d >= 0) {
+        s.n_M0invT = 2LL * it1[i] * (d + 1);
+        s.n_M1T = 2LL * it1[i] * d;
+        s.n_M0inv = 2LL * it2[i] * (d + 1);
+        s.n_M1 = 2LL * it2[i] * d;
+        s.mv_paper = s.iterations * 2.0 * (d + 1) * 3.0;
+      } else {
+        s.mv_paper = s.iterations * 2.0;
+      }
+      s.true_residual = rel;
+      s.seconds = secs;
+    }
+  }
+  cudaEventRecord(ev, B->st);
+  cudaStreamWaitEvent(user, ev, 0);
+  cudaEventDestroy(ev);
+  B.reset();
+  if (worst != UFG_OK) set_error("at least one problem of the batch did not converge");
+  return worst;
+}

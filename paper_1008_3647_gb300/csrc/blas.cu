@@ -42,11 +42,18 @@ __device__ __forceinline__ void block_pair_store(double d1, double d2, double* p
 template <typename R, int OP>
 __global__ void __launch_bounds__(VEC_NT)
 vec_kernel(long long n, const DevScalars* __restrict__ sc, R* a, R* b, R* c, R* d, R* e, R* f,
-           double* part) {
-  if (sc != nullptr && sc->done) return;
+           double* part, const int4* tiles, int exec_if) {
+  long long stride = (long long)gridDim.x * VEC_NT;
+  long long i0 = (long long)blockIdx.x * VEC_NT + threadIdx.x;
+  if (tiles != nullptr) {  // batched: one contiguous range of one problem per CTA
+    const int4 tl = tiles[blockIdx.x];
+    sc = sc + tl.x;
+    i0 = (long long)tl.y + threadIdx.x;
+    n = (long long)tl.y + tl.z;
+    stride = VEC_NT;
+  }
+  if (sc != nullptr && exec_if >= 0 && sc->done != exec_if) return;
   double d1 = 0.0, d2 = 0.0;
-  const long long stride = (long long)gridDim.x * VEC_NT;
-  const long long i0 = (long long)blockIdx.x * VEC_NT + threadIdx.x;
   if constexpr (OP == V_CG_UPDATE) {
     const R al = (R)sc->alpha;
     for (long long i = i0; i < n; i += stride) {
@@ -95,11 +102,13 @@ vec_kernel(long long n, const DevScalars* __restrict__ sc, R* a, R* b, R* c, R* 
 
 template <typename R>
 static cudaError_t vec_dispatch(int op, long long n, const DevScalars* sc, R* a, R* b, R* c, R* d,
-                                R* e, R* f, double* part, int grid, cudaStream_t st) {
+                                R* e, R* f, double* part, int grid, cudaStream_t st,
+                                const int4* tiles = nullptr, int exec_if = 0) {
   switch (op) {
 #define CASE(OPC)                                                                         \
   case OPC:                                                                               \
-    vec_kernel<R, OPC><<<grid, VEC_NT, 0, st>>>(n, sc, a, b, c, d, e, f, part);           \
+    vec_kernel<R, OPC><<<grid, VEC_NT, 0, st>>>(n, sc, a, b, c, d, e, f, part, tiles,     \
+                                                exec_if);                                 \
     break;
     CASE(V_CG_UPDATE)
     CASE(V_CG_P)
@@ -129,12 +138,23 @@ cudaError_t launch_vec(int prec, int op, long long n, const DevScalars* sc, void
                              (float*)f, part, grid, st);
 }
 
+cudaError_t launch_vec_batch(int prec, int op, const int4* tiles, int ntiles, const DevScalars* scs,
+                             int exec_if, void* a, void* b, void* c, void* d, void* e, void* f,
+                             double* part, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (prec == 0)
+    return vec_dispatch<double>(op, 0, scs, (double*)a, (double*)b, (double*)c, (double*)d,
+                                (double*)e, (double*)f, part, ntiles, st, tiles, exec_if);
+  return vec_dispatch<float>(op, 0, scs, (float*)a, (float*)b, (float*)c, (float*)d, (float*)e,
+                             (float*)f, part, ntiles, st, tiles, exec_if);
+}
+
 // ---- scalar kernels ------------------------------------------------------------------------
-__device__ double block_sum(const double* part, int nparts, int k) {
+__device__ double block_sum(const double* part, int nparts, int k, int i0 = 0) {
   __shared__ double red[VEC_NT];
   double s = 0.0;
   if (part != nullptr)
-    for (int i = threadIdx.x; i < nparts; i += VEC_NT) s += part[2 * i + k];
+    for (int i = i0 + threadIdx.x; i < nparts; i += VEC_NT) s += part[2 * i + k];
   red[threadIdx.x] = s;
   __syncthreads();
   for (int w = VEC_NT / 2; w > 0; w >>= 1) {
@@ -148,6 +168,9 @@ __device__ double block_sum(const double* part, int nparts, int k) {
 
 __device__ __forceinline__ bool bad(double v) { return !isfinite(v); }
 
+__device__ void scalar_update(int op, DevScalars* sc, const double* part, double a0, double a1,
+                              const double* part2, double b0, double b1);
+
 __global__ void __launch_bounds__(VEC_NT)
 scalar_kernel(int op, DevScalars* sc, const double* part, int nparts, const double* part2,
               int nparts2) {
@@ -158,6 +181,27 @@ scalar_kernel(int op, DevScalars* sc, const double* part, int nparts, const doub
   const double b0 = block_sum(part2, nparts2, 0);
   const double b1 = block_sum(part2, nparts2, 1);
   if (threadIdx.x != 0) return;
+  scalar_update(op, sc, part, a0, a1, part2, b0, b1);
+}
+
+__global__ void __launch_bounds__(VEC_NT)
+scalar_batch_kernel(int op, DevScalars* scs, const BatchProb* probs, const double* part, int kind,
+                    const double* part2, int kind2, int exec_if) {
+  DevScalars* sc = scs + blockIdx.x;
+  const BatchProb& pr = probs[blockIdx.x];
+  if (exec_if >= 0 && sc->done != exec_if) return;
+  const int i0 = kind == 0 ? pr.st0 : pr.vt0, i1 = kind == 0 ? pr.st1 : pr.vt1;
+  const int j0 = kind2 == 0 ? pr.st0 : pr.vt0, j1 = kind2 == 0 ? pr.st1 : pr.vt1;
+  const double a0 = block_sum(part, i1, 0, i0);
+  const double a1 = block_sum(part, i1, 1, i0);
+  const double b0 = block_sum(part2, j1, 0, j0);
+  const double b1 = block_sum(part2, j1, 1, j0);
+  if (threadIdx.x != 0) return;
+  scalar_update(op, sc, part, a0, a1, part2, b0, b1);
+}
+
+__device__ void scalar_update(int op, DevScalars* sc, const double* part, double a0, double a1,
+                              const double* part2, double b0, double b1) {
   if ((op == OP_CG_INIT || op == OP_BI_INIT) && part2 != nullptr) sc->bn = sqrt(b1);  // rhs.rhs
   const double tb = sc->tol * sc->bn;
   switch (op) {
@@ -223,6 +267,9 @@ scalar_kernel(int op, DevScalars* sc, const double* part, int nparts, const doub
       sc->omega = a1 > 0.0 ? a0 / a1 : 0.0;
       if (bad(sc->omega)) sc->done = 4;
       break;
+    case OP_NORM2:  // part = (-, v.v)
+      sc->rr = a1;
+      break;
     case OP_BI_RCHECK:  // part = (rhat.r, r.r)
       sc->rr = a1;
       sc->rho_old = sc->rho;
@@ -237,6 +284,15 @@ scalar_kernel(int op, DevScalars* sc, const double* part, int nparts, const doub
 cudaError_t launch_scalar(int op, DevScalars* sc, const double* part, int nparts,
                           const double* part2, int nparts2, cudaStream_t st) {
   scalar_kernel<<<1, VEC_NT, 0, st>>>(op, sc, part, nparts, part2, nparts2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scalar_batch(int op, DevScalars* scs, const BatchProb* probs, int nprob,
+                                const double* part, int kind, const double* part2, int kind2,
+                                int exec_if, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  scalar_batch_kernel<<<nprob, VEC_NT, 0, st>>>(op, scs, probs, part, kind, part2, kind2,
+                                                exec_if);
   return cudaGetLastError();
 }
 

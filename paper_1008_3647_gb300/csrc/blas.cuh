@@ -8,6 +8,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "slice_call.h"
+
 namespace ufg {
 
 // Solver scalars in device memory.
@@ -35,6 +37,7 @@ enum ScalarOp {
   OP_BI_SCHECK,     // ss = s.s, converged?
   OP_BI_OMEGA,      // omega = (t.s) / (t.t)
   OP_BI_RCHECK,     // rr = r.r, converged?, rho_old = rho
+  OP_NORM2,         // rr = v.v only (no other state touched)
 };
 
 // Partial pairs per producing CTA: up to this many CTAs per producer.
@@ -60,6 +63,17 @@ cudaError_t launch_vec(int prec, int op, long long n, const DevScalars* sc, void
                        void* c, void* d, void* e, void* f, double* part, int* nparts,
                        cudaStream_t st);
 int vec_grid(long long n);
+
+// Batched form: CTA i works on tiles[i] = (problem, start, length) of the packed arenas with
+// the scalars scs[problem]; it runs while scs[problem].done == exec_if (exec_if < 0: always).
+cudaError_t launch_vec_batch(int prec, int op, const int4* tiles, int ntiles, const DevScalars* scs,
+                             int exec_if, void* a, void* b, void* c, void* d, void* e, void* f,
+                             double* part, cudaStream_t st);
+// Batched scalar kernel: CTA p reduces problem p's partials (kind 0: slice CTAs [st0, st1),
+// kind 1: vector CTAs [vt0, vt1)) and updates scs[p], while scs[p].done == exec_if.
+cudaError_t launch_scalar_batch(int op, DevScalars* scs, const BatchProb* probs, int nprob,
+                                const double* part, int kind, const double* part2, int kind2,
+                                int exec_if, cudaStream_t st);
 
 // Mixed-precision glue: y32 = scale * x64 and x64 += scale * e32.
 cudaError_t launch_to_f32(const double* x, double scale, float* y, long long n, cudaStream_t st);

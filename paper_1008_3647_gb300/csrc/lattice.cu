@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -13,6 +14,10 @@
 namespace ufg {
 
 static thread_local std::string g_err;
+static std::atomic<long long> g_launches{0};
+
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
   char buf[1024];
@@ -217,6 +222,7 @@ const void* fld(const ufg_field* f, char which, int prec) {
 
 static ufg_status run(const ufg_lattice* lat, const SliceCall& c, cudaStream_t st) {
   cudaError_t e = slice_dispatch(lat->nx, c, st);
+  note_launches(1);
   if (e != cudaSuccess) return cuda_fail(e, "slice kernel launch");
   return UFG_OK;
 }
@@ -251,6 +257,7 @@ ufg_status op_M0inv(const ufg_field* f, int prec, const void* x, void* y, void* 
   const void* bk = prec ? (const void*)lat->bk32 : (const void*)lat->bk64;
   cudaError_t e = launch_recurrence(prec, tmp, tmp, bk, lat->V, lat->ntau, transpose, 1.0, nullptr,
                                     0.0, 0, nullptr, st);
+  note_launches(1);
   if (e != cudaSuccess) return cuda_fail(e, "recurrence kernel launch");
   SliceCall iv = base_call(lat, FAM_INV, prec);
   iv.in = tmp;
@@ -269,6 +276,7 @@ ufg_status ensure_sca(ufg_field* f, double alpha, cudaStream_t st) {
   }
   cudaError_t e = launch_sca_setup(f->w64, lat->V, lat->ntau, alpha, f->L64, f->Di64, f->L32,
                                    f->Di32, st);
+  note_launches(1);
   if (e != cudaSuccess) return cuda_fail(e, "SCA setup launch");
   f->sca_alpha = alpha;
   return UFG_OK;
@@ -312,6 +320,7 @@ extern "C" {
 const char* ufg_last_error(void) { return g_err.c_str(); }
 const char* ufg_version(void) { return "ufg-gb300 0.1 (sm_103a)"; }
 const char* ufg_supported_nx(void) { return "4,6,8,10,12,16,32"; }
+long long ufg_kernel_launches(void) { return launches_so_far(); }
 
 ufg_status ufg_lattice_create(int nx, int ntau, double tau, double g, int dispersion,
                               ufg_lattice** out) {
@@ -372,6 +381,7 @@ ufg_status ufg_field_update(ufg_field* f, const double* sigma, void* stream) {
   UFG_CUDA(cudaMemcpyAsync(f->sigma, sigma, (size_t)L->S * sizeof(double), cudaMemcpyDefault, st));
   UFG_CUDA(launch_potentials(f->sigma, L->A, L->S, f->w64, f->s64, f->c64, f->w32, f->s32, f->c32,
                              st));
+  note_launches(1);
   f->sca_alpha = -1.0;
   return UFG_OK;
 }

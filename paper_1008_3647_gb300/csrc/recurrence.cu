@@ -45,20 +45,53 @@ cudaError_t launch_potentials(const double* sigma, double A, long long S, double
 // chunk (<= LMAX slices) in registers: pass 1 forms the chunk's zero-start end value, one lane
 // per mode folds the chunks to the closed boundary value and each chunk's incoming state, pass 2
 // replays the chunk from registers and writes.  One HBM read and one write per element.
+template <typename R>
+struct RecArgs {
+  const R* in;
+  R* out;
+  const R* bk;
+  long long V;
+  int ntau, len, transpose;
+  double out_scale;
+  R* acc;
+  double acc_coef;
+  int acc_mode;
+  const int* done;
+  int exec_if;
+  const int2* tiles;        // batched mode: (problem, 32-mode block) per CTA
+  const BatchProb* probs;
+};
+
 template <typename R, int LMAX>
-__global__ void recurrence_kernel(const R* in, R* out, const R* __restrict__ bk, long long V,
-                                  int ntau, int len, int transpose, double out_scale, R* acc,
-                                  double acc_coef, int acc_mode, const int* done) {
+__global__ void recurrence_kernel(const RecArgs<R> a) {
   __shared__ R Es[32][33];
   __shared__ R Ps[32][33];
   __shared__ R Is[32][33];
-  if (done != nullptr && *done) return;
   const int lane = threadIdx.x;
   const int ch = threadIdx.y;
   const int nch = blockDim.y;
-  const long long mode = (long long)blockIdx.x * 32 + lane;
+  long long V = a.V, mode;
+  int ntau = a.ntau, len = a.len;
+  size_t off = 0;
+  const int* done = a.done;
+  if (a.tiles != nullptr) {
+    const int2 tl = a.tiles[blockIdx.x];
+    const BatchProb& pr = a.probs[tl.x];
+    V = pr.V;
+    ntau = pr.ntau;
+    len = (ntau + nch - 1) / nch;
+    off = (size_t)pr.off;
+    done = pr.done;
+    mode = (long long)tl.y * 32 + lane;
+  } else {
+    mode = (long long)blockIdx.x * 32 + lane;
+  }
+  if (done != nullptr && a.exec_if >= 0 && *done != a.exec_if) return;
+  const R* in = a.in + off;
+  R* out = a.out ? a.out + off : nullptr;
+  R* acc = a.acc ? a.acc + off : nullptr;
   const bool active = mode < V;
-  const R b = active ? bk[mode] : R(0);
+  const R b = active ? a.bk[mode] : R(0);
   const int l0 = ch * len;
   R y[LMAX];
   R e = R(0), p = R(1);
@@ -66,7 +99,7 @@ __global__ void recurrence_kernel(const R* in, R* out, const R* __restrict__ bk,
   for (int i = 0; i < LMAX; ++i) {
     const int l = l0 + i;
     if (i < len && l < ntau && active) {
-      const int t = transpose ? ntau - 1 - l : l;
+      const int t = a.transpose ? ntau - 1 - l : l;
       y[i] = in[(size_t)t * V + mode];
       e = y[i] + b * e;
       p = p * b;
@@ -96,14 +129,24 @@ __global__ void recurrence_kernel(const R* in, R* out, const R* __restrict__ bk,
   for (int i = 0; i < LMAX; ++i) {
     const int l = l0 + i;
     if (i < len && l < ntau && active) {
-      const int t = transpose ? ntau - 1 - l : l;
+      const int t = a.transpose ? ntau - 1 - l : l;
       x = y[i] + b * x;
       const size_t g = (size_t)t * V + mode;
-      if (acc_mode == 1) acc[g] = R(acc_coef) * x;
-      if (acc_mode == 2) acc[g] += R(acc_coef) * x;
-      if (out != nullptr) out[g] = R(out_scale) * x;
+      if (a.acc_mode == 1) acc[g] = R(a.acc_coef) * x;
+      if (a.acc_mode == 2) acc[g] += R(a.acc_coef) * x;
+      if (out != nullptr) out[g] = R(a.out_scale) * x;
     }
   }
+}
+
+template <typename R>
+static cudaError_t rec_launch(const RecArgs<R>& a, int lmax, dim3 grid, dim3 block,
+                              cudaStream_t st) {
+  if (lmax == 16)
+    recurrence_kernel<R, 16><<<grid, block, 0, st>>>(a);
+  else
+    recurrence_kernel<R, 32><<<grid, block, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_recurrence(int prec, const void* in, void* out, const void* bk, long long V,
@@ -116,25 +159,32 @@ cudaError_t launch_recurrence(int prec, const void* in, void* out, const void* b
   dim3 block(32, nch);
   dim3 grid((unsigned)((V + 31) / 32));
   if (prec == 0) {
-    if (lmax == 16)
-      recurrence_kernel<double, 16><<<grid, block, 0, st>>>(
-          (const double*)in, (double*)out, (const double*)bk, V, ntau, len, transpose, out_scale,
-          (double*)acc, acc_coef, acc_mode, done);
-    else
-      recurrence_kernel<double, 32><<<grid, block, 0, st>>>(
-          (const double*)in, (double*)out, (const double*)bk, V, ntau, len, transpose, out_scale,
-          (double*)acc, acc_coef, acc_mode, done);
-  } else {
-    if (lmax == 16)
-      recurrence_kernel<float, 16><<<grid, block, 0, st>>>(
-          (const float*)in, (float*)out, (const float*)bk, V, ntau, len, transpose, out_scale,
-          (float*)acc, acc_coef, acc_mode, done);
-    else
-      recurrence_kernel<float, 32><<<grid, block, 0, st>>>(
-          (const float*)in, (float*)out, (const float*)bk, V, ntau, len, transpose, out_scale,
-          (float*)acc, acc_coef, acc_mode, done);
+    RecArgs<double> a{(const double*)in, (double*)out, (const double*)bk, V, ntau, len, transpose,
+                      out_scale, (double*)acc, acc_coef, acc_mode, done, 0, nullptr, nullptr};
+    return rec_launch(a, lmax, grid, block, st);
   }
-  return cudaGetLastError();
+  RecArgs<float> a{(const float*)in, (float*)out, (const float*)bk, V, ntau, len, transpose,
+                   out_scale, (float*)acc, acc_coef, acc_mode, done, 0, nullptr, nullptr};
+  return rec_launch(a, lmax, grid, block, st);
+}
+
+cudaError_t launch_recurrence_batch(int prec, const void* in, void* out, const void* bk,
+                                    int max_ntau, int transpose, double out_scale, void* acc,
+                                    double acc_coef, int acc_mode, int exec_if, const int2* tiles,
+                                    int ntiles, const BatchProb* probs, cudaStream_t st) {
+  const int lmax = max_ntau <= 512 ? 16 : 32;
+  const int nch = (max_ntau + lmax - 1) / lmax;
+  if (nch > 32 || ntiles <= 0) return ntiles <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+  dim3 block(32, nch);
+  dim3 grid((unsigned)ntiles);
+  if (prec == 0) {
+    RecArgs<double> a{(const double*)in, (double*)out, (const double*)bk, 0, 0, 0, transpose,
+                      out_scale, (double*)acc, acc_coef, acc_mode, nullptr, exec_if, tiles, probs};
+    return rec_launch(a, lmax, grid, block, st);
+  }
+  RecArgs<float> a{(const float*)in, (float*)out, (const float*)bk, 0, 0, 0, transpose, out_scale,
+                   (float*)acc, acc_coef, acc_mode, nullptr, exec_if, tiles, probs};
+  return rec_launch(a, lmax, grid, block, st);
 }
 
 // ---- strong-coupling approximation (Sec. 4) -----------------------------------------------

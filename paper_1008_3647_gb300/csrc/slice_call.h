@@ -6,6 +6,25 @@ namespace ufg {
 
 enum SliceFamily { FAM_KIN = 0, FAM_FWD = 1, FAM_INV = 2 };
 
+// Batched mode: one problem of a batch as the kernels see it (device table).
+struct BatchProb {
+  long long off;     // element offset of the problem's vectors inside every arena
+  int ntau;          // time slices of the problem
+  int V;             // sites per slice
+  int st0, st1;      // slice-kernel CTAs [st0, st1) of this problem (partials index range)
+  int vt0, vt1;      // vector-kernel CTAs [vt0, vt1)
+  int rt0, rt1;      // recurrence CTAs [rt0, rt1)
+  double A;          // coupling of the problem
+  int* done;         // the problem's solver state flag
+};
+// One slice-kernel work unit: `spc` time slices of one problem.
+struct BatchTile {
+  int prob;
+  int t0;
+};
+// Run policy on the done flag: run while the flag equals exec_if (0: running, 2: restart
+// requested); exec_if = -1 runs unconditionally.
+
 // Runtime description of one slice launch (host side, type-erased pointers).
 struct SliceCall {
   int fam = FAM_KIN;
@@ -26,6 +45,11 @@ struct SliceCall {
   double* partials = nullptr;  // [grid][2] when want_dotP || want_self
   int want_dotP = 0, want_self = 0;
   const int* done = nullptr;   // optional early-exit flag (solver loops)
+  int exec_if = 0;             // run while *done == exec_if (-1: always)
+  const BatchTile* tiles = nullptr;  // batched mode: tile table (device), one tile per unit
+  const BatchProb* probs = nullptr;  // batched mode: problem table (device)
+  int ntiles = 0;
+  int scale_by_A = 0;          // batched mode: multiply a by the problem's coupling A
   int ntau = 0;
   int shift = 0;               // -1: t_in = t_out - 1, +1: t_in = t_out + 1, 0: t_in = t_out
   int spc = 1;                 // time slices per CTA (cluster)

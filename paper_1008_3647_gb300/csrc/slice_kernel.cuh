@@ -50,6 +50,10 @@ struct SliceArgs {
   double* partials;
   int want_dotP, want_self;
   const int* done;
+  int exec_if;
+  const BatchTile* tiles;
+  const BatchProb* probs;
+  int scale_by_A;
   int ntau, shift, spc;
 };
 
@@ -84,29 +88,54 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
   R* sm = reinterpret_cast<R*>(smem_raw);
   __shared__ double red[SLICE_NT / 32][2];
 
-  if (A.done != nullptr && *A.done) return;  // same value in every CTA of the grid
+  // single problem: unit -> slices [unit*spc, ...); batched: unit -> tile (problem, t0)
+  const int unit = blockIdx.x / C;
+  int t0, ntau;
+  size_t off = 0;
+  const int* done = A.done;
+  double acoef = A.a;
+  if (A.tiles != nullptr) {
+    const BatchTile tl = A.tiles[unit];
+    const BatchProb& pr = A.probs[tl.prob];
+    t0 = tl.t0;
+    ntau = pr.ntau;
+    off = (size_t)pr.off;
+    done = pr.done;
+    if (A.scale_by_A) acoef *= pr.A;
+  } else {
+    t0 = unit * A.spc;
+    ntau = A.ntau;
+  }
+  if (done != nullptr && A.exec_if >= 0 && *done != A.exec_if) return;  // uniform per problem
 
   int rank = 0;
   if constexpr (C > 1) rank = (int)cg::this_cluster().block_rank();
-  const int unit = blockIdx.x / C;
-  const int t0 = unit * A.spc;
-  const int nsl = min(A.spc, A.ntau - t0);
+  const int nsl = min(A.spc, ntau - t0);
   const int tid = threadIdx.x;
+  const R* gin = A.in + off;
+  const R* gpre = A.pre ? A.pre + off : nullptr;
+  R* gout = A.out + off;
+  const R* gid = A.id ? A.id + off : nullptr;
+  const R* gpost = A.post ? A.post + off : nullptr;
+  const R* gpost2 = A.post2 ? A.post2 + off : nullptr;
+  const R* gU = A.U ? A.U + off : nullptr;
+  const R* gV = A.V ? A.V + off : nullptr;
+  const R* gdot = A.dotP ? A.dotP + off : nullptr;
 
   // ---- 1. load (with per-site / per-mode multipliers) ----
   for (int s = 0; s < nsl; ++s) {
     const int t_out = t0 + s;
     int t_in = t_out;
-    if (A.shift < 0) t_in = (t_out == 0) ? A.ntau - 1 : t_out - 1;
-    if (A.shift > 0) t_in = (t_out == A.ntau - 1) ? 0 : t_out + 1;
+    if (A.shift < 0) t_in = (t_out == 0) ? ntau - 1 : t_out - 1;
+    if (A.shift > 0) t_in = (t_out == ntau - 1) ? 0 : t_out + 1;
     const size_t gbase = (size_t)t_in * VOL + (size_t)rank * CHUNK;
     R* dst = sm + s * NP * PLANE;
     for (int e = tid * VW; e < CHUNK; e += SLICE_NT * VW) {
       R v[VW];
-      ld16(A.in + gbase + e, v);
-      if (A.pre != nullptr) {
+      ld16(gin + gbase + e, v);
+      if (gpre != nullptr) {
         R w[VW];
-        ld16(A.pre + gbase + e, w);
+        ld16(gpre + gbase + e, w);
 #pragma unroll
         for (int k = 0; k < VW; ++k) v[k] *= w[k];
       }
@@ -174,7 +203,7 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
     const int t_out = t0 + s;
     R sgn = R(1);
     if (A.shift < 0 && t_out != 0) sgn = R(-1);
-    if (A.shift > 0 && t_out != A.ntau - 1) sgn = R(-1);
+    if (A.shift > 0 && t_out != ntau - 1) sgn = R(-1);
     R v[N];
 #pragma unroll
     for (int z = 0; z < N; ++z) {
@@ -185,14 +214,14 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
       const size_t g = obase + (size_t)zp * NN;
       R b = sgn * val;
       if (A.bkpost != nullptr) b *= A.bkpost[zp * NN + q];
-      if (A.post != nullptr) b *= A.post[g];
-      if (A.post2 != nullptr) b *= A.post2[g];
-      if (A.id != nullptr) b += A.id[g];
-      R o = R(A.a) * b;
-      if (A.U != nullptr) o += R(A.bU) * A.U[g];
-      if (A.V != nullptr) o += R(A.cV) * A.V[g];
-      A.out[g] = o;
-      if (A.want_dotP) acc_dot += (double)o * (double)A.dotP[g];
+      if (gpost != nullptr) b *= gpost[g];
+      if (gpost2 != nullptr) b *= gpost2[g];
+      if (gid != nullptr) b += gid[g];
+      R o = R(acoef) * b;
+      if (gU != nullptr) o += R(A.bU) * gU[g];
+      if (gV != nullptr) o += R(A.cV) * gV[g];
+      gout[g] = o;
+      if (A.want_dotP) acc_dot += (double)o * (double)gdot[g];
       if (A.want_self) acc_self += (double)o * (double)o;
     });
   }
@@ -242,6 +271,10 @@ inline void fill_args(SliceArgs<N, R>& a, const SliceCall& c) {
   a.want_dotP = c.want_dotP;
   a.want_self = c.want_self;
   a.done = c.done;
+  a.exec_if = c.exec_if;
+  a.tiles = c.tiles;
+  a.probs = c.probs;
+  a.scale_by_A = c.scale_by_A;
   a.ntau = c.ntau;
   a.shift = c.shift;
   a.spc = c.spc;
@@ -256,7 +289,7 @@ inline cudaError_t launch_one(const SliceCall& c, cudaStream_t st) {
   auto kern = slice_kernel<N, R, C, FAM>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  const int units = (c.ntau + c.spc - 1) / c.spc;
+  const int units = c.tiles != nullptr ? c.ntiles : (c.ntau + c.spc - 1) / c.spc;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(units * C);
   cfg.blockDim = dim3(SLICE_NT);

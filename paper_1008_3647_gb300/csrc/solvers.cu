@@ -55,11 +55,20 @@ struct ufg_solver {
   DevScalars* sc_host = nullptr;  // pinned
   double* red_dev = nullptr;      // scratch scalar for host-visible reductions
   double* red_host = nullptr;     // pinned
-  std::map<std::string, cudaGraphExec_t> graphs;
+  struct GraphEntry {
+    cudaGraphExec_t exec;
+    long long kernels;
+  };
+  std::map<std::string, GraphEntry> graphs;
   Counts counts;
 };
 
 namespace {
+
+cudaError_t sdisp(int nx, const SliceCall& c, cudaStream_t st) {
+  note_launches(1);
+  return slice_dispatch(nx, c, st);
+}
 
 double* slot(ufg_solver* S, int k) { return S->parts + (size_t)k * 2 * MAX_PARTIAL_CTAS; }
 
@@ -84,7 +93,7 @@ ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const v
     c.shift = -1;
     c.out = t1;
     c.done = done;
-    cudaError_t e = slice_dispatch(L->nx, c, S->st);
+    cudaError_t e = sdisp(L->nx, c, S->st);
     if (e != cudaSuccess) return cuda_fail(e, "slice kernel (M of Q)");
     in = t1;
     op = OPK_MDAG;
@@ -112,7 +121,7 @@ ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const v
   c.partials = part;
   c.done = done;
   if (nparts) *nparts = slice_grid(L, prec);
-  cudaError_t e = slice_dispatch(L->nx, c, S->st);
+  cudaError_t e = sdisp(L->nx, c, S->st);
   if (e != cudaSuccess) return cuda_fail(e, "slice kernel");
   return UFG_OK;
 }
@@ -122,6 +131,7 @@ ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const v
     cudaError_t err_ = launch_vec(prec, op, n, S->sc, (void*)(a), (void*)(b), (void*)(c),     \
                                   (void*)(d), (void*)(e), (void*)(f), part, np, S->st);       \
     if (err_ != cudaSuccess) return cuda_fail(err_, "vector kernel");                         \
+    note_launches(1);                                                                         \
   } while (0)
 
 #define VEC_NODONE(prec, op, n, a, b, c, d, e, f, part, np)                                  \
@@ -129,12 +139,14 @@ ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const v
     cudaError_t err_ = launch_vec(prec, op, n, nullptr, (void*)(a), (void*)(b), (void*)(c),   \
                                   (void*)(d), (void*)(e), (void*)(f), part, np, S->st);       \
     if (err_ != cudaSuccess) return cuda_fail(err_, "vector kernel");                         \
+    note_launches(1);                                                                         \
   } while (0)
 
 #define SCALAR(op, part, np, part2, np2)                                                      \
   do {                                                                                        \
     cudaError_t err_ = launch_scalar(op, S->sc, part, np, part2, np2, S->st);                 \
     if (err_ != cudaSuccess) return cuda_fail(err_, "scalar kernel");                         \
+    note_launches(1);                                                                         \
   } while (0)
 
 // ---- preconditioners (z = P r in precision prec) -------------------------------------------
@@ -183,7 +195,7 @@ ufg_status pc_cheb(ufg_solver* S, const ufg_field* f, int prec, const void* r, v
     c.shift = -1;
     c.out = t1;
     c.done = &S->sc->done;
-    cudaError_t e = slice_dispatch(L->nx, c, S->st);
+    cudaError_t e = sdisp(L->nx, c, S->st);
     if (e != cudaSuccess) return cuda_fail(e, "slice kernel (Chebyshev)");
     S->counts.M++;
     SliceCall c2 = base_call(L, FAM_KIN, prec);
@@ -198,7 +210,7 @@ ufg_status pc_cheb(ufg_solver* S, const ufg_field* f, int prec, const void* r, v
     c2.V = cur;
     c2.cV = fin * bk2[k] / nk[k];
     c2.done = &S->sc->done;
-    e = slice_dispatch(L->nx, c2, S->st);
+    e = sdisp(L->nx, c2, S->st);
     if (e != cudaSuccess) return cuda_fail(e, "slice kernel (Chebyshev)");
     S->counts.Mdag++;
     cur = z;
@@ -238,6 +250,7 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
                                       L->ntau, tr ? 1 : 0, 1.0, V.acc, coef, acc_mode, done,
                                       S->st);
     if (e != cudaSuccess) return cuda_fail(e, "recurrence kernel");
+    note_launches(1);
     if (tr) S->counts.M0invT++; else S->counts.M0inv++;
     return UFG_OK;
   };
@@ -245,7 +258,7 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
   fw.in = r;
   fw.out = V.spec;
   fw.done = done;
-  cudaError_t e = slice_dispatch(L->nx, fw, S->st);
+  cudaError_t e = sdisp(L->nx, fw, S->st);
   if (e != cudaSuccess) return cuda_fail(e, "forward transform");
   UFG_TRY(rec(cw[0], 1, d > 0));
   for (int nn = 1; nn <= d; ++nn) {
@@ -254,7 +267,7 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
       iv.in = V.spec;
       iv.out = V.wr;
       iv.done = done;
-      e = slice_dispatch(L->nx, iv, S->st);
+      e = sdisp(L->nx, iv, S->st);
       if (e != cudaSuccess) return cuda_fail(e, "inverse transform");
       SliceCall m1 = base_call(L, FAM_FWD, prec);  // spec = -A F^T (M1 w)
       m1.in = V.wr;
@@ -264,7 +277,7 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
       m1.a = -L->A;
       m1.out = V.spec;
       m1.done = done;
-      e = slice_dispatch(L->nx, m1, S->st);
+      e = sdisp(L->nx, m1, S->st);
       if (e != cudaSuccess) return cuda_fail(e, "M1 + forward transform");
       S->counts.M1++;
     } else {
@@ -276,13 +289,13 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
       m1t.a = -L->A;
       m1t.out = V.wr;
       m1t.done = done;
-      e = slice_dispatch(L->nx, m1t, S->st);
+      e = sdisp(L->nx, m1t, S->st);
       if (e != cudaSuccess) return cuda_fail(e, "M1^T + inverse transform");
       SliceCall fw2 = base_call(L, FAM_FWD, prec);
       fw2.in = V.wr;
       fw2.out = V.spec;
       fw2.done = done;
-      e = slice_dispatch(L->nx, fw2, S->st);
+      e = sdisp(L->nx, fw2, S->st);
       if (e != cudaSuccess) return cuda_fail(e, "forward transform");
       S->counts.M1T++;
     }
@@ -292,7 +305,7 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
   iv.in = V.acc;
   iv.out = z;
   iv.done = done;
-  e = slice_dispatch(L->nx, iv, S->st);
+  e = sdisp(L->nx, iv, S->st);
   if (e != cudaSuccess) return cuda_fail(e, "inverse transform");
   return UFG_OK;
 }
@@ -317,6 +330,7 @@ ufg_status pc_apply(ufg_solver* S, ufg_field* f, int prec, const void* r, void* 
       cudaError_t e = launch_sca_apply(prec, Lt, Di, r, z, f->lat->V, f->lat->ntau, &S->sc->done,
                                        S->st);
       if (e != cudaSuccess) return cuda_fail(e, "SCA apply");
+      note_launches(1);
       S->counts.sca++;
       return UFG_OK;
     }
@@ -346,16 +360,19 @@ ufg_status run_body(ufg_solver* S, const std::string& key, int reps, Body&& body
   auto it = S->graphs.find(key);
   if (it == S->graphs.end()) {
     if (S->graphs.size() > 64) {
-      for (auto& kv : S->graphs) cudaGraphExecDestroy(kv.second);
+      for (auto& kv : S->graphs) cudaGraphExecDestroy(kv.second.exec);
       S->graphs.clear();
     }
     const Counts saved = S->counts;
+    const long long l0 = launches_so_far();
     UFG_CUDA(cudaStreamBeginCapture(S->st, cudaStreamCaptureModeThreadLocal));
     ufg_status s = UFG_OK;
     for (int i = 0; i < reps && s == UFG_OK; ++i) s = body();
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(S->st, &g);
     S->counts = saved;
+    const long long captured = launches_so_far() - l0;
+    note_launches(-captured);
     if (s != UFG_OK) {
       if (g) cudaGraphDestroy(g);
       return s;
@@ -365,9 +382,10 @@ ufg_status run_body(ufg_solver* S, const std::string& key, int reps, Body&& body
     e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-    it = S->graphs.emplace(key, ex).first;
+    it = S->graphs.emplace(key, ufg_solver::GraphEntry{ex, captured}).first;
   }
-  UFG_CUDA(cudaGraphLaunch(it->second, S->st));
+  UFG_CUDA(cudaGraphLaunch(it->second.exec, S->st));
+  note_launches(it->second.kernels);
   return UFG_OK;
 }
 
@@ -559,6 +577,7 @@ ufg_status norm64(ufg_solver* S, const double* v, long long n, double* out) {
   VEC_NODONE(0, V_DOT, n, v, v, nullptr, nullptr, nullptr, nullptr, slot(S, P_RES), &np);
   cudaError_t e = launch_reduce_to(slot(S, P_RES), np, 0, S->red_dev, S->st);
   if (e != cudaSuccess) return cuda_fail(e, "reduce");
+  note_launches(1);
   UFG_CUDA(cudaMemcpyAsync(S->red_host, S->red_dev, sizeof(double), cudaMemcpyDeviceToHost, S->st));
   UFG_CUDA(cudaStreamSynchronize(S->st));
   *out = std::sqrt(*S->red_host);
@@ -573,6 +592,7 @@ ufg_status residual64(ufg_solver* S, ufg_field* f, int op, const double* x, cons
   UFG_TRY(apply_op(S, f, 0, op, x, r, -1.0, rhs, 1.0, nullptr, true, slot(S, P_RES), &np));
   cudaError_t e = launch_reduce_to(slot(S, P_RES), np, 1, S->red_dev, S->st);
   if (e != cudaSuccess) return cuda_fail(e, "reduce");
+  note_launches(1);
   UFG_CUDA(cudaMemcpyAsync(S->red_host, S->red_dev, sizeof(double), cudaMemcpyDeviceToHost, S->st));
   UFG_CUDA(cudaStreamSynchronize(S->st));
   *rn = std::sqrt(*S->red_host);
@@ -650,6 +670,7 @@ ufg_status solve_system(ufg_solver* S, ufg_field* f, int op, const double* rhs, 
     out->outer += 1;
     cudaError_t e = launch_to_f32(S->r64, 1.0 / rn, (float*)V.rhs, n, S->st);
     if (e != cudaSuccess) return cuda_fail(e, "to_f32");
+    note_launches(1);
     // the inner solve asks at least what the outer target still needs
     const double t_in = std::fmax(inner, 0.5 * tol * bn / rn);
     KrylovResult kr;
@@ -662,6 +683,7 @@ ufg_status solve_system(ufg_solver* S, ufg_field* f, int op, const double* rhs, 
     }
     e = launch_axpy_f32_to_f64(x64, (const float*)V.x, rn, n, S->st);
     if (e != cudaSuccess) return cuda_fail(e, "axpy mixed");
+    note_launches(1);
   }
   return UFG_OK;
 }
@@ -836,7 +858,7 @@ ufg_status ufg_solver_create(const ufg_lattice* L, ufg_solver** out) {
 void ufg_solver_destroy(ufg_solver* S) {
   if (!S) return;
   if (S->st) cudaStreamSynchronize(S->st);
-  for (auto& kv : S->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : S->graphs) cudaGraphExecDestroy(kv.second.exec);
   for (int prec = 0; prec < 2; ++prec) {
     VecSet& V = S->vs[prec];
     void** all[] = {&V.r, &V.rhat, &V.p, &V.v, &V.s, &V.t, &V.y, &V.z, &V.q, &V.tmp, &V.u,
@@ -979,6 +1001,7 @@ ufg_status ufg_solve_bicgstab_two_step(ufg_solver* S, ufg_field* f, const double
     cudaError_t e = launch_vec(0, V_ADD, S->lat->S, nullptr, xd, S->xs64, nullptr, nullptr,
                                nullptr, nullptr, nullptr, nullptr, S->st);
     if (e != cudaSuccess) return cuda_fail(e, "vector kernel");
+    note_launches(1);
     o1.iters += c1.iters;
     o2.iters += c2.iters;
     o1.restarts += c1.restarts;
@@ -1028,7 +1051,7 @@ ufg_status ufg_force_from_solution(ufg_solver* S, ufg_field* f, const double* X,
   c.id = X;
   c.shift = -1;
   c.out = Y;
-  cudaError_t e = slice_dispatch(L->nx, c, S->st);
+  cudaError_t e = sdisp(L->nx, c, S->st);
   if (e != cudaSuccess) return cuda_fail(e, "slice kernel (Y = M X)");
   // dS/dsigma_t = 2 A cos sigma_t X_t [exp(-tau K) Y~_{t+1}], Y~_{N_tau} = -Y_0:
   // base = sgn * K(Y_{t_in}) * c_t * X_t with sgn = -1 except at the wrap, out = -2 * scale * base
@@ -1039,7 +1062,7 @@ ufg_status ufg_force_from_solution(ufg_solver* S, ufg_field* f, const double* X,
   fc.shift = +1;
   fc.a = -2.0 * scale;
   fc.out = dS;
-  e = slice_dispatch(L->nx, fc, S->st);
+  e = sdisp(L->nx, fc, S->st);
   if (e != cudaSuccess) return cuda_fail(e, "slice kernel (force)");
   return UFG_OK;
 }
@@ -1063,6 +1086,7 @@ ufg_status ufg_hmc_force(ufg_solver* S, ufg_field* f, const double* phi, double*
     if (e != cudaSuccess) return cuda_fail(e, "dot");
     e = launch_reduce_to(slot(S, P_RES), np, 0, S->red_dev, S->st);
     if (e != cudaSuccess) return cuda_fail(e, "reduce");
+    note_launches(2);
     UFG_CUDA(cudaMemcpyAsync(S->red_host, S->red_dev, sizeof(double), cudaMemcpyDeviceToHost,
                              S->st));
     UFG_CUDA(cudaStreamSynchronize(S->st));

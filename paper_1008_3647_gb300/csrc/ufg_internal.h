@@ -31,6 +31,10 @@ ufg_status cuda_fail(cudaError_t e, const char* what);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Kernel-launch accounting (every launch of this library's kernels, graph replays included).
+void note_launches(long long n);
+long long launches_so_far();
+
 // ---- small device buffers -----------------------------------------------------------------
 template <typename T>
 ufg_status dev_alloc(T** p, size_t n) {
@@ -59,6 +63,11 @@ cudaError_t launch_potentials(const double* sigma, double A, long long S, double
 cudaError_t launch_recurrence(int prec, const void* in, void* out, const void* bk, long long V,
                               int ntau, int transpose, double out_scale, void* acc,
                               double acc_coef, int acc_mode, const int* done, cudaStream_t st);
+// Batched form: one CTA per (problem, 32-mode block) tile; max_ntau bounds every problem's N_tau.
+cudaError_t launch_recurrence_batch(int prec, const void* in, void* out, const void* bk,
+                                    int max_ntau, int transpose, double out_scale, void* acc,
+                                    double acc_coef, int acc_mode, int exec_if, const int2* tiles,
+                                    int ntiles, const BatchProb* probs, cudaStream_t st);
 // Strong-coupling factors (per site, sequential in t) and apply.
 cudaError_t launch_sca_setup(const double* w64, long long V, int ntau, double alpha, double* L64,
                              double* Di64, float* L32, float* Di32, cudaStream_t st);

@@ -73,6 +73,7 @@ _SIGS = {
     "ufg_last_error": (ctypes.c_char_p, []),
     "ufg_version": (ctypes.c_char_p, []),
     "ufg_supported_nx": (ctypes.c_char_p, []),
+    "ufg_kernel_launches": (ctypes.c_longlong, []),
     "ufg_lattice_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp)]),
     "ufg_lattice_destroy": (None, [_vp]),
@@ -128,6 +129,10 @@ def load(path: str | None = None):
         return lib
 
 
+def ufg_kernel_launches():
+    return int(load().ufg_kernel_launches())
+
+
 def _check(status):
     if status != UFG_OK:
         raise UfgError(status, load().ufg_last_error().decode())
@@ -141,9 +146,10 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
-def _vec(t, shape, dtypes=(torch.float64, torch.float32)):
-    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
-        raise ValueError("vectors must be contiguous CUDA tensors")
+def _vec(t, shape, dtypes=(torch.float64, torch.float32), host_ok=False):
+    if not isinstance(t, torch.Tensor) or not t.is_contiguous() or not (t.is_cuda or host_ok):
+        raise ValueError("vectors must be contiguous CUDA tensors" +
+                         (" (or host tensors)" if host_ok else ""))
     if tuple(t.shape) != tuple(shape) or t.dtype not in dtypes:
         raise ValueError("expected shape %s dtype in %s, got %s %s" % (shape, dtypes, tuple(t.shape),
                                                                        t.dtype))
@@ -176,14 +182,15 @@ class Field:
 
     def __init__(self, lattice: Lattice, sigma: torch.Tensor):
         lib = load()
-        _vec(sigma, lattice.shape, (torch.float64,))
+        _vec(sigma, lattice.shape, (torch.float64,), host_ok=True)
         h = _vp()
         _check(lib.ufg_field_create(lattice._h, _ptr(sigma), _stream(), ctypes.byref(h)))
         self._h = h
         self.lattice = lattice
 
     def update(self, sigma: torch.Tensor):
-        _vec(sigma, self.lattice.shape, (torch.float64,))
+        """New sigma from a CUDA tensor or a host tensor (pinned memory copies asynchronously)."""
+        _vec(sigma, self.lattice.shape, (torch.float64,), host_ok=True)
         _check(load().ufg_field_update(self._h, _ptr(sigma), _stream()))
 
     def __del__(self):
@@ -270,6 +277,10 @@ class Solver:
         return z
 
     def _solve(self, name, field, b, x, kw):
+        """b, x: CUDA tensors or host tensors (host buffers are staged by the library)."""
+        _vec(b, self.lattice.shape, (torch.float64,), host_ok=True)
+        if x is not None:
+            _vec(x, self.lattice.shape, (torch.float64,), host_ok=True)
         lib = load()
         p = _params(**kw)
         st = Stats()

@@ -1,0 +1,73 @@
+"""Batched solves of uneven lattices (one launch per phase for the whole batch): every problem
+reaches the 1e-10 true residual (recomputed by the FP64 oracle) and agrees with its solo solve."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1008_3647_gb300.inputs import batch_shapes, field_and_source
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ufg():
+    from paper_1008_3647_gb300 import ufg as u
+    u.load()
+    return u
+
+
+def _problems(shapes):
+    out = []
+    for nx, nt, seed in shapes:
+        sg, b = field_and_source(nx, nt, seed)
+        out.append({"nx": nx, "ntau": nt, "sigma_h": sg, "b_h": b,
+                    "sigma": torch.from_numpy(sg).cuda(), "b": torch.from_numpy(b).cuda(),
+                    "x": torch.zeros(nt, nx, nx, nx, dtype=torch.float64, device="cuda")})
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_uneven_batch_converges_and_matches_solo(ufg, precision):
+    shapes = [(6, 40, 1), (8, 80, 2), (10, 40, 3), (12, 40, 4), (6, 80, 5), (8, 40, 6), (10, 80, 7)]
+    probs = _problems(shapes)
+    prec = ufg.UFG_FP64 if precision == "fp64" else ufg.UFG_MIXED
+    stats = ufg.ufg_solve_batch(probs, "wce", {"order": 2}, tol=1e-10, precision=prec)
+    for pr, st in zip(probs, stats):
+        assert st["status"] == ufg.UFG_OK, st
+        olat = O.Lattice(pr["nx"], pr["ntau"])
+        x = pr["x"].cpu().numpy()
+        r = pr["b_h"] - O.apply_Q(olat, pr["sigma_h"], x)
+        assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(pr["b_h"])
+        # the same problem solved alone
+        lat = ufg.Lattice(pr["nx"], pr["ntau"])
+        solver = ufg.Solver(lat)
+        solver.ufg_set_preconditioner("wce", order=2)
+        field = ufg.Field(lat, pr["sigma"])
+        xs, ss = solver.ufg_solve_bicgstab_two_step(field, pr["b"], tol=1e-10, precision=prec)
+        assert ss["status"] == ufg.UFG_OK
+        if precision == "fp64":
+            assert abs(ss["iterations"] - st["iterations"]) <= 2
+        assert float((xs - pr["x"]).norm() / xs.norm()) < 1e-7
+
+
+def test_batch_96_problems_shapes(ufg):
+    shapes = batch_shapes(96)
+    assert len(shapes) == 96
+    assert {s[0] for s in shapes} <= {6, 8, 10, 12} and {s[1] for s in shapes} <= {40, 80, 120, 160}
+    probs = _problems(shapes)
+    stats = ufg.ufg_solve_batch(probs, "wce", {"order": 2}, tol=1e-10, precision=ufg.UFG_MIXED)
+    assert all(st["status"] == ufg.UFG_OK for st in stats)
+    # spot-check a few problems with the oracle's residual (the biggest and two others)
+    for i in sorted(range(96), key=lambda i: -shapes[i][0] ** 3 * shapes[i][1])[:1] + [0, 50]:
+        pr = probs[i]
+        olat = O.Lattice(pr["nx"], pr["ntau"])
+        r = pr["b_h"] - O.apply_Q(olat, pr["sigma_h"], pr["x"].cpu().numpy())
+        assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(pr["b_h"])
+
+
+def test_batch_rejects_bad_problem(ufg):
+    probs = _problems([(6, 10, 1)])
+    probs[0]["nx"] = 7
+    with pytest.raises(ufg.UfgError):
+        ufg.ufg_solve_batch(probs, "wce", {"order": 1})
