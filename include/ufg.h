@@ -207,6 +207,22 @@ ufg_status ufg_force_from_solution(ufg_solver* s, ufg_field* f, const double* X,
 ufg_status ufg_solve_batch(int n, const ufg_problem* probs, int pc_kind, const ufg_pc_params* pc,
                            const ufg_params* p, ufg_stats* stats, void* stream);
 
+/* y = M^T M x in FP64 without allocating any device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc where they need the operator (code
+ * inside a CUDA-graph capture, under a memory pool that forbids extra allocations, or in a plugin
+ * that must not grow its device footprint).  sigma, x, y: device FP64 [N_tau][N_x]^3, 16-byte
+ * aligned, x and y not overlapping; the lattice (N_x, N_tau, tau, g, dispersion) is as in
+ * ufg_lattice_create.  The two intermediates (1 + A sin sigma and M x) live in a file-scope static
+ * device array of 2 x 2^20 doubles (16 MiB) that every GPU loading the library holds until exit,
+ * so N_x^3 N_tau must be <= 2^20 sites (UFG_INVALID_ARG otherwise, with a message).  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call overwrites the whole used
+ * part of the array before reading it, so nothing needs clearing, but calls share the array:
+ * calls that overlap on the GPU (different streams, or different host threads) race and must be
+ * serialised by the caller.  Asynchronous on stream. */
+ufg_status ufg_apply_Q_noalloc(int nx, int ntau, double tau, double g, int dispersion,
+                               const double* sigma, const double* x, double* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

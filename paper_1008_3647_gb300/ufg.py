@@ -104,6 +104,8 @@ _SIGS = {
     "ufg_solve_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
                                        ctypes.POINTER(PcParams), ctypes.POINTER(Params),
                                        ctypes.POINTER(Stats), _vp]),
+    "ufg_apply_Q_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, _vp, _vp, _vp, _vp]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -370,3 +372,15 @@ class PseudofermionAction(torch.autograd.Function):
         (x,) = ctx.saved_tensors
         dS = ctx.solver.ufg_force_from_solution(ctx.field, x, scale=float(gS))
         return dS, None, None, None
+
+
+def ufg_apply_Q_noalloc(nx, ntau, tau, g, sigma, x, y, dispersion=0):
+    """y = M^T M x (FP64) through the allocation-free entry point: for callers that cannot
+    allocate device memory where they need the operator.  Limited to N_x^3 N_tau <= 2^20 sites;
+    calls that overlap on the GPU race on the library's static scratch."""
+    shape = (ntau, nx, nx, nx)
+    for t in (sigma, x, y):
+        _vec(t, shape, (torch.float64,))
+    _check(load().ufg_apply_Q_noalloc(nx, ntau, tau, g, dispersion, _ptr(sigma), _ptr(x), _ptr(y),
+                                      _stream()))
+    return y
