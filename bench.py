@@ -34,8 +34,9 @@ if ROOT not in sys.path:
 
 METRIC = "solves/s to 1e-10 residual (mixed vs FP64 GPU); M apply GB/s vs HBM peak"
 NX, NTAU, PER_RANK, TOL = 16, 256, 8, 1e-10
-WORKLOAD = ("16^3x256 lattice (tau=0.05, g=5), 8 seeded problems per rank, two-step BiCGStab "
-            "+ WCE order 2, mixed FP32-inner/FP64-outer, tol 1e-10")
+WORKLOAD = ("16^3x256 lattice (tau=0.05, g=5), 8 seeded problems per rank solved together by "
+            "ufg_solve_batch: two-step BiCGStab + WCE order 2, mixed FP32-inner/FP64-outer, "
+            "tol 1e-10")
 ORACLE_COUNTS = os.path.join(ROOT, "tests", "golden", "oracle_counts_16x256.json")
 
 
@@ -205,6 +206,20 @@ def run_ufg(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    probs_d = [{"nx": NX, "ntau": NTAU, "tau": 0.05, "g": 5.0, "sigma": sig_d[i], "b": b_d[i],
+                "x": x_d[i]} for i in range(PER_RANK)]
+    probs_h = [{"nx": NX, "ntau": NTAU, "tau": 0.05, "g": 5.0, "sigma": sig_h[i], "b": b_h[i],
+                "x": x_h[i]} for i in range(PER_RANK)]
+
+    def step_batch(precision, host=False):
+        """The rank's problems through the batched entry point (field set-up included)."""
+        stats = ufg.ufg_solve_batch(probs_h if host else probs_d, "wce", {"order": 2}, tol=TOL,
+                                    precision=precision, inner_tol=1e-5, check_every=8)
+        bad = [st for st in stats if st["status"] != ufg.UFG_OK]
+        if bad:
+            raise RuntimeError("batched solve failed: %s" % bad[0])
+        return stats
+
     def step(precision, host=False, pc=("wce", {"order": 2}), kind="bicg"):
         stats = []
         for i in range(PER_RANK):
@@ -233,26 +248,31 @@ def run_ufg(args, rank, world, local_rank):
             total += e0.elapsed_time(e1) / 1e3
         return max_over_ranks(total, world, dev)
 
-    # warm-up (also captures the CUDA graphs of every solve configuration used below)
+    # warm-up (also builds the batch workspaces and captures the CUDA graphs used below)
     for _ in range(args.warmup):
-        step(ufg.UFG_MIXED)
-    step(ufg.UFG_FP64)
-    step(ufg.UFG_MIXED, host=True)
+        step_batch(ufg.UFG_MIXED)
+    step_batch(ufg.UFG_FP64)
+    step_batch(ufg.UFG_MIXED, host=True)
 
     launches0 = ufg.ufg_kernel_launches()
     stats_box = {}
     with ClockSampler(local_rank) as clk:
-        t_mixed = timed(args.steps, lambda: stats_box.__setitem__("mixed", step(ufg.UFG_MIXED)))
+        t_mixed = timed(args.steps,
+                        lambda: stats_box.__setitem__("mixed", step_batch(ufg.UFG_MIXED)))
     launches = ufg.ufg_kernel_launches() - launches0
     clocks = clk.summary()
-    t_e2e = timed(args.steps, lambda: step(ufg.UFG_MIXED, host=True))
+    t_e2e = timed(args.steps, lambda: step_batch(ufg.UFG_MIXED, host=True))
     n64 = max(1, min(args.steps, 2))
-    t_fp64 = timed(n64, lambda: stats_box.__setitem__("fp64", step(ufg.UFG_FP64)))
+    t_fp64 = timed(n64, lambda: stats_box.__setitem__("fp64", step_batch(ufg.UFG_FP64)))
+    # the same problems one at a time through the single-problem entry point
+    step(ufg.UFG_MIXED)
+    t_solo = timed(1, lambda: step(ufg.UFG_MIXED))
 
     solves = PER_RANK * world
     value = solves * args.steps / t_mixed
     e2e = solves * args.steps / t_e2e
     fp64 = solves * n64 / t_fp64
+    solo = solves / t_solo
 
     # roofline of the dominant kernel: fused M apply (slice kernel, KIN family) at 32^3 x 512
     hbm, peak_src = peaks()
@@ -278,6 +298,8 @@ def run_ufg(args, rank, world, local_rank):
         "fp64": {"value": fp64, "unit": "solves/s", "mixed_speedup": value / fp64,
                  "iterations_mean": statistics.mean(s["iterations"] for s in stats_box["fp64"]),
                  "true_residual_max": max(s["true_residual"] for s in stats_box["fp64"])},
+        "solo_mixed": {"value": solo, "unit": "solves/s",
+                       "note": "same problems, one ufg_solve_bicgstab_two_step call each"},
         "mixed": {"iterations_mean": statistics.mean(s["iterations"] for s in sm),
                   "outer_mean": statistics.mean(s["outer_iterations"] for s in sm),
                   "true_residual_max": max(s["true_residual"] for s in sm),

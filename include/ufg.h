@@ -103,8 +103,8 @@ typedef struct {
   double seconds;          /* wall time of the call */
 } ufg_stats;
 
-/* One independent problem of a batched solve.  sigma, b, x: device FP64 pointers of its own
- * lattice size. */
+/* One independent problem of a batched solve.  sigma, b, x: FP64 arrays of its own lattice size
+ * (device or host pointers). */
 typedef struct {
   int nx, ntau;
   double tau, g;
@@ -134,6 +134,15 @@ ufg_status ufg_lattice_create(int nx, int ntau, double tau, double g, int disper
 void ufg_lattice_destroy(ufg_lattice* lat);
 /* Coupling A of the lattice (Sec. 1). */
 double ufg_lattice_coupling(const ufg_lattice* lat);
+/* Autotuner: times the fused M apply for every compiled launch shape (CTAs per cluster C, time
+ * slices per CTA) on this lattice, in FP64 and FP32, and keeps the fastest for all later applies
+ * and solves built on the lattice.  Results are cached per (GPU name, N_x, N_tau, precision) in
+ * the process and, if the environment variable UFG_TUNE_CACHE names a file, appended to it and
+ * read back by later processes.  Allocates and frees three temporary vectors; call it before any
+ * stream capture.  Synchronises stream. */
+ufg_status ufg_lattice_autotune(ufg_lattice* lat, void* stream);
+/* The launch shape in use for a precision (UFG_FP64 / UFG_FP32). */
+ufg_status ufg_lattice_launch_shape(const ufg_lattice* lat, int precision, int* C, int* spc);
 
 /* Auxiliary field: copies sigma (device FP64, [N_tau][N_x]^3) and derives per site, in FP64 and
  * FP32, w = 1 + A sin sigma (B_t), s = sin sigma (C_t of Eq. MatrixM_1), c = A cos sigma (force),
@@ -201,11 +210,19 @@ ufg_status ufg_force_from_solution(ufg_solver* s, ufg_field* f, const double* X,
                                    double scale, void* stream);
 
 /* n independent problems of mixed lattice sizes, each solved by two-step BiCGStab with the
- * preconditioner settings pc_kind/pc, all problems advanced together by batched kernels (one
- * launch per phase for the whole batch) and the iteration body captured in a CUDA graph.
- * stats: n entries (nullable). */
+ * preconditioner settings pc_kind (UFG_PC_NONE or UFG_PC_WCE)/pc, all problems advanced together
+ * by batched kernels (one launch per phase per lattice extent for the whole batch) with the
+ * iteration body captured in a CUDA graph; a composite-residual correction round runs for the
+ * problems that need it.  Batched N_x: 4..16 (even, built), 3 <= N_tau <= 512.  sigma, b, x of
+ * each problem may be device or host pointers.  The workspace of a batch (arenas sized to the sum
+ * of the problems, tile tables, graphs) is allocated on the first call with a given list of
+ * shapes and kept for later calls with the same shapes (two such workspaces at most); release it
+ * with ufg_batch_cache_clear.  Calls are serialised by a library lock.  stats: n entries
+ * (nullable).  Returns the first non-OK problem status, UFG_OK if all converged. */
 ufg_status ufg_solve_batch(int n, const ufg_problem* probs, int pc_kind, const ufg_pc_params* pc,
                            const ufg_params* p, ufg_stats* stats, void* stream);
+/* Frees the cached batch workspaces. */
+void ufg_batch_cache_clear(void);
 
 /* y = M^T M x in FP64 without allocating any device memory.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc where they need the operator (code

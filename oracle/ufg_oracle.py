@@ -558,10 +558,12 @@ def solve_bicgstab_two_step(lat, sigma, b, tol=1e-10, maxit=20000, pc=None):
         counter.add("M")
         return apply_M(lat, sigma, u)
     y, it1, ok1 = bicgstab(mdag, b, 0.5 * tol, maxit, _make_pc(lat, sigma, pc, counter, True))
+    r1 = bicgstab.last_restarts
     tol2 = tol * math.sqrt(_dot(b, b)) / (2.0 * (2.0 + lat.A) * math.sqrt(_dot(y, y)))
     x, it2, ok2 = bicgstab(m, y, tol2, maxit, _make_pc(lat, sigma, pc, counter, False))
     return x, {"iterations": it1 + it2, "iterations_step": (it1, it2),
-               "converged": ok1 and ok2, "counts": dict(counter)}
+               "converged": ok1 and ok2, "counts": dict(counter),
+               "restarts": r1 + bicgstab.last_restarts}
 
 
 def mv_formula(method: str, iterations: int, d: int = 0, beta: float = 1.0) -> float:

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -69,6 +70,7 @@ struct Batch {
   float* c32 = nullptr;
   Arena ar[2];
   double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *y64 = nullptr;
+  double *rc64 = nullptr, *cr64 = nullptr;  // correction round: residual copy and correction
   double* scale = nullptr;        // per-problem scale factors (mixed precision glue)
   double* scale_h = nullptr;      // pinned
   double* parts = nullptr;
@@ -253,7 +255,8 @@ struct BRes {
 // BiCGStab on A x = rhs for every problem whose scalars say running (tol set per problem by the
 // caller in scs_h before the call); prec selects the arena.
 ufg_status bicg_b(Batch& B, int prec, int op, const std::vector<double>& tol,
-                  const std::vector<char>& active, int maxit, int check_every, BRes* res) {
+                  const std::vector<char>& active, int maxit, int check_every, BRes* res,
+                  double div_limit = 0.0) {
   Arena& V = B.ar[prec];
   const bool pc = B.pc_kind == UFG_PC_WCE;
   const bool tr = op == BOP_MDAG;
@@ -263,6 +266,7 @@ ufg_status bicg_b(Batch& B, int prec, int op, const std::vector<double>& tol,
     h.tol = tol[p];
     h.maxit = maxit;
     h.restart_cos = 1e-12;
+    h.div_limit = div_limit;
     h.rho_old = h.alpha = h.omega = 1.0;
     h.done = active[p] ? 0 : 1;
   }
@@ -390,6 +394,26 @@ __global__ void mixed_batch_kernel(const int4* tiles, const double* scale, doubl
   }
 }
 
+__global__ void axpy_batch_kernel(const int4* tiles, const double* scale, double* x,
+                                  const double* y, int copy) {
+  const int4 tl = tiles[blockIdx.x];
+  const double sc = scale[tl.x];
+  if (sc == 0.0) return;
+  for (long long i = (long long)tl.y + threadIdx.x; i < (long long)tl.y + tl.z; i += blockDim.x)
+    x[i] = copy ? y[i] : x[i] + sc * y[i];
+}
+
+// x += scale_p * y per problem (copy: x = y where scale_p != 0), FP64 arenas
+ufg_status axpy_b(Batch& B, double* x, const double* y, const std::vector<double>& sc,
+                  int copy = 0) {
+  std::memcpy(B.scale_h, sc.data(), B.n * sizeof(double));
+  UFG_CUDA(cudaMemcpyAsync(B.scale, B.scale_h, B.n * sizeof(double), cudaMemcpyHostToDevice, B.st));
+  note_launches(1);
+  axpy_batch_kernel<<<B.nvtiles, 256, 0, B.st>>>(B.vtiles, B.scale, x, y, copy);
+  UFG_CUDA(cudaGetLastError());
+  return UFG_OK;
+}
+
 ufg_status mixed_glue(Batch& B, int mode, double* x64, float* y32, const std::vector<double>& sc) {
   std::memcpy(B.scale_h, sc.data(), B.n * sizeof(double));
   UFG_CUDA(cudaMemcpyAsync(B.scale, B.scale_h, B.n * sizeof(double), cudaMemcpyHostToDevice, B.st));
@@ -401,31 +425,37 @@ ufg_status mixed_glue(Batch& B, int mode, double* x64, float* y32, const std::ve
 
 // Solves A x = rhs (FP64 arenas) for every problem to per-problem relative tolerances.
 ufg_status solve_b(Batch& B, int op, const double* rhs, double* x, const std::vector<double>& tol,
-                   const ufg_params* p, std::vector<int>& iters, std::vector<int>& outer,
-                   std::vector<int>& restarts, std::vector<int>& done) {
+                   const std::vector<char>& want, const ufg_params* p, std::vector<int>& iters,
+                   std::vector<int>& outer, std::vector<int>& restarts, std::vector<int>& done) {
   const size_t bytes = (size_t)B.S * sizeof(double);
   const int ce = p->check_every > 0 ? p->check_every : 8;
-  std::vector<char> active(B.n, 1);
-  if (p->precision != UFG_MIXED) {
+  std::vector<char> active = want;
+  // FP64 Krylov from x = 0 for the problems in `mask`; results copied into x for those only
+  auto fp64 = [&](const std::vector<char>& mask) -> ufg_status {
     Arena& V = B.ar[0];
     UFG_CUDA(cudaMemcpyAsync(V.rhs, rhs, bytes, cudaMemcpyDeviceToDevice, B.st));
     BRes r;
-    UFG_TRY(bicg_b(B, 0, op, tol, active, p->maxit, ce, &r));
-    UFG_CUDA(cudaMemcpyAsync(x, V.x, bytes, cudaMemcpyDeviceToDevice, B.st));
+    UFG_TRY(bicg_b(B, 0, op, tol, mask, p->maxit, ce, &r));
+    std::vector<double> sel(B.n, 0.0);
     for (int i = 0; i < B.n; ++i) {
+      if (!mask[i]) continue;
+      sel[i] = 1.0;
       iters[i] += r.iters[i];
       restarts[i] += r.restarts[i];
       done[i] = r.done[i];
     }
-    return UFG_OK;
-  }
+    return axpy_b(B, x, (const double*)V.x, sel, 1);
+  };
+  if (p->precision != UFG_MIXED) return fp64(want);
+  std::vector<char> fallback(B.n, 0);
   std::vector<double> bn;
   UFG_TRY(norms_b(B, rhs, bn));
   UFG_CUDA(cudaMemsetAsync(x, 0, bytes, B.st));
   UFG_CUDA(cudaMemcpyAsync(B.r64, rhs, bytes, cudaMemcpyDeviceToDevice, B.st));
   std::vector<double> rn = bn;
   const double inner = p->inner_tol > 0 ? p->inner_tol : 1e-5;
-  for (int i = 0; i < B.n; ++i) done[i] = 5;
+  for (int i = 0; i < B.n; ++i)
+    if (want[i]) done[i] = 5;
   for (int round = 0; round < 60; ++round) {
     if (round > 0) {
       // r64 = rhs - A x64 for every problem (FP64)
@@ -440,6 +470,7 @@ ufg_status solve_b(Batch& B, int op, const double* rhs, double* x, const std::ve
     std::vector<double> inv(B.n, 0.0), tin(B.n, 1.0);
     for (int i = 0; i < B.n; ++i) {
       active[i] = 0;
+      if (!want[i]) continue;
       if (!std::isfinite(rn[i])) {
         done[i] = 4;
         continue;
@@ -461,19 +492,45 @@ ufg_status solve_b(Batch& B, int op, const double* rhs, double* x, const std::ve
     if (!any) break;
     UFG_TRY(mixed_glue(B, 0, B.r64, (float*)B.ar[1].rhs, inv));
     BRes r;
-    UFG_TRY(bicg_b(B, 1, op, tin, active, p->maxit, ce, &r));
+    UFG_TRY(bicg_b(B, 1, op, tin, active, std::min(p->maxit, 1000), ce, &r, 1e8));
+    std::vector<double> sc(B.n, 0.0);
     for (int i = 0; i < B.n; ++i) {
       if (!active[i]) continue;
       iters[i] += r.iters[i];
       restarts[i] += r.restarts[i];
-      if (r.done[i] == 4) done[i] = 4;
+      if (r.done[i] == 1) {
+        sc[i] = rn[i];
+      } else {  // failed inner solve: not applied; the problem is finished in FP64
+        fallback[i] = 1;
+        rn[i] = 0.0;
+      }
     }
-    std::vector<double> sc(B.n, 0.0);
-    for (int i = 0; i < B.n; ++i) sc[i] = active[i] ? rn[i] : 0.0;
     UFG_TRY(mixed_glue(B, 1, x, (float*)B.ar[1].x, sc));
+    // problems in fallback leave the mixed loop (their residual check is skipped below)
+    for (int i = 0; i < B.n; ++i)
+      if (fallback[i]) bn[i] = 0.0;
   }
+  bool any_fb = false;
+  for (int i = 0; i < B.n; ++i) any_fb = any_fb || fallback[i];
+  if (any_fb) UFG_TRY(fp64(fallback));
   return UFG_OK;
 }
+
+std::string signature(int n, const ufg_problem* probs) {
+  std::string sig;
+  char buf[96];
+  for (int i = 0; i < n; ++i) {
+    snprintf(buf, sizeof(buf), "%d,%d,%.17g,%.17g;", probs[i].nx, probs[i].ntau, probs[i].tau,
+             probs[i].g);
+    sig += buf;
+  }
+  return sig;
+}
+
+// Batch workspaces are kept between calls with the same problem shapes (arenas, tile tables and
+// captured graphs are reused; only sigma and b are staged per call).  At most two are cached.
+std::mutex g_batch_mu;
+std::vector<std::pair<std::string, std::unique_ptr<Batch>>> g_batch_cache;
 
 ufg_status setup(Batch& B, int n, const ufg_problem* probs) {
   B.n = n;
@@ -589,7 +646,14 @@ ufg_status setup(Batch& B, int n, const ufg_problem* probs) {
   UFG_TRY(B.alloc(&B.b64, S));
   UFG_TRY(B.alloc(&B.r64, S));
   UFG_TRY(B.alloc(&B.y64, S));
-  // per-problem set-up: potentials from sigma, right-hand side into the arena
+  UFG_TRY(B.alloc(&B.rc64, S));
+  UFG_TRY(B.alloc(&B.cr64, S));
+  return UFG_OK;
+}
+
+// Per call: potentials from each problem's sigma and its right-hand side into the arenas.
+ufg_status stage_inputs(Batch& B, const ufg_problem* probs) {
+  const int n = B.n;
   for (int i = 0; i < n; ++i) {
     const BatchProb& bp = B.probs_h[i];
     const long long Sp = (long long)bp.V * bp.ntau;
@@ -632,37 +696,78 @@ extern "C" ufg_status ufg_solve_batch(int n, const ufg_problem* probs, int pc_ki
     return UFG_INVALID_ARG;
   }
   const auto t0 = std::chrono::steady_clock::now();
-  auto B = std::make_unique<Batch>();
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  const std::string sig = signature(n, probs);
+  Batch* Bp = nullptr;
+  for (auto& kv : g_batch_cache)
+    if (kv.first == sig) Bp = kv.second.get();
+  if (Bp == nullptr) {
+    auto nb = std::make_unique<Batch>();
+    ufg_status s = setup(*nb, n, probs);
+    if (s != UFG_OK) return s;
+    if (g_batch_cache.size() >= 2) g_batch_cache.erase(g_batch_cache.begin());
+    g_batch_cache.emplace_back(sig, std::move(nb));
+    Bp = g_batch_cache.back().second.get();
+  }
+  Batch* B = Bp;
   B->pc_kind = pc_kind;
   if (pc) B->pc = *pc;
   cudaStream_t user = as_stream(stream);
   cudaEvent_t ev;
   UFG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-  UFG_TRY(setup(*B, n, probs));
   UFG_CUDA(cudaEventRecord(ev, user));
   UFG_CUDA(cudaStreamWaitEvent(B->st, ev, 0));
+  UFG_TRY(stage_inputs(*B, probs));
   std::vector<int> it1(n, 0), it2(n, 0), out1(n, 0), out2(n, 0), rs1(n, 0), rs2(n, 0),
       d1(n, 0), d2(n, 0);
-  // step 1: M^T y = b to tol/2
-  std::vector<double> tol1(n, 0.5 * p->tol);
-  UFG_TRY(solve_b(*B, BOP_MDAG, B->b64, B->y64, tol1, p, it1, out1, rs1, d1));
-  std::vector<double> bn, yn;
-  UFG_TRY(norms_b(*B, B->b64, bn));
-  UFG_TRY(norms_b(*B, B->y64, yn));
-  std::vector<double> tol2(n);
-  for (int i = 0; i < n; ++i) {
-    const double A = B->probs_h[i].A;
-    tol2[i] = yn[i] > 0 ? p->tol * bn[i] / (2.0 * (2.0 + A) * yn[i]) : 1.0;
-  }
-  UFG_TRY(solve_b(*B, BOP_M, B->y64, B->x64, tol2, p, it2, out2, rs2, d2));
+  // two-step solve of M^T M x = rhs for the problems in `want`, relative tolerance tol_i
+  auto two_step = [&](const double* rhs, double* xout, const std::vector<double>& tol,
+                      const std::vector<char>& want) -> ufg_status {
+    std::vector<double> tol1(n), bnr, ynr, tol2(n);
+    for (int i = 0; i < n; ++i) tol1[i] = 0.5 * tol[i];
+    UFG_TRY(solve_b(*B, BOP_MDAG, rhs, B->y64, tol1, want, p, it1, out1, rs1, d1));
+    UFG_TRY(norms_b(*B, rhs, bnr));
+    UFG_TRY(norms_b(*B, B->y64, ynr));
+    for (int i = 0; i < n; ++i) {
+      const double A = B->probs_h[i].A;
+      tol2[i] = ynr[i] > 0 ? tol[i] * bnr[i] / (2.0 * (2.0 + A) * ynr[i]) : 1.0;
+    }
+    return solve_b(*B, BOP_M, B->y64, xout, tol2, want, p, it2, out2, rs2, d2);
+  };
   // true residual of the normal equations per problem: r = b - M^T (M x)
-  for (int i = 0; i < n; ++i) B->scs_h[i].done = 0;
-  UFG_TRY(write_scs(*B));
-  UFG_TRY(apply_b(*B, 0, BOP_M, B->x64, B->ar[0].t, 1.0, nullptr, 0.0, nullptr, false, nullptr, -1));
-  UFG_TRY(apply_b(*B, 0, BOP_MDAG, B->ar[0].t, B->r64, -1.0, B->b64, 1.0, nullptr, false, nullptr,
-                  -1));
-  std::vector<double> rn;
-  UFG_TRY(norms_b(*B, B->r64, rn));
+  std::vector<double> bn, rn;
+  UFG_TRY(norms_b(*B, B->b64, bn));
+  auto residual = [&]() -> ufg_status {
+    for (int i = 0; i < n; ++i) B->scs_h[i].done = 0;
+    UFG_TRY(write_scs(*B));
+    UFG_TRY(apply_b(*B, 0, BOP_M, B->x64, B->ar[0].t, 1.0, nullptr, 0.0, nullptr, false, nullptr,
+                    -1));
+    UFG_TRY(apply_b(*B, 0, BOP_MDAG, B->ar[0].t, B->r64, -1.0, B->b64, 1.0, nullptr, false,
+                    nullptr, -1));
+    return norms_b(*B, B->r64, rn);
+  };
+  std::vector<char> all(n, 1);
+  UFG_TRY(two_step(B->b64, B->x64, std::vector<double>(n, p->tol), all));
+  UFG_TRY(residual());
+  // one defect-correction round on the composite residual where it is still above tol
+  std::vector<char> need(n, 0);
+  std::vector<double> tolc(n, 1.0), add(n, 0.0);
+  bool any = false;
+  for (int i = 0; i < n; ++i) {
+    if (d1[i] == 1 && d2[i] == 1 && bn[i] > 0 && rn[i] > p->tol * bn[i]) {
+      need[i] = 1;
+      tolc[i] = p->tol * bn[i] / rn[i];
+      add[i] = 1.0;
+      any = true;
+    }
+  }
+  if (any) {
+    const size_t bytes = (size_t)B->S * sizeof(double);
+    UFG_CUDA(cudaMemcpyAsync(B->rc64, B->r64, bytes, cudaMemcpyDeviceToDevice, B->st));
+    UFG_TRY(two_step(B->rc64, B->cr64, tolc, need));
+    UFG_TRY(axpy_b(*B, B->x64, B->cr64, add));
+    UFG_TRY(residual());
+  }
   ufg_status worst = UFG_OK;
   for (int i = 0; i < n; ++i) {
     const BatchProb& bp = B->probs_h[i];
@@ -709,7 +814,11 @@ extern "C" ufg_status ufg_solve_batch(int n, const ufg_problem* probs, int pc_ki
   cudaEventRecord(ev, B->st);
   cudaStreamWaitEvent(user, ev, 0);
   cudaEventDestroy(ev);
-  B.reset();
   if (worst != UFG_OK) set_error("at least one problem of the batch did not converge");
   return worst;
+}
+
+extern "C" void ufg_batch_cache_clear(void) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  g_batch_cache.clear();
 }

@@ -222,6 +222,7 @@ __device__ void scalar_update(int op, DevScalars* sc, const double* part, double
       sc->rr = a1;
       if (bad(a1)) sc->done = 4;
       else if (sqrt(a1) <= tb) sc->done = 1;
+      else if (sc->div_limit > 0 && sqrt(a1) > sc->div_limit * sc->bn) sc->done = 6;
       else if (sc->iters >= sc->maxit) sc->done = 5;
       break;
     case OP_CG_BETA: {  // part = (r.z, -) or, without preconditioner, part2 = (-, r.r)
@@ -262,6 +263,7 @@ __device__ void scalar_update(int op, DevScalars* sc, const double* part, double
       sc->ss = a1;
       if (bad(a1)) sc->done = 4;
       else if (sqrt(a1) <= tb) sc->done = 1;
+      else if (sc->div_limit > 0 && sqrt(a1) > sc->div_limit * sc->bn) sc->done = 6;
       break;
     case OP_BI_OMEGA:  // part = slice partials (t.s, t.t)
       sc->omega = a1 > 0.0 ? a0 / a1 : 0.0;
@@ -275,6 +277,7 @@ __device__ void scalar_update(int op, DevScalars* sc, const double* part, double
       sc->rho_old = sc->rho;
       if (bad(a1)) sc->done = 4;
       else if (sqrt(a1) <= tb) sc->done = 1;
+      else if (sc->div_limit > 0 && sqrt(a1) > sc->div_limit * sc->bn) sc->done = 6;
       else if (sc->omega == 0.0) sc->done = 2;
       else if (sc->iters >= sc->maxit) sc->done = 5;
       break;

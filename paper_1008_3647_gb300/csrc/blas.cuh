@@ -20,7 +20,9 @@ struct DevScalars {
   double rho, rho_old, omega, rhatn2;       // BiCGStab
   double rr, ss;
   double restart_cos;                       // near-breakdown threshold on |rho|
-  int done;        // 0 running, 1 converged, 2 restart requested, 4 non-finite, 5 maxit
+  double div_limit;                         // > 0: stop with done = 6 once ||r|| > div_limit ||rhs||
+  int done;        // 0 running, 1 converged, 2 restart requested, 4 non-finite, 5 maxit,
+                   // 6 diverged
   int iters;
   int maxit;
   int pad;

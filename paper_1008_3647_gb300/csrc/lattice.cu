@@ -2,6 +2,7 @@
 // C-ABI operator applications (M, M^T, Q, M1, M1^T, kinetic, M0^{-1}, M0^{-T}).
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <atomic>
 #include <mutex>
@@ -497,3 +498,169 @@ ufg_status ufg_apply_M0invT(ufg_field* f, const void* x, void* y, int prec, void
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Launch-shape autotuner: times the fused M apply (the slice kernel every operator shares) for
+// each compiled (cluster size, slices per CTA) candidate on this lattice and keeps the fastest per
+// precision.  Results are cached per (device name, N_x, N_tau, precision) in the process and, when
+// UFG_TUNE_CACHE names a file, in that file (one "name nx ntau prec C spc" line per entry).
+// ---------------------------------------------------------------------------------------------
+namespace ufg {
+namespace {
+
+std::mutex g_tune_mu;
+std::vector<std::string> g_tune_lines;  // "name nx ntau prec C spc"
+bool g_tune_loaded = false;
+
+std::string device_name() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+  std::string s = p.name;
+  for (char& c : s)
+    if (c == ' ') c = '_';
+  return s;
+}
+
+void load_tune_file() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("UFG_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char buf[256];
+  while (std::fgets(buf, sizeof(buf), f)) {
+    std::string l(buf);
+    while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+    if (!l.empty()) g_tune_lines.push_back(l);
+  }
+  std::fclose(f);
+}
+
+bool lookup(const std::string& key, int* C, int* spc) {
+  for (const auto& l : g_tune_lines) {
+    if (l.compare(0, key.size(), key) == 0 && l.size() > key.size() && l[key.size()] == ' ') {
+      return std::sscanf(l.c_str() + key.size(), "%d %d", C, spc) == 2;
+    }
+  }
+  return false;
+}
+
+void store(const std::string& key, int C, int spc) {
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s %d %d", key.c_str(), C, spc);
+  g_tune_lines.push_back(buf);
+  const char* path = std::getenv("UFG_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s\n", buf);
+  std::fclose(f);
+}
+
+}  // namespace
+}  // namespace ufg
+
+extern "C" ufg_status ufg_lattice_autotune(ufg_lattice* L, void* stream) {
+  clear_error();
+  if (!L) {
+    set_error("null lattice");
+    return UFG_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  load_tune_file();
+  cudaStream_t st = as_stream(stream);
+  const int N = L->nx;
+  for (int prec = 0; prec < 2; ++prec) {
+    char key[160];
+    std::snprintf(key, sizeof(key), "%s %d %d %d", device_name().c_str(), N, L->ntau, prec);
+    int C = 0, spc = 0;
+    if (lookup(key, &C, &spc)) {
+      L->C[prec] = C;
+      L->spc[prec] = spc;
+      continue;
+    }
+    std::vector<std::pair<int, int>> cand;
+    const size_t es = prec ? 4 : 8;
+    const int cs[] = {1, 2, 4};
+    for (int c : cs) {
+      if (c > 1 && N < 16) continue;
+      if (N % c) continue;
+      for (int s = 1; s <= 8; s *= 2) {
+        const size_t smem = (size_t)s * (N / c) * N * (N + 1) * es;
+        if (smem > 200 * 1024) continue;
+        if (s > 1 && (L->ntau + s - 1) / s * c < 152) continue;  // keep at least one wave
+        cand.emplace_back(c, s);
+      }
+    }
+    if (cand.empty()) continue;
+    const size_t n = (size_t)L->S;
+    void *x = nullptr, *y = nullptr, *w = nullptr;
+    if (cudaMalloc(&x, n * es) != cudaSuccess || cudaMalloc(&y, n * es) != cudaSuccess ||
+        cudaMalloc(&w, n * es) != cudaSuccess) {
+      cudaFree(x);
+      cudaFree(y);
+      cudaFree(w);
+      cudaGetLastError();
+      set_error("autotune: temporary allocation failed");
+      return UFG_OOM;
+    }
+    cudaMemsetAsync(x, 0, n * es, st);
+    cudaMemsetAsync(w, 0, n * es, st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    std::pair<int, int> bestc = {L->C[prec], L->spc[prec]};
+    for (auto& cd : cand) {
+      SliceCall c = base_call(L, FAM_KIN, prec);
+      c.C = cd.first;
+      c.spc = cd.second;
+      c.in = x;
+      c.pre = w;
+      c.id = x;
+      c.shift = -1;
+      c.out = y;
+      if (slice_dispatch(N, c, st) != cudaSuccess) {  // shape not available: skip it
+        cudaGetLastError();
+        continue;
+      }
+      cudaEventRecord(e0, st);
+      const int reps = 5;
+      for (int r = 0; r < reps; ++r) slice_dispatch(N, c, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bestc = cd;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(y);
+    cudaFree(w);
+    L->C[prec] = bestc.first;
+    L->spc[prec] = bestc.second;
+    store(key, bestc.first, bestc.second);
+  }
+  return UFG_OK;
+}
+
+extern "C" ufg_status ufg_lattice_launch_shape(const ufg_lattice* L, int precision, int* C,
+                                               int* spc) {
+  if (!L || !C || !spc || (precision != UFG_FP64 && precision != UFG_FP32)) {
+    set_error("launch_shape: bad arguments");
+    return UFG_INVALID_ARG;
+  }
+  *C = L->C[precision];
+  *spc = L->spc[precision];
+  return UFG_OK;
+}

@@ -70,8 +70,18 @@ __device__ __forceinline__ void ld16(const R* p, R (&o)[Vec16<R>::W]) {
 
 constexpr int SLICE_NT = 256;
 
-template <int N, typename R, int C, int FAM>
-__global__ void __launch_bounds__(SLICE_NT)
+// Epilogue operand mask: the specialised variants know at compile time which operands exist;
+// EPI_ANY tests every optional pointer at run time.
+enum EpiBits { E_ID = 1, E_POST = 2, E_POST2 = 4, E_UV = 8, E_DOT = 16, E_BK = 32, EPI_ANY = 63 };
+
+// Resident CTAs per SM the register allocation must allow (256 threads each).
+template <int N, typename R>
+constexpr int slice_min_blocks() {
+  return N >= 32 ? (sizeof(R) == 4 ? 3 : 1) : (N >= 16 ? (sizeof(R) == 4 ? 3 : 2) : 3);
+}
+
+template <int N, typename R, int C, int FAM, int EPI>
+__global__ void __launch_bounds__(SLICE_NT, (slice_min_blocks<N, R>()))
 slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
   constexpr int NP = N / C;          // z-planes of one slice held by this CTA
   constexpr int PITCH = N + 1;       // padded row
@@ -130,6 +140,7 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
     if (A.shift > 0) t_in = (t_out == ntau - 1) ? 0 : t_out + 1;
     const size_t gbase = (size_t)t_in * VOL + (size_t)rank * CHUNK;
     R* dst = sm + s * NP * PLANE;
+#pragma unroll 4
     for (int e = tid * VW; e < CHUNK; e += SLICE_NT * VW) {
       R v[VW];
       ld16(gin + gbase + e, v);
@@ -145,14 +156,18 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
 #pragma unroll
         for (int k = 0; k < VW; ++k) v[k] *= w[k];
       }
+      if constexpr (N % VW == 0) {  // a vector never crosses a row: one address per vector
+        const int row = e / N;      // row index over all planes of this slice
+        R* d = dst + row * PITCH + (e - row * N);
 #pragma unroll
-      for (int k = 0; k < VW; ++k) {
-        const int idx = e + k;
-        const int p = idx / NN;
-        const int rem = idx - p * NN;
-        const int row = rem / N;
-        const int col = rem - row * N;
-        dst[p * PLANE + row * PITCH + col] = v[k];
+        for (int k = 0; k < VW; ++k) d[k] = v[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+          const int idx = e + k;
+          const int row = idx / N;
+          dst[row * PITCH + (idx - row * N)] = v[k];
+        }
       }
     }
   }
@@ -213,16 +228,47 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
     line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef, [&](int zp, R val) {
       const size_t g = obase + (size_t)zp * NN;
       R b = sgn * val;
-      if (A.bkpost != nullptr) b *= A.bkpost[zp * NN + q];
-      if (gpost != nullptr) b *= gpost[g];
-      if (gpost2 != nullptr) b *= gpost2[g];
-      if (gid != nullptr) b += gid[g];
-      R o = R(acoef) * b;
-      if (gU != nullptr) o += R(A.bU) * gU[g];
-      if (gV != nullptr) o += R(A.cV) * gV[g];
-      gout[g] = o;
-      if (A.want_dotP) acc_dot += (double)o * (double)gdot[g];
-      if (A.want_self) acc_self += (double)o * (double)o;
+      if constexpr (EPI == EPI_ANY) {
+        if (A.bkpost != nullptr) b *= A.bkpost[zp * NN + q];
+        if (gpost != nullptr) b *= gpost[g];
+        if (gpost2 != nullptr) b *= gpost2[g];
+        if (gid != nullptr) b += gid[g];
+        R o = R(acoef) * b;
+        if (gU != nullptr) o += R(A.bU) * gU[g];
+        if (gV != nullptr) o += R(A.cV) * gV[g];
+        gout[g] = o;
+        if (A.want_dotP) acc_dot += (double)o * (double)gdot[g];
+        if (A.want_self) acc_self += (double)o * (double)o;
+      } else if constexpr (EPI & E_UV) {  // U or V may alias out (in-place updates)
+        if constexpr (EPI & E_BK) b *= A.bkpost[zp * NN + q];
+        if constexpr (EPI & E_POST) b *= gpost[g];
+        if constexpr (EPI & E_POST2) b *= gpost2[g];
+        if constexpr (EPI & E_ID) b += gid[g];
+        R o = R(acoef) * b;
+        if (gU != nullptr) o += R(A.bU) * gU[g];
+        if (gV != nullptr) o += R(A.cV) * gV[g];
+        gout[g] = o;
+        if constexpr (EPI & E_DOT) {
+          if (A.want_dotP) acc_dot += (double)o * (double)gdot[g];
+          if (A.want_self) acc_self += (double)o * (double)o;
+        }
+      } else {  // operands never alias the output: loads may move ahead of earlier stores
+        const R* __restrict__ rid = gid;
+        const R* __restrict__ rpost = gpost;
+        const R* __restrict__ rpost2 = gpost2;
+        const R* __restrict__ rdot = gdot;
+        R* __restrict__ rout = gout;
+        if constexpr (EPI & E_BK) b *= __ldg(A.bkpost + zp * NN + q);
+        if constexpr (EPI & E_POST) b *= __ldg(rpost + g);
+        if constexpr (EPI & E_POST2) b *= __ldg(rpost2 + g);
+        if constexpr (EPI & E_ID) b += __ldg(rid + g);
+        const R o = R(acoef) * b;
+        rout[g] = o;
+        if constexpr (EPI & E_DOT) {
+          if (A.want_dotP) acc_dot += (double)o * (double)__ldg(rdot + g);
+          if (A.want_self) acc_self += (double)o * (double)o;
+        }
+      }
     });
   }
 
@@ -280,15 +326,24 @@ inline void fill_args(SliceArgs<N, R>& a, const SliceCall& c) {
   a.spc = c.spc;
 }
 
-template <int N, typename R, int C, int FAM>
-inline cudaError_t launch_one(const SliceCall& c, cudaStream_t st) {
+template <int N, typename R, int C, int FAM, int EPI>
+inline cudaError_t launch_epi(const SliceCall& c, cudaStream_t st) {
   SliceArgs<N, R> a;
   fill_args<N, R>(a, c);
   constexpr int PLANE = N * (N + 1);
   const size_t smem = (size_t)c.spc * (N / C) * PLANE * sizeof(R);
-  auto kern = slice_kernel<N, R, C, FAM>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
+  auto kern = slice_kernel<N, R, C, FAM, EPI>;
+  // attributes are set once per instantiation (outside any stream capture that follows)
+  static int configured_smem = 0;
+  if ((int)smem > configured_smem) {
+    cudaError_t err =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
+    if (err != cudaSuccess) return err;
+    configured_smem = (int)smem;
+  }
   const int units = c.tiles != nullptr ? c.ntiles : (c.ntau + c.spc - 1) / c.spc;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(units * C);
@@ -305,6 +360,32 @@ inline cudaError_t launch_one(const SliceCall& c, cudaStream_t st) {
     cfg.numAttrs = 1;
   }
   return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <int N, typename R, int C, int FAM>
+inline cudaError_t launch_one(const SliceCall& c, cudaStream_t st) {
+  const int mask = (c.id ? E_ID : 0) | (c.post ? E_POST : 0) | (c.post2 ? E_POST2 : 0) |
+                   ((c.U || c.V) ? E_UV : 0) | ((c.want_dotP || c.want_self) ? E_DOT : 0) |
+                   (c.bkpost ? E_BK : 0);
+  if constexpr (FAM == FAM_KIN) {
+    switch (mask) {
+      case E_ID: return launch_epi<N, R, C, FAM, E_ID>(c, st);                       // M
+      case E_ID | E_POST: return launch_epi<N, R, C, FAM, E_ID | E_POST>(c, st);     // M^T
+      case E_ID | E_DOT: return launch_epi<N, R, C, FAM, E_ID | E_DOT>(c, st);
+      case E_ID | E_POST | E_DOT: return launch_epi<N, R, C, FAM, E_ID | E_POST | E_DOT>(c, st);
+    }
+  } else if constexpr (FAM == FAM_FWD) {
+    switch (mask) {
+      case 0: return launch_epi<N, R, C, FAM, 0>(c, st);
+      case E_BK: return launch_epi<N, R, C, FAM, E_BK>(c, st);
+    }
+  } else {
+    switch (mask) {
+      case 0: return launch_epi<N, R, C, FAM, 0>(c, st);
+      case E_POST: return launch_epi<N, R, C, FAM, E_POST>(c, st);
+    }
+  }
+  return launch_epi<N, R, C, FAM, EPI_ANY>(c, st);
 }
 
 template <int N, typename R, int FAM>

@@ -6,6 +6,7 @@
 // (blas.cuh), so the host captures `check_every` iterations into a CUDA graph once and replays it,
 // reading back the convergence flag between replays.  The solver runs on its own non-blocking
 // stream ordered after/before the caller's stream by events.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -395,10 +396,11 @@ ufg_status read_scalars(ufg_solver* S) {
   return UFG_OK;
 }
 
-ufg_status write_scalars(ufg_solver* S, double tol, int maxit) {
+ufg_status write_scalars(ufg_solver* S, double tol, int maxit, double div_limit = 0.0) {
   std::memset(S->sc_host, 0, sizeof(DevScalars));
   S->sc_host->tol = tol;
   S->sc_host->maxit = maxit;
+  S->sc_host->div_limit = div_limit;
   S->sc_host->restart_cos = 1e-12;
   S->sc_host->rho_old = S->sc_host->alpha = S->sc_host->omega = 1.0;
   UFG_CUDA(cudaMemcpyAsync(S->sc, S->sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice, S->st));
@@ -422,11 +424,11 @@ struct KrylovResult {
 
 // ---- CG on Q x = rhs (vectors of precision prec; rhs, x live in the VecSet) ----------------
 ufg_status run_cg(ufg_solver* S, ufg_field* f, int prec, double tol, int maxit, int check_every,
-                  bool x0, KrylovResult* res) {
+                  bool x0, KrylovResult* res, double div_limit = 0.0) {
   VecSet& V = S->vs[prec];
   const long long n = f->lat->S;
   const bool pc = S->pc_kind == UFG_PC_CHEB || S->pc_kind == UFG_PC_SCA;
-  UFG_TRY(write_scalars(S, tol, maxit));
+  UFG_TRY(write_scalars(S, tol, maxit, div_limit));
   int np = 0, npd = 0, nps = 0;
   if (x0) {
     UFG_TRY(apply_op(S, f, prec, OPK_Q, V.x, V.r, -1.0, V.rhs, 1.0, nullptr, false, nullptr,
@@ -485,12 +487,12 @@ ufg_status run_cg(ufg_solver* S, ufg_field* f, int prec, double tol, int maxit, 
 
 // ---- BiCGStab on A x = rhs, A = M or M^T, right preconditioner P_d or P_d^T -----------------
 ufg_status run_bicgstab(ufg_solver* S, ufg_field* f, int prec, int op, double tol, int maxit,
-                        int check_every, bool x0, KrylovResult* res) {
+                        int check_every, bool x0, KrylovResult* res, double div_limit = 0.0) {
   VecSet& V = S->vs[prec];
   const long long n = f->lat->S;
   const bool pc = S->pc_kind == UFG_PC_WCE;
   const bool tr = (op == OPK_MDAG);
-  UFG_TRY(write_scalars(S, tol, maxit));
+  UFG_TRY(write_scalars(S, tol, maxit, div_limit));
   auto restart = [&](bool have_x) -> ufg_status {
     int n1 = 0, n2 = 0;
     if (have_x) {
@@ -604,6 +606,7 @@ struct SolveOut {
   int outer = 0;
   int restarts = 0;
   int done = 0;
+  int fallback = 0;  // mixed precision: an FP32 inner solve failed and FP64 finished the system
 };
 
 ufg_status status_of(int done) {
@@ -612,6 +615,7 @@ ufg_status status_of(int done) {
     case 3: set_error("BiCGStab breakdown persisted through 100 restarts"); return UFG_BREAKDOWN;
     case 4: set_error("non-finite value in the Krylov recursion"); return UFG_NONFINITE;
     case 5: set_error("iteration limit reached"); return UFG_NOT_CONVERGED;
+    case 6: set_error("Krylov recursion diverged"); return UFG_NOT_CONVERGED;
   }
   set_error("solver stopped in state %d", done);
   return UFG_INTERNAL;
@@ -624,22 +628,25 @@ ufg_status solve_system(ufg_solver* S, ufg_field* f, int op, const double* rhs, 
                         bool x0, double tol, const ufg_params* p, SolveOut* out) {
   const long long n = f->lat->S;
   const int ce = p->check_every > 0 ? p->check_every : 8;
-  auto krylov = [&](int prec, double t, bool guess, KrylovResult* kr) -> ufg_status {
-    if (op == OPK_Q) return run_cg(S, f, prec, t, p->maxit, ce, guess, kr);
-    return run_bicgstab(S, f, prec, op, t, p->maxit, ce, guess, kr);
+  auto krylov = [&](int prec, double t, bool guess, KrylovResult* kr, int maxit,
+                    double div) -> ufg_status {
+    if (op == OPK_Q) return run_cg(S, f, prec, t, maxit, ce, guess, kr, div);
+    return run_bicgstab(S, f, prec, op, t, maxit, ce, guess, kr, div);
   };
-  if (p->precision != UFG_MIXED) {
+  auto fp64_solve = [&](bool guess) -> ufg_status {
     VecSet& V = S->vs[0];
     UFG_CUDA(cudaMemcpyAsync(V.rhs, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, S->st));
-    if (x0) UFG_CUDA(cudaMemcpyAsync(V.x, x64, n * sizeof(double), cudaMemcpyDeviceToDevice, S->st));
+    if (guess)
+      UFG_CUDA(cudaMemcpyAsync(V.x, x64, n * sizeof(double), cudaMemcpyDeviceToDevice, S->st));
     KrylovResult kr;
-    UFG_TRY(krylov(0, tol, x0, &kr));
+    UFG_TRY(krylov(0, tol, guess, &kr, p->maxit, 0.0));
     UFG_CUDA(cudaMemcpyAsync(x64, V.x, n * sizeof(double), cudaMemcpyDeviceToDevice, S->st));
     out->iters += kr.iters;
     out->restarts += kr.restarts;
     out->done = kr.done;
     return UFG_OK;
-  }
+  };
+  if (p->precision != UFG_MIXED) return fp64_solve(x0);
   // mixed precision: x64 += ||r|| e32 with Q e32 = r / ||r|| solved in FP32
   double bn = 0.0;
   UFG_TRY(norm64(S, rhs, n, &bn));
@@ -671,15 +678,17 @@ ufg_status solve_system(ufg_solver* S, ufg_field* f, int op, const double* rhs, 
     cudaError_t e = launch_to_f32(S->r64, 1.0 / rn, (float*)V.rhs, n, S->st);
     if (e != cudaSuccess) return cuda_fail(e, "to_f32");
     note_launches(1);
-    // the inner solve asks at least what the outer target still needs
+    // the inner solve asks at least what the outer target still needs; it is capped and
+    // guarded against divergence, and a failed inner solve is never applied: the system is
+    // then finished in FP64 from the current iterate
     const double t_in = std::fmax(inner, 0.5 * tol * bn / rn);
     KrylovResult kr;
-    UFG_TRY(krylov(1, t_in, false, &kr));
+    UFG_TRY(krylov(1, t_in, false, &kr, std::min(p->maxit, 1000), 1e8));
     out->iters += kr.iters;
     out->restarts += kr.restarts;
-    if (kr.done == 4) {
-      out->done = 4;
-      return UFG_OK;
+    if (kr.done != 1) {
+      out->fallback = 1;
+      return fp64_solve(true);
     }
     e = launch_axpy_f32_to_f64(x64, (const float*)V.x, rn, n, S->st);
     if (e != cudaSuccess) return cuda_fail(e, "axpy mixed");

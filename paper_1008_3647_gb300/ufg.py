@@ -78,6 +78,9 @@ _SIGS = {
                                           ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp)]),
     "ufg_lattice_destroy": (None, [_vp]),
     "ufg_lattice_coupling": (ctypes.c_double, [_vp]),
+    "ufg_lattice_autotune": (ctypes.c_int, [_vp, _vp]),
+    "ufg_lattice_launch_shape": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                ctypes.POINTER(ctypes.c_int)]),
     "ufg_field_create": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "ufg_field_update": (ctypes.c_int, [_vp, _vp, _vp]),
     "ufg_field_destroy": (None, [_vp]),
@@ -104,6 +107,7 @@ _SIGS = {
     "ufg_solve_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
                                        ctypes.POINTER(PcParams), ctypes.POINTER(Params),
                                        ctypes.POINTER(Stats), _vp]),
+    "ufg_batch_cache_clear": (None, []),
     "ufg_apply_Q_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_int, _vp, _vp, _vp, _vp]),
 }
@@ -172,6 +176,15 @@ class Lattice:
     @property
     def shape(self):
         return (self.ntau, self.nx, self.nx, self.nx)
+
+    def ufg_lattice_autotune(self):
+        _check(load().ufg_lattice_autotune(self._h, _stream()))
+        return {p: self.ufg_lattice_launch_shape(p) for p in (UFG_FP64, UFG_FP32)}
+
+    def ufg_lattice_launch_shape(self, precision=UFG_FP32):
+        c, s = ctypes.c_int(0), ctypes.c_int(0)
+        _check(load().ufg_lattice_launch_shape(self._h, precision, ctypes.byref(c), ctypes.byref(s)))
+        return c.value, s.value
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -334,8 +347,13 @@ class Solver:
         return S.value, X, st.as_dict()
 
 
+def ufg_batch_cache_clear():
+    load().ufg_batch_cache_clear()
+
+
 def ufg_solve_batch(problems, pc_kind="wce", pc=None, **kw):
-    """problems: list of dicts with nx, ntau, tau, g, sigma, b, x (CUDA float64 tensors)."""
+    """problems: list of dicts with nx, ntau, tau, g, sigma, b, x (float64 tensors, CUDA or host
+    memory; host tensors are staged by the library)."""
     lib = load()
     arr = (Problem * len(problems))()
     for i, pr in enumerate(problems):

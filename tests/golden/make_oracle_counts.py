@@ -37,10 +37,11 @@ def main(seeds=(0, 1, 2), nx=8, ntau=64, tol=1e-10):
         sigma, b = field_and_source(nx, ntau, seed)
         for name, (kind, pc) in METHODS.items():
             fn = O.solve_cg_normal if kind == "cg" else O.solve_bicgstab_two_step
+            O.bicgstab.last_restarts = 0
             _, info = fn(lat, sigma, b, tol, 20000, pc)
             out["runs"]["%s/%d" % (name, seed)] = {
                 "iterations": info["iterations"], "steps": info.get("iterations_step"),
-                "converged": info["converged"]}
+                "converged": info["converged"], "restarts": info.get("restarts", 0)}
             print(name, seed, info["iterations"], info.get("iterations_step"), flush=True)
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_counts_8x64.json")
     with open(path, "w") as f:

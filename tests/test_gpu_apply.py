@@ -120,3 +120,19 @@ def test_invalid_arguments_rejected(ufg):
     with pytest.raises(ufg.UfgError) as e:  # in place (x aliases y) is rejected
         ufg.ufg_apply_M(field, x, x)
     assert e.value.status == ufg.UFG_INVALID_ARG
+
+
+@pytest.mark.parametrize("nx,ntau", [(8, 64), (16, 40), (32, 8)])
+def test_autotuned_launch_shape_keeps_parity(ufg, nx, ntau):
+    lat = ufg.Lattice(nx, ntau)
+    shapes = lat.ufg_lattice_autotune()
+    for prec, (C, spc) in shapes.items():
+        assert C in (1, 2, 4) and spc in (1, 2, 4, 8)
+    sigma, x = field_and_source(nx, ntau, 77)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    olat = O.Lattice(nx, ntau)
+    for dtype in (torch.float64, torch.float32):
+        xd = torch.from_numpy(x).to("cuda", dtype)
+        for fn, ref_fn in [("ufg_apply_M", O.apply_M), ("ufg_apply_Mdag", O.apply_Mdag)]:
+            y = getattr(ufg, fn)(field, xd).double().cpu().numpy()
+            assert _rel(y, ref_fn(olat, sigma, xd.double().cpu().numpy())) < TOL[dtype]

@@ -46,8 +46,11 @@ def test_uneven_batch_converges_and_matches_solo(ufg, precision):
         field = ufg.Field(lat, pr["sigma"])
         xs, ss = solver.ufg_solve_bicgstab_two_step(field, pr["b"], tol=1e-10, precision=prec)
         assert ss["status"] == ufg.UFG_OK
-        if precision == "fp64":
-            assert abs(ss["iterations"] - st["iterations"]) <= 2
+        if precision == "fp64" and ss["restarts"] == 0 and st["restarts"] == 0:
+            # same algorithm, reduction trees differ only in tiling: counts agree; after a
+            # near-breakdown restart the count depends on rounding and is not compared
+            assert abs(ss["iterations"] - st["iterations"]) <= 1, (
+                ss["iterations_step"], st["iterations_step"])
         assert float((xs - pr["x"]).norm() / xs.norm()) < 1e-7
 
 
@@ -57,7 +60,8 @@ def test_batch_96_problems_shapes(ufg):
     assert {s[0] for s in shapes} <= {6, 8, 10, 12} and {s[1] for s in shapes} <= {40, 80, 120, 160}
     probs = _problems(shapes)
     stats = ufg.ufg_solve_batch(probs, "wce", {"order": 2}, tol=1e-10, precision=ufg.UFG_MIXED)
-    assert all(st["status"] == ufg.UFG_OK for st in stats)
+    bad = [(i, shapes[i], st) for i, st in enumerate(stats) if st["status"] != ufg.UFG_OK]
+    assert not bad, bad[:3]
     # spot-check a few problems with the oracle's residual (the biggest and two others)
     for i in sorted(range(96), key=lambda i: -shapes[i][0] ** 3 * shapes[i][1])[:1] + [0, 50]:
         pr = probs[i]
