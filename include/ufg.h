@@ -141,7 +141,9 @@ double ufg_lattice_coupling(const ufg_lattice* lat);
  * read back by later processes.  Allocates and frees three temporary vectors; call it before any
  * stream capture.  Synchronises stream. */
 ufg_status ufg_lattice_autotune(ufg_lattice* lat, void* stream);
-/* The launch shape in use for a precision (UFG_FP64 / UFG_FP32). */
+/* The launch shape in use for a precision (UFG_FP64 / UFG_FP32): C = 0 means the TMA-staged
+ * kernel (one time slice per CTA or cluster); otherwise C CTAs per cluster and spc slices per
+ * CTA of the shared-memory-staged kernel. */
 ufg_status ufg_lattice_launch_shape(const ufg_lattice* lat, int precision, int* C, int* spc);
 
 /* Auxiliary field: copies sigma (device FP64, [N_tau][N_x]^3) and derives per site, in FP64 and

@@ -75,7 +75,7 @@ def build(verbose=False, force=False) -> str:
                 sys.stderr.write("== %s\n%s" % (os.path.basename(obj), log))
     objs = [o for o, _ in results]
     if force or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        cmd = [cc] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcuda"]
+        cmd = [cc] + ARCH + ["-shared", "-o", LIB] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -111,6 +111,7 @@ ufg_status slice(Batch& B, Group& g, SliceCall c, int exec_if) {
   c.ntiles = g.ntiles;
   c.probs = B.probs;
   c.exec_if = exec_if;
+  c.nelem = B.S;
   if (c.partials) c.partials += 2 * (size_t)g.cta_base;
   note_launches(1);
   cudaError_t e = slice_dispatch(g.lat->nx, c, B.st);
@@ -543,11 +544,13 @@ ufg_status setup(Batch& B, int n, const ufg_problem* probs) {
     return (long long)probs[a].nx * probs[a].nx * probs[a].nx * probs[a].ntau >
            (long long)probs[b].nx * probs[b].nx * probs[b].nx * probs[b].ntau;
   });
+  // arena offsets padded to 256 elements: every problem starts on a row of the TMA views
   B.off.assign(n, 0);
   long long o = 0;
   for (int i : order) {
     B.off[i] = o;
     o += (long long)probs[i].nx * probs[i].nx * probs[i].nx * probs[i].ntau;
+    o = (o + 255) / 256 * 256;
   }
   B.S = o;
   // groups by (N_x, tau)

@@ -178,6 +178,8 @@ static ufg_status build_tables(ufg_lattice* L) {
       }
   UFG_TRY(dev_alloc(&L->bk64, (size_t)L->V));
   UFG_TRY(dev_alloc(&L->bk32, (size_t)L->V));
+  UFG_TRY(dev_alloc(&L->dev_err, 1));
+  UFG_CUDA(cudaMemset(L->dev_err, 0, sizeof(int)));
   UFG_CUDA(cudaMemcpy(L->bk64, bk.data(), bk.size() * sizeof(double), cudaMemcpyHostToDevice));
   UFG_CUDA(cudaMemcpy(L->bk32, bkf.data(), bkf.size() * sizeof(float), cudaMemcpyHostToDevice));
   return UFG_OK;
@@ -209,6 +211,8 @@ SliceCall base_call(const ufg_lattice* lat, int fam, int prec) {
   c.ntau = lat->ntau;
   c.spc = lat->spc[prec];
   c.C = lat->C[prec];
+  c.err = lat->dev_err;
+  c.allow_tma = lat->use_tma[prec];
   return c;
 }
 
@@ -366,6 +370,7 @@ void ufg_lattice_destroy(ufg_lattice* L) {
   if (!L) return;
   dev_free(L->bk64);
   dev_free(L->bk32);
+  dev_free(L->dev_err);
   delete L;
 }
 
@@ -578,11 +583,15 @@ extern "C" ufg_status ufg_lattice_autotune(ufg_lattice* L, void* stream) {
     std::snprintf(key, sizeof(key), "%s %d %d %d", device_name().c_str(), N, L->ntau, prec);
     int C = 0, spc = 0;
     if (lookup(key, &C, &spc)) {
-      L->C[prec] = C;
-      L->spc[prec] = spc;
+      L->use_tma[prec] = C == 0;
+      if (C > 0) {
+        L->C[prec] = C;
+        L->spc[prec] = spc;
+      }
       continue;
     }
     std::vector<std::pair<int, int>> cand;
+    cand.emplace_back(0, 1);  // (0, 1): the TMA-staged kernel (where it applies)
     const size_t es = prec ? 4 : 8;
     const int cs[] = {1, 2, 4};
     for (int c : cs) {
@@ -616,8 +625,9 @@ extern "C" ufg_status ufg_lattice_autotune(ufg_lattice* L, void* stream) {
     std::pair<int, int> bestc = {L->C[prec], L->spc[prec]};
     for (auto& cd : cand) {
       SliceCall c = base_call(L, FAM_KIN, prec);
-      c.C = cd.first;
-      c.spc = cd.second;
+      c.allow_tma = cd.first == 0;
+      c.C = cd.first == 0 ? L->C[prec] : cd.first;
+      c.spc = cd.first == 0 ? L->spc[prec] : cd.second;
       c.in = x;
       c.pre = w;
       c.id = x;
@@ -647,8 +657,13 @@ extern "C" ufg_status ufg_lattice_autotune(ufg_lattice* L, void* stream) {
     cudaFree(x);
     cudaFree(y);
     cudaFree(w);
-    L->C[prec] = bestc.first;
-    L->spc[prec] = bestc.second;
+    if (bestc.first == 0) {
+      L->use_tma[prec] = 1;
+    } else {
+      L->use_tma[prec] = 0;
+      L->C[prec] = bestc.first;
+      L->spc[prec] = bestc.second;
+    }
     store(key, bestc.first, bestc.second);
   }
   return UFG_OK;
@@ -660,7 +675,7 @@ extern "C" ufg_status ufg_lattice_launch_shape(const ufg_lattice* L, int precisi
     set_error("launch_shape: bad arguments");
     return UFG_INVALID_ARG;
   }
-  *C = L->C[precision];
+  *C = L->use_tma[precision] ? 0 : L->C[precision];
   *spc = L->spc[precision];
   return UFG_OK;
 }

@@ -50,6 +50,10 @@ struct SliceCall {
   const BatchProb* probs = nullptr;  // batched mode: problem table (device)
   int ntiles = 0;
   int scale_by_A = 0;          // batched mode: multiply a by the problem's coupling A
+  long long nelem = 0;         // elements of the arenas (0: ntau * N^3, a single problem)
+  int* err = nullptr;          // device flag raised if a bounded wait ran out
+  int allow_tma = 1;           // 0 forces the non-TMA kernel
+  int* grid_out = nullptr;     // receives the number of CTAs launched (= partial pairs written)
   int ntau = 0;
   int shift = 0;               // -1: t_in = t_out - 1, +1: t_in = t_out + 1, 0: t_in = t_out
   int spc = 1;                 // time slices per CTA (cluster)

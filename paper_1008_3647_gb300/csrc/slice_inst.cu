@@ -1,11 +1,33 @@
 // Explicit instantiation of the slice kernels for one lattice extent N = UFG_N (compiled once per
 // supported N so the heavy unrolled kernels build in parallel).
+#include <cstdlib>
+
 #include "slice_kernel.cuh"
+#include "slice_tma.cuh"
 
 #ifndef UFG_N
 #error "UFG_N must be defined"
 #endif
 
 namespace ufg {
-template cudaError_t slice_launch<UFG_N>(const SliceCall& c, cudaStream_t st);
+
+static bool tma_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("UFG_NO_TMA");
+    v = (e && e[0] == '1') ? 0 : 1;
+  }
+  return v == 1;
+}
+
+// The TMA-pipelined kernel where it applies, the shared-memory-staged kernel otherwise.
+template <>
+cudaError_t slice_launch<UFG_N>(const SliceCall& c, cudaStream_t st) {
+  if (c.allow_tma && tma_enabled()) {
+    const cudaError_t e = slice_tma_try<UFG_N>(c, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  return slice_launch_plain<UFG_N>(c, st);
+}
+
 }  // namespace ufg

@@ -345,6 +345,7 @@ inline cudaError_t launch_epi(const SliceCall& c, cudaStream_t st) {
     configured_smem = (int)smem;
   }
   const int units = c.tiles != nullptr ? c.ntiles : (c.ntau + c.spc - 1) / c.spc;
+  if (c.grid_out) *c.grid_out = units * C;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(units * C);
   cfg.blockDim = dim3(SLICE_NT);
@@ -402,7 +403,7 @@ inline cudaError_t launch_C(const SliceCall& c, cudaStream_t st) {
 }
 
 template <int N>
-cudaError_t slice_launch(const SliceCall& c, cudaStream_t st) {
+cudaError_t slice_launch_plain(const SliceCall& c, cudaStream_t st) {
   if (c.prec == 0) {
     switch (c.fam) {
       case FAM_KIN: return launch_C<N, double, FAM_KIN>(c, st);

@@ -1,0 +1,466 @@
+// TMA-staged form of the slice kernel for the shapes whose rows are one 64- or 128-byte swizzle
+// span (FP32 N = 16, 32; FP64 N = 8, 16).
+//
+// Each CTA (or cluster of C CTAs splitting a slice's z-planes) handles one work unit (a time
+// slice, or a (problem, slice) tile of a batch).  Its planes -- and those of the per-site load
+// multiplier w / s -- arrive in shared memory through the tensor-memory accelerator
+// (cp.async.bulk.tensor, one box per operand, 128B/64B swizzle) completing on an mbarrier, with no
+// thread instructions spent on the copy.  The three line passes and the epilogue are those of
+// slice_kernel.cuh; shared memory is addressed through the swizzle instead of padding, which
+// keeps every pass free of bank conflicts:
+//   x-pass: a thread owns a row and reads it as 16-byte chunks, chunk c of row r stored at
+//           c ^ f(r) (f(r) = r & 7 for 128-byte rows, (r >> 1) & 3 for 64-byte rows);
+//   y-, z-pass: lanes own consecutive x of one row, a permutation of the row's words.
+// Clusters of four CTAs for 32^3 FP32 slices; two or three CTAs per SM.
+#pragma once
+#include <cooperative_groups.h>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "line_ops.cuh"
+#include "slice_call.h"
+#include "slice_kernel.cuh"
+
+namespace ufg {
+
+template <int N, typename R>
+struct TmaArgs {
+  CUtensorMap tm_in;   // [rows][N] view of the input arena, box N x (N/C * N)
+  CUtensorMap tm_pre;  // same view of the per-site multiplier (when has_pre)
+  LineCoef<N, R> coef;
+  const R* bkpost;
+  R* out;
+  const R* id;
+  const R* post;
+  const R* post2;
+  const R* U;
+  const R* V;
+  const R* dotP;
+  double a, bU, cV;
+  double* partials;
+  int want_dotP, want_self;
+  const int* done;
+  int exec_if;
+  const BatchTile* tiles;
+  const BatchProb* probs;
+  int scale_by_A;
+  int ntau, shift, units, has_pre;
+  int* err;  // set on an mbarrier wait that ran out (never expected)
+};
+
+template <int N, typename R>
+struct SwzGeom {
+  static constexpr int RB = N * (int)sizeof(R);
+  static_assert(RB == 64 || RB == 128, "TMA path covers 64- and 128-byte rows");
+  // element offset of (row r, column col) in a swizzled box
+  __device__ __forceinline__ static int off(int r, int col) {
+    const int b = col * (int)sizeof(R);
+    const int f = RB == 128 ? (r & 7) : ((r >> 1) & 3);
+    return (r * RB + ((((b >> 4) ^ f)) << 4) + (b & 15)) / (int)sizeof(R);
+  }
+  // element offset of chunk c (16 bytes) of row r
+  __device__ __forceinline__ static int chunk(int r, int c) {
+    const int f = RB == 128 ? (r & 7) : ((r >> 1) & 3);
+    return (r * RB + ((c ^ f) << 4)) / (int)sizeof(R);
+  }
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_rows(void* dst, const CUtensorMap* tm, int row,
+                                              uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(row), "r"(smem_addr(bar))
+      : "memory");
+}
+
+constexpr int TMA_NT = 256;
+constexpr uint32_t TMA_WAIT_LIMIT = 1u << 22;  // try_wait rounds before giving up (< 1 s)
+
+// Resident CTAs per SM the register allocation must allow.
+template <int N, typename R>
+constexpr int tma_min_blocks() {
+  return (N == 32 && sizeof(R) == 4) ? 3 : (N <= 8 ? 3 : 2);
+}
+
+// One work unit per CTA (a persistent loop would make the compiler hoist the ~500 line-operator
+// coefficients out of it into registers); several CTAs per SM overlap one another's TMA loads,
+// line passes and stores.
+template <int N, typename R, int C, int FAM, int EPI>
+__global__ void __launch_bounds__(TMA_NT, (tma_min_blocks<N, R>()))
+slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
+  namespace cg = cooperative_groups;
+  using G = SwzGeom<N, R>;
+  constexpr int NP = N / C;
+  constexpr int NN = N * N;
+  constexpr int VOL = N * N * N;
+  constexpr int ROWS = NP * N;      // rows of one box
+  constexpr int BUF = ROWS * N;     // elements of one box
+  constexpr int CPR = G::RB / 16;   // 16-byte chunks per row
+  constexpr int EPC = 16 / (int)sizeof(R);
+  constexpr bool IN_SPEC = (FAM == FAM_INV);
+  constexpr bool OUT_SPEC = (FAM == FAM_FWD);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ double red[TMA_NT / 32][2];
+  __shared__ alignas(8) uint64_t bar;
+
+  const int tid = threadIdx.x;
+  const int unit = blockIdx.x / C;
+  int t_out, ntau;
+  size_t off = 0;
+  const int* done = A.done;
+  double acoef = A.a;
+  if (A.tiles != nullptr) {
+    const BatchTile tl = A.tiles[unit];
+    const BatchProb& pr = A.probs[tl.prob];
+    t_out = tl.t0;
+    ntau = pr.ntau;
+    off = (size_t)pr.off;
+    done = pr.done;
+    if (A.scale_by_A) acoef *= pr.A;
+  } else {
+    t_out = unit;
+    ntau = A.ntau;
+  }
+  if (done != nullptr && A.exec_if >= 0 && *done != A.exec_if) return;  // uniform per cluster
+  int rank = 0;
+  if constexpr (C > 1) rank = (int)cg::this_cluster().block_rank();
+  int t_in = t_out;
+  if (A.shift < 0) t_in = (t_out == 0) ? ntau - 1 : t_out - 1;
+  if (A.shift > 0) t_in = (t_out == ntau - 1) ? 0 : t_out + 1;
+  // swizzled boxes need a 1024-byte aligned destination: align the dynamic region explicitly
+  unsigned char* const base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  R* const xs = reinterpret_cast<R*>(base);
+  const R* const ws = reinterpret_cast<R*>(base) + BUF;
+
+  // ---- TMA: this CTA's planes of x (and of the load multiplier) in one box each ----
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const int row = (int)((off + (size_t)t_in * VOL + (size_t)rank * NP * NN) / N);
+    mbar_expect_tx(&bar, (uint32_t)(BUF * sizeof(R)) * (A.has_pre ? 2u : 1u));
+    tma_load_rows(xs, &A.tm_in, row, &bar);
+    if (A.has_pre) tma_load_rows(const_cast<R*>(ws), &A.tm_pre, row, &bar);
+  }
+  __syncthreads();  // the mbarrier is initialised before anyone waits on it
+  {
+    uint32_t n = 0;
+    while (!mbar_try_wait(&bar, 0u)) {
+      if (++n > TMA_WAIT_LIMIT) {
+        if (A.err != nullptr) atomicExch(A.err, 1);
+        break;
+      }
+    }
+  }
+
+  // ---- x-pass: one row per thread, read as 16-byte chunks ----
+  for (int r = tid; r < ROWS; r += TMA_NT) {
+    R v[N];
+#pragma unroll
+    for (int c = 0; c < CPR; ++c) {
+      const int o = G::chunk(r, c);
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) v[c * EPC + e] = xs[o + e];
+      if (A.has_pre) {
+#pragma unroll
+        for (int e = 0; e < EPC; ++e) v[c * EPC + e] *= ws[o + e];
+      }
+    }
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef, [&](int i, R val) { xs[G::off(r, i)] = val; });
+  }
+  __syncthreads();
+  // ---- y-pass ----
+  for (int l = tid; l < NP * N; l += TMA_NT) {
+    const int p = l / N, x = l - (l / N) * N;
+    R v[N];
+#pragma unroll
+    for (int y = 0; y < N; ++y) v[y] = xs[G::off(p * N + y, x)];
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef,
+                                     [&](int i, R val) { xs[G::off(p * N + i, x)] = val; });
+  }
+  if constexpr (C > 1) {
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+  const R* owner[C];
+#pragma unroll
+  for (int o = 0; o < C; ++o) {
+    if constexpr (C > 1) {
+      owner[o] = (o == rank) ? xs : cg::this_cluster().map_shared_rank(xs, o);
+    } else {
+      owner[o] = xs;
+    }
+  }
+  // ---- z-pass + epilogue ----
+  constexpr int COLS = NN / C;
+  R sgn = R(1);
+  if (A.shift < 0 && t_out != 0) sgn = R(-1);
+  if (A.shift > 0 && t_out != ntau - 1) sgn = R(-1);
+  const R* gid = A.id ? A.id + off : nullptr;
+  const R* gpost = A.post ? A.post + off : nullptr;
+  const R* gpost2 = A.post2 ? A.post2 + off : nullptr;
+  const R* gU = A.U ? A.U + off : nullptr;
+  const R* gV = A.V ? A.V + off : nullptr;
+  const R* gdot = A.dotP ? A.dotP + off : nullptr;
+  R* gout = A.out + off;
+  double acc_dot = 0.0, acc_self = 0.0;
+  for (int l = tid; l < COLS; l += TMA_NT) {
+    const int q = rank * COLS + l;
+    const int y = q / N, x = q - (q / N) * N;
+    R v[N];
+#pragma unroll
+    for (int z = 0; z < N; ++z) v[z] = owner[z / NP][G::off((z % NP) * N + y, x)];
+    const size_t obase = (size_t)t_out * VOL + q;
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef, [&](int zp, R val) {
+      const size_t g = obase + (size_t)zp * NN;
+      R b = sgn * val;
+      if constexpr (EPI == EPI_ANY || (EPI & E_UV)) {
+        if (A.bkpost != nullptr) b *= A.bkpost[zp * NN + q];
+        if (gpost != nullptr) b *= gpost[g];
+        if (gpost2 != nullptr) b *= gpost2[g];
+        if (gid != nullptr) b += gid[g];
+        R o = R(acoef) * b;
+        if (gU != nullptr) o += R(A.bU) * gU[g];
+        if (gV != nullptr) o += R(A.cV) * gV[g];
+        gout[g] = o;
+        if (A.want_dotP) acc_dot += (double)o * (double)gdot[g];
+        if (A.want_self) acc_self += (double)o * (double)o;
+      } else {
+        const R* __restrict__ rid = gid;
+        const R* __restrict__ rpost = gpost;
+        const R* __restrict__ rpost2 = gpost2;
+        const R* __restrict__ rdot = gdot;
+        R* __restrict__ rout = gout;
+        if constexpr (EPI & E_BK) b *= __ldg(A.bkpost + zp * NN + q);
+        if constexpr (EPI & E_POST) b *= __ldg(rpost + g);
+        if constexpr (EPI & E_POST2) b *= __ldg(rpost2 + g);
+        if constexpr (EPI & E_ID) b += __ldg(rid + g);
+        const R o = R(acoef) * b;
+        rout[g] = o;
+        if constexpr (EPI & E_DOT) {
+          if (A.want_dotP) acc_dot += (double)o * (double)__ldg(rdot + g);
+          if (A.want_self) acc_self += (double)o * (double)o;
+        }
+      }
+    });
+  }
+  if (A.want_dotP || A.want_self) {  // one partial pair per CTA, indexed like the plain kernel
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+      acc_dot += __shfl_xor_sync(0xffffffffu, acc_dot, o2);
+      acc_self += __shfl_xor_sync(0xffffffffu, acc_self, o2);
+    }
+    if ((tid & 31) == 0) {
+      red[tid >> 5][0] = acc_dot;
+      red[tid >> 5][1] = acc_self;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double d = 0.0, q2 = 0.0;
+      for (int w = 0; w < TMA_NT / 32; ++w) {
+        d += red[w][0];
+        q2 += red[w][1];
+      }
+      A.partials[2 * blockIdx.x] = d;
+      A.partials[2 * blockIdx.x + 1] = q2;
+    }
+  }
+  if constexpr (C > 1) cg::this_cluster().sync();  // peers may still read this CTA's planes
+}
+
+}  // namespace ufg
+
+namespace ufg {
+
+// cuTensorMapEncodeTiled, resolved through the runtime at first use so that loading the library
+// does not require the driver library on machines without a GPU.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+template <typename R>
+inline cudaError_t encode_rows(CUtensorMap* tm, const void* base, long long nelem, int N,
+                               int box_rows) {
+  EncodeTiledFn encode = encode_tiled_fn();
+  if (encode == nullptr) return cudaErrorNotSupported;  // falls back to the plain kernel
+  const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)(nelem / N)};
+  const cuuint64_t strides[1] = {(cuuint64_t)N * sizeof(R)};
+  const cuuint32_t box[2] = {(cuuint32_t)N, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const int rb = N * (int)sizeof(R);
+  const CUtensorMapSwizzle sw = rb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  CUresult r = encode(
+      tm, sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+      const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int N, typename R, int C, int FAM, int EPI>
+inline cudaError_t tma_launch_epi(const SliceCall& c, cudaStream_t st) {
+  constexpr int NP = N / C;
+  constexpr int ROWS = NP * N;
+  constexpr int BUF = ROWS * N;
+  TmaArgs<N, R> a;
+  std::memset(&a, 0, sizeof(a));
+  const long long nelem = c.nelem > 0 ? c.nelem : (long long)c.ntau * N * N * N;
+  cudaError_t e = encode_rows<R>(&a.tm_in, c.in, nelem, N, ROWS);
+  if (e != cudaSuccess) return cudaErrorNotSupported;
+  a.has_pre = c.pre != nullptr;
+  if (a.has_pre) {
+    e = encode_rows<R>(&a.tm_pre, c.pre, nelem, N, ROWS);
+    if (e != cudaSuccess) return cudaErrorNotSupported;
+  }
+  a.coef = *reinterpret_cast<const LineCoef<N, R>*>(c.coef);
+  a.bkpost = static_cast<const R*>(c.bkpost);
+  a.out = static_cast<R*>(c.out);
+  a.id = static_cast<const R*>(c.id);
+  a.post = static_cast<const R*>(c.post);
+  a.post2 = static_cast<const R*>(c.post2);
+  a.U = static_cast<const R*>(c.U);
+  a.V = static_cast<const R*>(c.V);
+  a.dotP = static_cast<const R*>(c.dotP);
+  a.a = c.a;
+  a.bU = c.bU;
+  a.cV = c.cV;
+  a.partials = c.partials;
+  a.want_dotP = c.want_dotP;
+  a.want_self = c.want_self;
+  a.done = c.done;
+  a.exec_if = c.exec_if;
+  a.tiles = c.tiles;
+  a.probs = c.probs;
+  a.scale_by_A = c.scale_by_A;
+  a.ntau = c.ntau;
+  a.shift = c.shift;
+  a.units = c.tiles != nullptr ? c.ntiles : c.ntau;
+  a.err = c.err;
+  const size_t smem = (size_t)(a.has_pre ? 2 : 1) * BUF * sizeof(R) + 1024;
+  auto kern = slice_tma_kernel<N, R, C, FAM, EPI>;
+  static int configured = 0;
+  if (!configured) {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(2 * BUF * sizeof(R) + 1024));
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
+    if (err != cudaSuccess) return err;
+    configured = 1;
+  }
+  const int clusters = a.units;
+  if (c.grid_out) *c.grid_out = clusters * C;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(clusters * C);
+  cfg.blockDim = dim3(TMA_NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (C > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <int N, typename R, int C, int FAM>
+inline cudaError_t tma_launch_fam(const SliceCall& c, cudaStream_t st) {
+  const int mask = (c.id ? E_ID : 0) | (c.post ? E_POST : 0) | (c.post2 ? E_POST2 : 0) |
+                   ((c.U || c.V) ? E_UV : 0) | ((c.want_dotP || c.want_self) ? E_DOT : 0) |
+                   (c.bkpost ? E_BK : 0);
+  if constexpr (FAM == FAM_KIN) {
+    switch (mask) {
+      case E_ID: return tma_launch_epi<N, R, C, FAM, E_ID>(c, st);
+      case E_ID | E_POST: return tma_launch_epi<N, R, C, FAM, E_ID | E_POST>(c, st);
+      case E_ID | E_DOT: return tma_launch_epi<N, R, C, FAM, E_ID | E_DOT>(c, st);
+      case E_ID | E_POST | E_DOT: return tma_launch_epi<N, R, C, FAM, E_ID | E_POST | E_DOT>(c, st);
+    }
+  } else if constexpr (FAM == FAM_FWD) {
+    switch (mask) {
+      case 0: return tma_launch_epi<N, R, C, FAM, 0>(c, st);
+      case E_BK: return tma_launch_epi<N, R, C, FAM, E_BK>(c, st);
+    }
+  } else {
+    switch (mask) {
+      case 0: return tma_launch_epi<N, R, C, FAM, 0>(c, st);
+      case E_POST: return tma_launch_epi<N, R, C, FAM, E_POST>(c, st);
+    }
+  }
+  return tma_launch_epi<N, R, C, FAM, EPI_ANY>(c, st);
+}
+
+// TMA path for one N: cudaErrorNotSupported when the call is outside what it covers.
+template <int N>
+inline cudaError_t slice_tma_try(const SliceCall& c, cudaStream_t st) {
+  if (c.bkpre != nullptr) return cudaErrorNotSupported;
+  if (c.prec == 1) {
+    if constexpr (N == 16 || N == 32) {
+      constexpr int C = N == 32 ? 4 : 1;
+      switch (c.fam) {
+        case FAM_KIN: return tma_launch_fam<N, float, C, FAM_KIN>(c, st);
+        case FAM_FWD: return tma_launch_fam<N, float, C, FAM_FWD>(c, st);
+        case FAM_INV: return tma_launch_fam<N, float, C, FAM_INV>(c, st);
+      }
+    }
+  } else {
+    if constexpr (N == 8 || N == 16) {
+      switch (c.fam) {
+        case FAM_KIN: return tma_launch_fam<N, double, 1, FAM_KIN>(c, st);
+        case FAM_FWD: return tma_launch_fam<N, double, 1, FAM_FWD>(c, st);
+        case FAM_INV: return tma_launch_fam<N, double, 1, FAM_INV>(c, st);
+      }
+    }
+  }
+  return cudaErrorNotSupported;
+}
+
+}  // namespace ufg

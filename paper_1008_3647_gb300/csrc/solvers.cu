@@ -73,11 +73,6 @@ cudaError_t sdisp(int nx, const SliceCall& c, cudaStream_t st) {
 
 double* slot(ufg_solver* S, int k) { return S->parts + (size_t)k * 2 * MAX_PARTIAL_CTAS; }
 
-int slice_grid(const ufg_lattice* L, int prec) {
-  const int units = (L->ntau + L->spc[prec] - 1) / L->spc[prec];
-  return units * L->C[prec];
-}
-
 // ---- operator applications with epilogues --------------------------------------------------
 // out = a * (A in) + bU * U   with partials (out . dotP, out . out) into `part` when requested.
 ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const void* in, void* out,
@@ -121,8 +116,10 @@ ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const v
   c.want_self = self;
   c.partials = part;
   c.done = done;
-  if (nparts) *nparts = slice_grid(L, prec);
+  int launched = 0;
+  c.grid_out = &launched;
   cudaError_t e = sdisp(L->nx, c, S->st);
+  if (nparts) *nparts = launched;
   if (e != cudaSuccess) return cuda_fail(e, "slice kernel");
   return UFG_OK;
 }

@@ -85,8 +85,10 @@ struct ufg_lattice {
   std::vector<unsigned char> coef[3][2];   // reduced line matrices [family][0 FP64 / 1 FP32]
   double* bk64 = nullptr;                  // per-mode exp(-tau E(k)), spectral layout [V]
   float* bk32 = nullptr;
+  int* dev_err = nullptr;                  // device flag of bounded waits that ran out
   int spc[2] = {1, 1};                     // slices per CTA (KIN family) per precision
   int C[2] = {1, 1};                       // cluster size per precision
+  int use_tma[2] = {1, 1};                 // TMA-staged slice kernel where it applies
   int device = 0;
 };
 

@@ -127,7 +127,7 @@ def test_autotuned_launch_shape_keeps_parity(ufg, nx, ntau):
     lat = ufg.Lattice(nx, ntau)
     shapes = lat.ufg_lattice_autotune()
     for prec, (C, spc) in shapes.items():
-        assert C in (1, 2, 4) and spc in (1, 2, 4, 8)
+        assert C in (0, 1, 2, 4) and spc in (1, 2, 4, 8)
     sigma, x = field_and_source(nx, ntau, 77)
     field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
     olat = O.Lattice(nx, ntau)
