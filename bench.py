@@ -233,7 +233,9 @@ def run_ufg(args, rank, world, local_rank):
             stats.append(st)
         return stats
 
-    def timed(nsteps, fn):
+    def timed(nsteps, fn, name):
+        """Device time of nsteps calls of fn; each call is one NVTX range `name` (so that a
+        profiler can select the launches of one timed region)."""
         total = 0.0
         for _ in range(nsteps):
             flush.fill_(1.0)  # evict L2 between steps (outside the timed window)
@@ -241,9 +243,11 @@ def run_ufg(args, rank, world, local_rank):
                 dist.barrier()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push(name)
             e0.record(stream)
             fn()
             e1.record(stream)
+            torch.cuda.nvtx.range_pop()
             torch.cuda.synchronize()
             total += e0.elapsed_time(e1) / 1e3
         return max_over_ranks(total, world, dev)
@@ -258,15 +262,17 @@ def run_ufg(args, rank, world, local_rank):
     stats_box = {}
     with ClockSampler(local_rank) as clk:
         t_mixed = timed(args.steps,
-                        lambda: stats_box.__setitem__("mixed", step_batch(ufg.UFG_MIXED)))
+                        lambda: stats_box.__setitem__("mixed", step_batch(ufg.UFG_MIXED)),
+                        "step_mixed")
     launches = ufg.ufg_kernel_launches() - launches0
     clocks = clk.summary()
-    t_e2e = timed(args.steps, lambda: step_batch(ufg.UFG_MIXED, host=True))
+    t_e2e = timed(args.steps, lambda: step_batch(ufg.UFG_MIXED, host=True), "step_e2e")
     n64 = max(1, min(args.steps, 2))
-    t_fp64 = timed(n64, lambda: stats_box.__setitem__("fp64", step_batch(ufg.UFG_FP64)))
+    t_fp64 = timed(n64, lambda: stats_box.__setitem__("fp64", step_batch(ufg.UFG_FP64)),
+                   "step_fp64")
     # the same problems one at a time through the single-problem entry point
     step(ufg.UFG_MIXED)
-    t_solo = timed(1, lambda: step(ufg.UFG_MIXED))
+    t_solo = timed(1, lambda: step(ufg.UFG_MIXED), "step_solo")
 
     solves = PER_RANK * world
     value = solves * args.steps / t_mixed

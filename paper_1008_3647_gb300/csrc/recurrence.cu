@@ -41,37 +41,41 @@ cudaError_t launch_potentials(const double* sigma, double A, long long S, double
 // which is the frequency-space diagonal [1 - exp(-i omega - tau E(k))]^{-1} of Sec. 3 written in
 // imaginary time.  M0^{-T} runs the same recurrence backwards in t.
 //
-// Layout: block = 32 modes (lanes, coalesced) x nch time chunks (warps).  Each thread keeps its
-// chunk (<= LMAX slices) in registers: pass 1 forms the chunk's zero-start end value, one lane
-// per mode folds the chunks to the closed boundary value and each chunk's incoming state, pass 2
-// replays the chunk from registers and writes.  One HBM read and one write per element.
+// Layout: block = 32 modes (lanes, coalesced 128/256-byte rows) x REC_NCH time chunks (warps).
+// Pass 1 streams the thread's chunk and forms its zero-start end value e and the propagator
+// p = b^len; one warp folds the REC_NCH chunk pairs into the closed boundary value and each chunk's
+// incoming state; pass 2 streams the chunk again (a re-read served from L2: a block's 32 modes x
+// N_tau elements were read microseconds earlier), continues the recurrence and writes.  Nothing
+// is held in registers across the passes, so eight 256-thread blocks fit on an SM and a batch of
+// 8 x 16^3 x 256 sites (1024 blocks) runs as a single wave; N_tau is unbounded.
+constexpr int REC_NCH = 8;
+
 template <typename R>
 struct RecArgs {
   const R* in;
   R* out;
   const R* bk;
   long long V;
-  int ntau, len, transpose;
+  int ntau, transpose;
   double out_scale;
   R* acc;
   double acc_coef;
-  int acc_mode;
+  int acc_mode;             // 0: none, 1: acc = coef x, 2: acc += coef x
   const int* done;
   int exec_if;
   const int2* tiles;        // batched mode: (problem, 32-mode block) per CTA
   const BatchProb* probs;
 };
 
-template <typename R, int LMAX>
-__global__ void recurrence_kernel(const RecArgs<R> a) {
-  __shared__ R Es[32][33];
-  __shared__ R Ps[32][33];
-  __shared__ R Is[32][33];
+template <typename R, int ACC, bool OUT>  // ACC = acc_mode; OUT: write out
+__global__ void __launch_bounds__(32 * REC_NCH, sizeof(R) == 4 ? 8 : 5) recurrence_kernel(const RecArgs<R> a) {
+  __shared__ R Es[REC_NCH][32];
+  __shared__ R Ps[REC_NCH][32];
+  __shared__ R Is[REC_NCH][32];
   const int lane = threadIdx.x;
   const int ch = threadIdx.y;
-  const int nch = blockDim.y;
   long long V = a.V, mode;
-  int ntau = a.ntau, len = a.len;
+  int ntau = a.ntau;
   size_t off = 0;
   const int* done = a.done;
   if (a.tiles != nullptr) {
@@ -79,7 +83,6 @@ __global__ void recurrence_kernel(const RecArgs<R> a) {
     const BatchProb& pr = a.probs[tl.x];
     V = pr.V;
     ntau = pr.ntau;
-    len = (ntau + nch - 1) / nch;
     off = (size_t)pr.off;
     done = pr.done;
     mode = (long long)tl.y * 32 + lane;
@@ -87,24 +90,23 @@ __global__ void recurrence_kernel(const RecArgs<R> a) {
     mode = (long long)blockIdx.x * 32 + lane;
   }
   if (done != nullptr && a.exec_if >= 0 && *done != a.exec_if) return;
-  const R* in = a.in + off;
-  R* out = a.out ? a.out + off : nullptr;
-  R* acc = a.acc ? a.acc + off : nullptr;
   const bool active = mode < V;
   const R b = active ? a.bk[mode] : R(0);
+  const int len = (ntau + REC_NCH - 1) / REC_NCH;
   const int l0 = ch * len;
-  R y[LMAX];
+  const int n = active ? max(0, min(len, ntau - l0)) : 0;  // elements of this thread's chunk
+  // element l of the chunk sits at time t = l0 + l (forward) or N_tau - 1 - (l0 + l) (transpose)
+  const long long step = a.transpose ? -V : V;
+  const long long first =
+      n > 0 ? (a.transpose ? (long long)(ntau - 1 - l0) : (long long)l0) * V + mode : 0;
+  const R* in = a.in + off + first;  // may alias out (in-place): each element is read, then written
   R e = R(0), p = R(1);
-#pragma unroll
-  for (int i = 0; i < LMAX; ++i) {
-    const int l = l0 + i;
-    if (i < len && l < ntau && active) {
-      const int t = a.transpose ? ntau - 1 - l : l;
-      y[i] = in[(size_t)t * V + mode];
-      e = y[i] + b * e;
+  {
+    const R* q = in;
+#pragma unroll 4
+    for (int l = 0; l < n; ++l, q += step) {
+      e = *q + b * e;
       p = p * b;
-    } else {
-      y[i] = R(0);
     }
   }
   Es[ch][lane] = e;
@@ -112,79 +114,80 @@ __global__ void recurrence_kernel(const RecArgs<R> a) {
   __syncthreads();
   if (ch == 0) {
     R Z = R(0), bN = R(1);
-    for (int c = 0; c < nch; ++c) {
+#pragma unroll
+    for (int c = 0; c < REC_NCH; ++c) {
       Z = Es[c][lane] + Ps[c][lane] * Z;
       bN = bN * Ps[c][lane];
     }
-    const R xlast = Z / (R(1) + bN);
-    R state = -xlast;  // x_{-1} = -x_{N_tau-1}
-    for (int c = 0; c < nch; ++c) {
+    R state = -(Z / (R(1) + bN));  // x_{-1} = -x_{N_tau-1}
+#pragma unroll
+    for (int c = 0; c < REC_NCH; ++c) {
       Is[c][lane] = state;
       state = Es[c][lane] + Ps[c][lane] * state;
     }
   }
   __syncthreads();
   R x = Is[ch][lane];
-#pragma unroll
-  for (int i = 0; i < LMAX; ++i) {
-    const int l = l0 + i;
-    if (i < len && l < ntau && active) {
-      const int t = a.transpose ? ntau - 1 - l : l;
-      x = y[i] + b * x;
-      const size_t g = (size_t)t * V + mode;
-      if (a.acc_mode == 1) acc[g] = R(a.acc_coef) * x;
-      if (a.acc_mode == 2) acc[g] += R(a.acc_coef) * x;
-      if (out != nullptr) out[g] = R(a.out_scale) * x;
-    }
+  R* out = OUT ? a.out + off + first : nullptr;
+  R* acc = ACC ? a.acc + off + first : nullptr;
+  const R oscale = R(a.out_scale), acoef = R(a.acc_coef);
+  const R* q = in;
+#pragma unroll 4
+  for (int l = 0; l < n; ++l, q += step) {
+    x = *q + b * x;
+    if constexpr (ACC == 1) *acc = acoef * x;
+    if constexpr (ACC == 2) *acc += acoef * x;
+    if constexpr (OUT) *out = oscale * x;
+    if constexpr (ACC != 0) acc += step;
+    if constexpr (OUT) out += step;
   }
 }
 
 template <typename R>
-static cudaError_t rec_launch(const RecArgs<R>& a, int lmax, dim3 grid, dim3 block,
-                              cudaStream_t st) {
-  if (lmax == 16)
-    recurrence_kernel<R, 16><<<grid, block, 0, st>>>(a);
-  else
-    recurrence_kernel<R, 32><<<grid, block, 0, st>>>(a);
+static cudaError_t rec_launch(const RecArgs<R>& a, unsigned grid, cudaStream_t st) {
+  const dim3 blk(32, REC_NCH);
+  const bool out = a.out != nullptr;
+  if (a.acc_mode != 0 && a.acc == nullptr) return cudaErrorInvalidValue;
+  switch (a.acc_mode * 2 + (out ? 1 : 0)) {
+    case 1: recurrence_kernel<R, 0, true><<<grid, blk, 0, st>>>(a); break;
+    case 2: recurrence_kernel<R, 1, false><<<grid, blk, 0, st>>>(a); break;
+    case 3: recurrence_kernel<R, 1, true><<<grid, blk, 0, st>>>(a); break;
+    case 4: recurrence_kernel<R, 2, false><<<grid, blk, 0, st>>>(a); break;
+    case 5: recurrence_kernel<R, 2, true><<<grid, blk, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;  // nothing to write
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_recurrence(int prec, const void* in, void* out, const void* bk, long long V,
                               int ntau, int transpose, double out_scale, void* acc,
                               double acc_coef, int acc_mode, const int* done, cudaStream_t st) {
-  const int lmax = ntau <= 512 ? 16 : 32;
-  const int nch = (ntau + lmax - 1) / lmax;
-  if (nch > 32) return cudaErrorInvalidValue;
-  const int len = (ntau + nch - 1) / nch;
-  dim3 block(32, nch);
-  dim3 grid((unsigned)((V + 31) / 32));
+  if (V <= 0 || ntau <= 0) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)((V + 31) / 32);
   if (prec == 0) {
-    RecArgs<double> a{(const double*)in, (double*)out, (const double*)bk, V, ntau, len, transpose,
+    RecArgs<double> a{(const double*)in, (double*)out, (const double*)bk, V, ntau, transpose,
                       out_scale, (double*)acc, acc_coef, acc_mode, done, 0, nullptr, nullptr};
-    return rec_launch(a, lmax, grid, block, st);
+    return rec_launch(a, grid, st);
   }
-  RecArgs<float> a{(const float*)in, (float*)out, (const float*)bk, V, ntau, len, transpose,
-                   out_scale, (float*)acc, acc_coef, acc_mode, done, 0, nullptr, nullptr};
-  return rec_launch(a, lmax, grid, block, st);
+  RecArgs<float> a{(const float*)in, (float*)out, (const float*)bk, V, ntau, transpose, out_scale,
+                   (float*)acc, acc_coef, acc_mode, done, 0, nullptr, nullptr};
+  return rec_launch(a, grid, st);
 }
 
 cudaError_t launch_recurrence_batch(int prec, const void* in, void* out, const void* bk,
                                     int max_ntau, int transpose, double out_scale, void* acc,
                                     double acc_coef, int acc_mode, int exec_if, const int2* tiles,
                                     int ntiles, const BatchProb* probs, cudaStream_t st) {
-  const int lmax = max_ntau <= 512 ? 16 : 32;
-  const int nch = (max_ntau + lmax - 1) / lmax;
-  if (nch > 32 || ntiles <= 0) return ntiles <= 0 ? cudaSuccess : cudaErrorInvalidValue;
-  dim3 block(32, nch);
-  dim3 grid((unsigned)ntiles);
+  (void)max_ntau;  // any N_tau: the chunk length follows each problem's own N_tau
+  if (ntiles <= 0) return cudaSuccess;
   if (prec == 0) {
-    RecArgs<double> a{(const double*)in, (double*)out, (const double*)bk, 0, 0, 0, transpose,
+    RecArgs<double> a{(const double*)in, (double*)out, (const double*)bk, 0, 0, transpose,
                       out_scale, (double*)acc, acc_coef, acc_mode, nullptr, exec_if, tiles, probs};
-    return rec_launch(a, lmax, grid, block, st);
+    return rec_launch(a, (unsigned)ntiles, st);
   }
-  RecArgs<float> a{(const float*)in, (float*)out, (const float*)bk, 0, 0, 0, transpose, out_scale,
+  RecArgs<float> a{(const float*)in, (float*)out, (const float*)bk, 0, 0, transpose, out_scale,
                    (float*)acc, acc_coef, acc_mode, nullptr, exec_if, tiles, probs};
-  return rec_launch(a, lmax, grid, block, st);
+  return rec_launch(a, (unsigned)ntiles, st);
 }
 
 // ---- strong-coupling approximation (Sec. 4) -----------------------------------------------
