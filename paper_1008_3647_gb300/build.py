@@ -33,7 +33,8 @@ def _flags(verbose=False):
                 "-I", os.path.join(ROOT, "include"), "-I", CSRC]
     if verbose:
         f += ["-Xptxas", "-v"]
-    return f
+    extra = os.environ.get("UFG_NVCC_FLAGS", "").split()
+    return f + extra
 
 
 def _jobs():

@@ -1,5 +1,6 @@
 // BLAS-1 vector kernels and single-CTA scalar kernels of the Krylov solvers (see blas.cuh).
 #include <cmath>
+#include <cstdint>
 
 #include "blas.cuh"
 #include "ufg_internal.h"
@@ -39,76 +40,152 @@ __device__ __forceinline__ void block_pair_store(double d1, double d2, double* p
   }
 }
 
-template <typename R, int OP>
+// W consecutive elements (W = 1, or 16 bytes of R) through registers.
+template <typename R, int W> struct Pack;
+template <typename R> struct Pack<R, 1> {
+  __device__ __forceinline__ static void ld(const R* p, R (&o)[1]) { o[0] = *p; }
+  __device__ __forceinline__ static void st(R* p, const R (&v)[1]) { *p = v[0]; }
+};
+template <> struct Pack<float, 4> {
+  __device__ __forceinline__ static void ld(const float* p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+  __device__ __forceinline__ static void st(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct Pack<double, 2> {
+  __device__ __forceinline__ static void ld(const double* p, double (&o)[2]) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
+  __device__ __forceinline__ static void st(double* p, const double (&v)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+
+// One BLAS-1 step on elements [i, i + W).  Per-thread partial sums d1, d2 stay in the working
+// precision (FP64 arithmetic is slow on this part and a thread sums a few dozen terms); the
+// block reduction is FP64.
+template <typename R, int OP, int W>
+__device__ __forceinline__ void vec_step(long long i, R al, R be, R om, R* a, R* b, R* c, R* d,
+                                         R* e, R* f, R& d1, R& d2) {
+  using P = Pack<R, W>;
+  R A[W], B[W], Cv[W], D[W], E[W], F[W];
+  if constexpr (OP == V_CG_UPDATE) {
+    P::ld(a + i, A); P::ld(b + i, B); P::ld(c + i, Cv); P::ld(d + i, D);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      A[k] += al * B[k];
+      Cv[k] -= al * D[k];
+      d2 += Cv[k] * Cv[k];
+    }
+    P::st(a + i, A); P::st(c + i, Cv);
+  } else if constexpr (OP == V_CG_P) {
+    P::ld(a + i, A); P::ld(b + i, B);
+#pragma unroll
+    for (int k = 0; k < W; ++k) A[k] = B[k] + be * A[k];
+    P::st(a + i, A);
+  } else if constexpr (OP == V_BI_P) {
+    P::ld(a + i, A); P::ld(b + i, B); P::ld(c + i, Cv);
+#pragma unroll
+    for (int k = 0; k < W; ++k) A[k] = B[k] + be * (A[k] - om * Cv[k]);
+    P::st(a + i, A);
+  } else if constexpr (OP == V_BI_S) {
+    P::ld(b + i, B); P::ld(c + i, Cv); P::ld(d + i, D); P::ld(e + i, E);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      A[k] = B[k] - al * Cv[k];
+      D[k] += al * E[k];
+      d2 += A[k] * A[k];
+    }
+    P::st(a + i, A); P::st(d + i, D);
+  } else if constexpr (OP == V_BI_X) {
+    P::ld(a + i, A); P::ld(b + i, B); P::ld(d + i, D); P::ld(e + i, E); P::ld(f + i, F);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      A[k] += om * B[k];
+      Cv[k] = D[k] - om * E[k];
+      d1 += F[k] * Cv[k];
+      d2 += Cv[k] * Cv[k];
+    }
+    P::st(a + i, A); P::st(c + i, Cv);
+  } else if constexpr (OP == V_DOT) {
+    if (a != nullptr) {
+      P::ld(a + i, A); P::ld(b + i, B);
+#pragma unroll
+      for (int k = 0; k < W; ++k) d1 += A[k] * B[k];
+    }
+    if (c != nullptr) {
+      P::ld(c + i, Cv); P::ld(d + i, D);
+#pragma unroll
+      for (int k = 0; k < W; ++k) d2 += Cv[k] * D[k];
+    }
+  } else if constexpr (OP == V_COPY) {
+    P::ld(b + i, B);
+    P::st(a + i, B);
+  } else if constexpr (OP == V_ZERO) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) A[k] = R(0);
+    P::st(a + i, A);
+  } else if constexpr (OP == V_ADD) {
+    P::ld(a + i, A); P::ld(b + i, B);
+#pragma unroll
+    for (int k = 0; k < W; ++k) A[k] += B[k];
+    P::st(a + i, A);
+  }
+}
+
+// VECW: every operand is 16-byte aligned and each CTA's range is a whole number of 16-byte
+// vectors (the batched tiles always are); otherwise element by element.
+template <typename R, int OP, bool VECW>
 __global__ void __launch_bounds__(VEC_NT)
 vec_kernel(long long n, const DevScalars* __restrict__ sc, R* a, R* b, R* c, R* d, R* e, R* f,
            double* part, const int4* tiles, int exec_if) {
-  long long stride = (long long)gridDim.x * VEC_NT;
-  long long i0 = (long long)blockIdx.x * VEC_NT + threadIdx.x;
+  constexpr int W = VECW ? 16 / (int)sizeof(R) : 1;
+  long long lo = 0, hi = n, step = (long long)gridDim.x * VEC_NT * W;
+  long long i0 = ((long long)blockIdx.x * VEC_NT + threadIdx.x) * W;
   if (tiles != nullptr) {  // batched: one contiguous range of one problem per CTA
     const int4 tl = tiles[blockIdx.x];
     sc = sc + tl.x;
-    i0 = (long long)tl.y + threadIdx.x;
-    n = (long long)tl.y + tl.z;
-    stride = VEC_NT;
+    lo = tl.y;
+    hi = (long long)tl.y + tl.z;
+    i0 = lo + (long long)threadIdx.x * W;
+    step = (long long)VEC_NT * W;
   }
   if (sc != nullptr && exec_if >= 0 && sc->done != exec_if) return;
-  double d1 = 0.0, d2 = 0.0;
-  if constexpr (OP == V_CG_UPDATE) {
-    const R al = (R)sc->alpha;
-    for (long long i = i0; i < n; i += stride) {
-      a[i] += al * b[i];
-      const R r = c[i] - al * d[i];
-      c[i] = r;
-      d2 += (double)r * (double)r;
-    }
-  } else if constexpr (OP == V_CG_P) {
-    const R be = (R)sc->beta;
-    for (long long i = i0; i < n; i += stride) a[i] = b[i] + be * a[i];
-  } else if constexpr (OP == V_BI_P) {
-    const R be = (R)sc->beta, om = (R)sc->omega;
-    for (long long i = i0; i < n; i += stride) a[i] = b[i] + be * (a[i] - om * c[i]);
-  } else if constexpr (OP == V_BI_S) {
-    const R al = (R)sc->alpha;
-    for (long long i = i0; i < n; i += stride) {
-      const R s = b[i] - al * c[i];
-      a[i] = s;
-      d[i] += al * e[i];
-      d2 += (double)s * (double)s;
-    }
-  } else if constexpr (OP == V_BI_X) {
-    const R om = (R)sc->omega;
-    for (long long i = i0; i < n; i += stride) {
-      a[i] += om * b[i];
-      const R r = d[i] - om * e[i];
-      c[i] = r;
-      d1 += (double)f[i] * (double)r;
-      d2 += (double)r * (double)r;
-    }
-  } else if constexpr (OP == V_DOT) {
-    for (long long i = i0; i < n; i += stride) {
-      if (a != nullptr) d1 += (double)a[i] * (double)b[i];
-      if (c != nullptr) d2 += (double)c[i] * (double)d[i];
-    }
-  } else if constexpr (OP == V_COPY) {
-    for (long long i = i0; i < n; i += stride) a[i] = b[i];
-  } else if constexpr (OP == V_ZERO) {
-    for (long long i = i0; i < n; i += stride) a[i] = R(0);
-  } else if constexpr (OP == V_ADD) {
-    for (long long i = i0; i < n; i += stride) a[i] += b[i];
-  }
-  if (part != nullptr) block_pair_store(d1, d2, part);
+  R al = R(0), be = R(0), om = R(0);
+  if constexpr (OP == V_CG_UPDATE || OP == V_BI_S) al = (R)sc->alpha;
+  if constexpr (OP == V_CG_P || OP == V_BI_P) be = (R)sc->beta;
+  if constexpr (OP == V_BI_P || OP == V_BI_X) om = (R)sc->omega;
+  R d1 = R(0), d2 = R(0);
+#pragma unroll 2
+  for (long long i = i0; i < hi; i += step)
+    vec_step<R, OP, W>(i, al, be, om, a, b, c, d, e, f, d1, d2);
+  if (part != nullptr) block_pair_store((double)d1, (double)d2, part);
 }
 
 template <typename R>
 static cudaError_t vec_dispatch(int op, long long n, const DevScalars* sc, R* a, R* b, R* c, R* d,
                                 R* e, R* f, double* part, int grid, cudaStream_t st,
                                 const int4* tiles = nullptr, int exec_if = 0) {
+  // 16-byte vectors when every operand is aligned and the ranges split into whole vectors
+  // (batched tiles start on 256-element boundaries and have lengths divisible by 8)
+  const uintptr_t al = reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
+                       reinterpret_cast<uintptr_t>(c) | reinterpret_cast<uintptr_t>(d) |
+                       reinterpret_cast<uintptr_t>(e) | reinterpret_cast<uintptr_t>(f);
+  const long long wv = 16 / (long long)sizeof(R);
+  const bool vecw = (al & 15u) == 0 && (tiles != nullptr || n % wv == 0);
   switch (op) {
-#define CASE(OPC)                                                                         \
-  case OPC:                                                                               \
-    vec_kernel<R, OPC><<<grid, VEC_NT, 0, st>>>(n, sc, a, b, c, d, e, f, part, tiles,     \
-                                                exec_if);                                 \
+#define CASE(OPC)                                                                          \
+  case OPC:                                                                                \
+    if (vecw)                                                                              \
+      vec_kernel<R, OPC, true><<<grid, VEC_NT, 0, st>>>(n, sc, a, b, c, d, e, f, part, tiles, \
+                                                        exec_if);                          \
+    else                                                                                   \
+      vec_kernel<R, OPC, false><<<grid, VEC_NT, 0, st>>>(n, sc, a, b, c, d, e, f, part,     \
+                                                         tiles, exec_if);                  \
     break;
     CASE(V_CG_UPDATE)
     CASE(V_CG_P)
@@ -150,20 +227,39 @@ cudaError_t launch_vec_batch(int prec, int op, const int4* tiles, int ntiles, co
 }
 
 // ---- scalar kernels ------------------------------------------------------------------------
-__device__ double block_sum(const double* part, int nparts, int k, int i0 = 0) {
-  __shared__ double red[VEC_NT];
-  double s = 0.0;
+// The four sums (pairs [i0, i1) of part, pairs [j0, j1) of part2) in one sweep: each thread adds
+// its strided share, the warps fold with shuffles and thread 0 adds the warp results in order
+// (a fixed, launch-independent order: the result is deterministic).  Valid in thread 0.
+__device__ void block_sums4(const double* part, int i0, int i1, const double* part2, int j0,
+                            int j1, double (&out)[4]) {
+  __shared__ double red[VEC_NT / 32][4];
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
   if (part != nullptr)
-    for (int i = i0 + threadIdx.x; i < nparts; i += VEC_NT) s += part[2 * i + k];
-  red[threadIdx.x] = s;
+    for (int i = i0 + (int)threadIdx.x; i < i1; i += VEC_NT) {
+      s[0] += part[2 * i];
+      s[1] += part[2 * i + 1];
+    }
+  if (part2 != nullptr)
+    for (int i = j0 + (int)threadIdx.x; i < j1; i += VEC_NT) {
+      s[2] += part2[2 * i];
+      s[3] += part2[2 * i + 1];
+    }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], off);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[threadIdx.x >> 5][k] = s[k];
   __syncthreads();
-  for (int w = VEC_NT / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double t = 0.0;
+      for (int w = 0; w < VEC_NT / 32; ++w) t += red[w][k];
+      out[k] = t;
+    }
   }
-  const double r = red[0];
-  __syncthreads();
-  return r;
 }
 
 __device__ __forceinline__ bool bad(double v) { return !isfinite(v); }
@@ -176,12 +272,10 @@ scalar_kernel(int op, DevScalars* sc, const double* part, int nparts, const doub
               int nparts2) {
   if (op != OP_CG_INIT && op != OP_BI_INIT && sc->done) return;
   // every thread takes part in the block sums; thread 0 then updates the scalars
-  const double a0 = block_sum(part, nparts, 0);
-  const double a1 = block_sum(part, nparts, 1);
-  const double b0 = block_sum(part2, nparts2, 0);
-  const double b1 = block_sum(part2, nparts2, 1);
+  double r[4];
+  block_sums4(part, 0, nparts, part2, 0, nparts2, r);
   if (threadIdx.x != 0) return;
-  scalar_update(op, sc, part, a0, a1, part2, b0, b1);
+  scalar_update(op, sc, part, r[0], r[1], part2, r[2], r[3]);
 }
 
 __global__ void __launch_bounds__(VEC_NT)
@@ -192,12 +286,10 @@ scalar_batch_kernel(int op, DevScalars* scs, const BatchProb* probs, const doubl
   if (exec_if >= 0 && sc->done != exec_if) return;
   const int i0 = kind == 0 ? pr.st0 : pr.vt0, i1 = kind == 0 ? pr.st1 : pr.vt1;
   const int j0 = kind2 == 0 ? pr.st0 : pr.vt0, j1 = kind2 == 0 ? pr.st1 : pr.vt1;
-  const double a0 = block_sum(part, i1, 0, i0);
-  const double a1 = block_sum(part, i1, 1, i0);
-  const double b0 = block_sum(part2, j1, 0, j0);
-  const double b1 = block_sum(part2, j1, 1, j0);
+  double r[4];
+  block_sums4(part, i0, i1, part2, j0, j1, r);
   if (threadIdx.x != 0) return;
-  scalar_update(op, sc, part, a0, a1, part2, b0, b1);
+  scalar_update(op, sc, part, r[0], r[1], part2, r[2], r[3]);
 }
 
 __device__ void scalar_update(int op, DevScalars* sc, const double* part, double a0, double a1,
@@ -324,8 +416,9 @@ cudaError_t launch_axpy_f32_to_f64(double* x, const float* e, double scale, long
 }
 
 __global__ void reduce_to_kernel(const double* part, int nparts, int k, double* out) {
-  const double s = block_sum(part, nparts, k);
-  if (threadIdx.x == 0) *out = s;
+  double r[4];
+  block_sums4(part, 0, nparts, nullptr, 0, 0, r);
+  if (threadIdx.x == 0) *out = r[k];
 }
 
 cudaError_t launch_reduce_to(const double* part, int nparts, int k, double* out, cudaStream_t st) {

@@ -34,7 +34,11 @@ namespace cg = cooperative_groups;
 
 template <int N, typename R>
 struct SliceArgs {
-  LineCoef<N, R> coef;
+  // one copy of the line operator per pass, so that the compiler does not keep all of its
+  // coefficients live in registers from the first pass to the last
+  LineCoef<N, R> coef_x;
+  LineCoef<N, R> coef_y;
+  LineCoef<N, R> coef_z;
   const R* in;
   const R* pre;
   const R* bkpre;
@@ -181,7 +185,7 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
     R v[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) v[j] = base[j];
-    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef, [&](int i, R val) { base[i] = val; });
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_x, [&](int i, R val) { base[i] = val; });
   }
   __syncthreads();
   for (int l = tid; l < nlines; l += SLICE_NT) {
@@ -190,7 +194,7 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
     R v[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) v[j] = base[j * PITCH];
-    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef, [&](int i, R val) { base[i * PITCH] = val; });
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_y, [&](int i, R val) { base[i * PITCH] = val; });
   }
   if constexpr (C > 1) {
     cg::this_cluster().sync();
@@ -209,7 +213,9 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
     }
   }
   constexpr int COLS = NN / C;
-  double acc_dot = 0.0, acc_self = 0.0;
+  // per-thread partial sums in the working precision (FP64 arithmetic is slow on this part and
+  // a thread sums at most N terms); converted to FP64 for the block reduction
+  R acc_dot = R(0), acc_self = R(0);
   const int ncols = nsl * COLS;
   for (int l = tid; l < ncols; l += SLICE_NT) {
     const int s = l / COLS;
@@ -225,7 +231,7 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
       v[z] = owner[z / NP][(s * NP + (z % NP)) * PLANE + y * PITCH + x];
     }
     const size_t obase = (size_t)t_out * VOL + q;
-    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef, [&](int zp, R val) {
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_z, [&](int zp, R val) {
       const size_t g = obase + (size_t)zp * NN;
       R b = sgn * val;
       if constexpr (EPI == EPI_ANY) {
@@ -237,8 +243,8 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
         if (gU != nullptr) o += R(A.bU) * gU[g];
         if (gV != nullptr) o += R(A.cV) * gV[g];
         gout[g] = o;
-        if (A.want_dotP) acc_dot += (double)o * (double)gdot[g];
-        if (A.want_self) acc_self += (double)o * (double)o;
+        if (A.want_dotP) acc_dot += o * gdot[g];
+        if (A.want_self) acc_self += o * o;
       } else if constexpr (EPI & E_UV) {  // U or V may alias out (in-place updates)
         if constexpr (EPI & E_BK) b *= A.bkpost[zp * NN + q];
         if constexpr (EPI & E_POST) b *= gpost[g];
@@ -249,8 +255,8 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
         if (gV != nullptr) o += R(A.cV) * gV[g];
         gout[g] = o;
         if constexpr (EPI & E_DOT) {
-          if (A.want_dotP) acc_dot += (double)o * (double)gdot[g];
-          if (A.want_self) acc_self += (double)o * (double)o;
+          if (A.want_dotP) acc_dot += o * gdot[g];
+          if (A.want_self) acc_self += o * o;
         }
       } else {  // operands never alias the output: loads may move ahead of earlier stores
         const R* __restrict__ rid = gid;
@@ -265,22 +271,23 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
         const R o = R(acoef) * b;
         rout[g] = o;
         if constexpr (EPI & E_DOT) {
-          if (A.want_dotP) acc_dot += (double)o * (double)__ldg(rdot + g);
-          if (A.want_self) acc_self += (double)o * (double)o;
+          if (A.want_dotP) acc_dot += o * __ldg(rdot + g);
+          if (A.want_self) acc_self += o * o;
         }
       }
     });
   }
 
   if (A.want_dotP || A.want_self) {
+    double pd = (double)acc_dot, ps = (double)acc_self;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      acc_dot += __shfl_xor_sync(0xffffffffu, acc_dot, off);
-      acc_self += __shfl_xor_sync(0xffffffffu, acc_self, off);
+      pd += __shfl_xor_sync(0xffffffffu, pd, off);
+      ps += __shfl_xor_sync(0xffffffffu, ps, off);
     }
     if ((tid & 31) == 0) {
-      red[tid >> 5][0] = acc_dot;
-      red[tid >> 5][1] = acc_self;
+      red[tid >> 5][0] = pd;
+      red[tid >> 5][1] = ps;
     }
     __syncthreads();
     if (tid == 0) {
@@ -298,7 +305,9 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
 
 template <int N, typename R>
 inline void fill_args(SliceArgs<N, R>& a, const SliceCall& c) {
-  a.coef = *reinterpret_cast<const LineCoef<N, R>*>(c.coef);
+  a.coef_x = *reinterpret_cast<const LineCoef<N, R>*>(c.coef);
+  a.coef_y = a.coef_x;
+  a.coef_z = a.coef_x;
   a.in = static_cast<const R*>(c.in);
   a.pre = static_cast<const R*>(c.pre);
   a.bkpre = static_cast<const R*>(c.bkpre);

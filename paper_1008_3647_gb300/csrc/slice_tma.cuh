@@ -29,7 +29,12 @@ template <int N, typename R>
 struct TmaArgs {
   CUtensorMap tm_in;   // [rows][N] view of the input arena, box N x (N/C * N)
   CUtensorMap tm_pre;  // same view of the per-site multiplier (when has_pre)
-  LineCoef<N, R> coef;
+  // The line operator once per pass: with a single copy the compiler keeps all of its
+  // coefficients in registers from the first pass to the last (118 instead of 56 registers for
+  // N = 16); separate copies stay constant-bank operands of the multiply-adds.
+  LineCoef<N, R> coef_x;
+  LineCoef<N, R> coef_y;
+  LineCoef<N, R> coef_z;
   const R* bkpost;
   R* out;
   const R* id;
@@ -47,6 +52,7 @@ struct TmaArgs {
   const BatchProb* probs;
   int scale_by_A;
   int ntau, shift, units, has_pre;
+  int pre_mode;  // the multiplier box is a per-mode table (one slice, the same for every t)
   int* err;  // set on an mbarrier wait that ran out (never expected)
 };
 
@@ -109,7 +115,7 @@ constexpr uint32_t TMA_WAIT_LIMIT = 1u << 22;  // try_wait rounds before giving 
 // Resident CTAs per SM the register allocation must allow.
 template <int N, typename R>
 constexpr int tma_min_blocks() {
-  return (N == 32 && sizeof(R) == 4) ? 3 : (N <= 8 ? 3 : 2);
+  return sizeof(R) == 4 ? (N == 16 ? 4 : 3) : (N <= 8 ? 4 : 3);
 }
 
 // One work unit per CTA (a persistent loop would make the compiler hoist the ~500 line-operator
@@ -169,7 +175,8 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
     const int row = (int)((off + (size_t)t_in * VOL + (size_t)rank * NP * NN) / N);
     mbar_expect_tx(&bar, (uint32_t)(BUF * sizeof(R)) * (A.has_pre ? 2u : 1u));
     tma_load_rows(xs, &A.tm_in, row, &bar);
-    if (A.has_pre) tma_load_rows(const_cast<R*>(ws), &A.tm_pre, row, &bar);
+    if (A.has_pre)
+      tma_load_rows(const_cast<R*>(ws), &A.tm_pre, A.pre_mode ? rank * NP * N : row, &bar);
   }
   __syncthreads();  // the mbarrier is initialised before anyone waits on it
   {
@@ -195,7 +202,7 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
         for (int e = 0; e < EPC; ++e) v[c * EPC + e] *= ws[o + e];
       }
     }
-    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef, [&](int i, R val) { xs[G::off(r, i)] = val; });
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_x, [&](int i, R val) { xs[G::off(r, i)] = val; });
   }
   __syncthreads();
   // ---- y-pass ----
@@ -204,7 +211,7 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
     R v[N];
 #pragma unroll
     for (int y = 0; y < N; ++y) v[y] = xs[G::off(p * N + y, x)];
-    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef,
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_y,
                                      [&](int i, R val) { xs[G::off(p * N + i, x)] = val; });
   }
   if constexpr (C > 1) {
@@ -233,7 +240,9 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   const R* gV = A.V ? A.V + off : nullptr;
   const R* gdot = A.dotP ? A.dotP + off : nullptr;
   R* gout = A.out + off;
-  double acc_dot = 0.0, acc_self = 0.0;
+  // per-thread partial sums in the working precision (FP64 arithmetic is slow on this part and
+  // a thread sums at most N terms); converted to FP64 for the block reduction
+  R acc_dot = R(0), acc_self = R(0);
   for (int l = tid; l < COLS; l += TMA_NT) {
     const int q = rank * COLS + l;
     const int y = q / N, x = q - (q / N) * N;
@@ -241,7 +250,7 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
 #pragma unroll
     for (int z = 0; z < N; ++z) v[z] = owner[z / NP][G::off((z % NP) * N + y, x)];
     const size_t obase = (size_t)t_out * VOL + q;
-    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef, [&](int zp, R val) {
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_z, [&](int zp, R val) {
       const size_t g = obase + (size_t)zp * NN;
       R b = sgn * val;
       if constexpr (EPI == EPI_ANY || (EPI & E_UV)) {
@@ -253,8 +262,8 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
         if (gU != nullptr) o += R(A.bU) * gU[g];
         if (gV != nullptr) o += R(A.cV) * gV[g];
         gout[g] = o;
-        if (A.want_dotP) acc_dot += (double)o * (double)gdot[g];
-        if (A.want_self) acc_self += (double)o * (double)o;
+        if (A.want_dotP) acc_dot += o * gdot[g];
+        if (A.want_self) acc_self += o * o;
       } else {
         const R* __restrict__ rid = gid;
         const R* __restrict__ rpost = gpost;
@@ -268,21 +277,22 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
         const R o = R(acoef) * b;
         rout[g] = o;
         if constexpr (EPI & E_DOT) {
-          if (A.want_dotP) acc_dot += (double)o * (double)__ldg(rdot + g);
-          if (A.want_self) acc_self += (double)o * (double)o;
+          if (A.want_dotP) acc_dot += o * __ldg(rdot + g);
+          if (A.want_self) acc_self += o * o;
         }
       }
     });
   }
   if (A.want_dotP || A.want_self) {  // one partial pair per CTA, indexed like the plain kernel
+    double pd = (double)acc_dot, ps = (double)acc_self;
 #pragma unroll
     for (int o2 = 16; o2 > 0; o2 >>= 1) {
-      acc_dot += __shfl_xor_sync(0xffffffffu, acc_dot, o2);
-      acc_self += __shfl_xor_sync(0xffffffffu, acc_self, o2);
+      pd += __shfl_xor_sync(0xffffffffu, pd, o2);
+      ps += __shfl_xor_sync(0xffffffffu, ps, o2);
     }
     if ((tid & 31) == 0) {
-      red[tid >> 5][0] = acc_dot;
-      red[tid >> 5][1] = acc_self;
+      red[tid >> 5][0] = pd;
+      red[tid >> 5][1] = ps;
     }
     __syncthreads();
     if (tid == 0) {
@@ -352,12 +362,17 @@ inline cudaError_t tma_launch_epi(const SliceCall& c, cudaStream_t st) {
   const long long nelem = c.nelem > 0 ? c.nelem : (long long)c.ntau * N * N * N;
   cudaError_t e = encode_rows<R>(&a.tm_in, c.in, nelem, N, ROWS);
   if (e != cudaSuccess) return cudaErrorNotSupported;
-  a.has_pre = c.pre != nullptr;
+  // at most one load multiplier: per site (pre) or per mode (bkpre, one slice long)
+  a.has_pre = (c.pre != nullptr || c.bkpre != nullptr) ? 1 : 0;
+  a.pre_mode = c.bkpre != nullptr ? 1 : 0;
   if (a.has_pre) {
-    e = encode_rows<R>(&a.tm_pre, c.pre, nelem, N, ROWS);
+    e = a.pre_mode ? encode_rows<R>(&a.tm_pre, c.bkpre, (long long)N * N * N, N, ROWS)
+                   : encode_rows<R>(&a.tm_pre, c.pre, nelem, N, ROWS);
     if (e != cudaSuccess) return cudaErrorNotSupported;
   }
-  a.coef = *reinterpret_cast<const LineCoef<N, R>*>(c.coef);
+  a.coef_x = *reinterpret_cast<const LineCoef<N, R>*>(c.coef);
+  a.coef_y = a.coef_x;
+  a.coef_z = a.coef_x;
   a.bkpost = static_cast<const R*>(c.bkpost);
   a.out = static_cast<R*>(c.out);
   a.id = static_cast<const R*>(c.id);
@@ -441,7 +456,7 @@ inline cudaError_t tma_launch_fam(const SliceCall& c, cudaStream_t st) {
 // TMA path for one N: cudaErrorNotSupported when the call is outside what it covers.
 template <int N>
 inline cudaError_t slice_tma_try(const SliceCall& c, cudaStream_t st) {
-  if (c.bkpre != nullptr) return cudaErrorNotSupported;
+  if (c.bkpre != nullptr && c.pre != nullptr) return cudaErrorNotSupported;
   if (c.prec == 1) {
     if constexpr (N == 16 || N == 32) {
       constexpr int C = N == 32 ? 4 : 1;
