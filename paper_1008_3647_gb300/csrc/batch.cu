@@ -186,9 +186,9 @@ ufg_status wce_b(Batch& B, int prec, const void* r, void* z, bool tr) {
   Arena& V = B.ar[prec];
   for (auto& g : B.groups) {
     const void* bk = prec ? (const void*)g.lat->bk32 : (const void*)g.lat->bk64;
-    auto rec = [&](double coef, int mode, bool write_out) -> ufg_status {
+    auto rec = [&](const void* in, double coef, int mode, bool write_out) -> ufg_status {
       note_launches(1);
-      cudaError_t e = launch_recurrence_batch(prec, V.spec, write_out ? V.spec : nullptr, bk,
+      cudaError_t e = launch_recurrence_batch(prec, in, write_out ? V.spec : nullptr, bk,
                                               g.max_ntau, tr ? 1 : 0, 1.0, V.acc, coef, mode, 0,
                                               g.rtiles, g.nrtiles, B.probs, B.st);
       if (e != cudaSuccess) return cuda_fail(e, "batched recurrence");
@@ -198,9 +198,22 @@ ufg_status wce_b(Batch& B, int prec, const void* r, void* z, bool tr) {
     fw.in = r;
     fw.out = V.spec;
     UFG_TRY(slice(B, g, fw, 0));
-    UFG_TRY(rec(cw[0], 1, d > 0));
+    UFG_TRY(rec(V.spec, cw[0], 1, d > 0));
+    const bool fused = slice_m1w_supported(g.lat->nx, prec);
     for (int nn = 1; nn <= d; ++nn) {
-      if (!tr) {
+      if (fused) {  // -A M1 (or M1^T) in momentum space in one kernel: spec -> wr
+        SliceCall m = base_call(g.lat, FAM_INV, prec);
+        m.fam = FAM_M1W;
+        m.coef2 = base_call(g.lat, FAM_FWD, prec).coef;
+        m.in = V.spec;
+        m.pre = fldb(B, 's', prec);
+        if (tr) m.bkpre = bk; else m.bkpost = bk;
+        m.shift = tr ? +1 : -1;
+        m.a = -1.0;
+        m.scale_by_A = 1;
+        m.out = V.wr;
+        UFG_TRY(slice(B, g, m, 0));
+      } else if (!tr) {
         SliceCall iv = base_call(g.lat, FAM_INV, prec);
         iv.in = V.spec;
         iv.out = V.wr;
@@ -229,7 +242,7 @@ ufg_status wce_b(Batch& B, int prec, const void* r, void* z, bool tr) {
         fw2.out = V.spec;
         UFG_TRY(slice(B, g, fw2, 0));
       }
-      UFG_TRY(rec(cw[nn], 2, nn < d));
+      UFG_TRY(rec(fused ? V.wr : V.spec, cw[nn], 2, nn < d));
     }
     SliceCall iv = base_call(g.lat, FAM_INV, prec);
     iv.in = V.acc;

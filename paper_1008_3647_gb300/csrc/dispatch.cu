@@ -10,6 +10,10 @@ bool slice_supported_n(int N) {
   return false;
 }
 
+bool slice_m1w_supported(int N, int prec) {
+  return prec == 1 ? N == 16 : (N == 8 || N == 16);
+}
+
 cudaError_t slice_dispatch(int N, const SliceCall& c, cudaStream_t st) {
   switch (N) {
     case 4: return slice_launch<4>(c, st);

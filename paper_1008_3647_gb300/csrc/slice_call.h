@@ -4,7 +4,10 @@
 
 namespace ufg {
 
-enum SliceFamily { FAM_KIN = 0, FAM_FWD = 1, FAM_INV = 2 };
+// FAM_M1W: the weak-coupling term -A M1 (Sec. 3) in momentum space, -A S^{+-1} F^T (s * F x), for
+// one slice in one kernel
+// (inverse transform, site multiplier, forward transform); coef = inverse, coef2 = forward family.
+enum SliceFamily { FAM_KIN = 0, FAM_FWD = 1, FAM_INV = 2, FAM_M1W = 3 };
 
 // Batched mode: one problem of a batch as the kernels see it (device table).
 struct BatchProb {
@@ -30,6 +33,7 @@ struct SliceCall {
   int fam = FAM_KIN;
   int prec = 0;               // 0 = FP64, 1 = FP32
   const void* coef = nullptr; // host LineCoef<N, R> for (fam, prec)
+  const void* coef2 = nullptr; // FAM_M1W: forward-transform coefficients
   const void* in = nullptr;
   const void* pre = nullptr;     // per-site load multiplier [S]
   const void* bkpre = nullptr;   // per-mode load multiplier [V]
@@ -68,5 +72,8 @@ cudaError_t slice_launch(const SliceCall& c, cudaStream_t st);
 // Runtime dispatch over the supported N (4, 6, 8, 10, 12, 16, 32).
 cudaError_t slice_dispatch(int N, const SliceCall& c, cudaStream_t st);
 bool slice_supported_n(int N);
+// Whether the fused FAM_M1W kernel exists for (N, precision): one CTA per slice with the slice
+// in 64- or 128-byte TMA rows (FP32 N = 16, FP64 N = 8 and 16).
+bool slice_m1w_supported(int N, int prec);
 
 }  // namespace ufg

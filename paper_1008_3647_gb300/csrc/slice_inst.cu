@@ -23,6 +23,7 @@ static bool tma_enabled() {
 // The TMA-pipelined kernel where it applies, the shared-memory-staged kernel otherwise.
 template <>
 cudaError_t slice_launch<UFG_N>(const SliceCall& c, cudaStream_t st) {
+  if (c.fam == FAM_M1W) return slice_m1w_try<UFG_N>(c, st);  // callers check support first
   if (c.allow_tma && tma_enabled()) {
     const cudaError_t e = slice_tma_try<UFG_N>(c, st);
     if (e != cudaErrorNotSupported) return e;

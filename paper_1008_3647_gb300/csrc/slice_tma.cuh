@@ -60,16 +60,18 @@ template <int N, typename R>
 struct SwzGeom {
   static constexpr int RB = N * (int)sizeof(R);
   static_assert(RB == 64 || RB == 128, "TMA path covers 64- and 128-byte rows");
-  // element offset of (row r, column col) in a swizzled box
-  __device__ __forceinline__ static int off(int r, int col) {
-    const int b = col * (int)sizeof(R);
-    const int f = RB == 128 ? (r & 7) : ((r >> 1) & 3);
-    return (r * RB + ((((b >> 4) ^ f)) << 4) + (b & 15)) / (int)sizeof(R);
+  static constexpr unsigned EPC = 16 / sizeof(R);  // elements per 16-byte chunk
+  // swizzle phase of row r: chunk c of the row is stored at chunk c ^ f(r)
+  __device__ __forceinline__ static unsigned f(unsigned r) {
+    return RB == 128 ? (r & 7u) : ((r >> 1) & 3u);
+  }
+  // element offset of (row r, column col) in a swizzled box (unsigned: shifts and masks only)
+  __device__ __forceinline__ static int off(unsigned r, unsigned col) {
+    return (int)(r * N + (((col / EPC) ^ f(r)) * EPC) + (col % EPC));
   }
   // element offset of chunk c (16 bytes) of row r
-  __device__ __forceinline__ static int chunk(int r, int c) {
-    const int f = RB == 128 ? (r & 7) : ((r >> 1) & 3);
-    return (r * RB + ((c ^ f) << 4)) / (int)sizeof(R);
+  __device__ __forceinline__ static int chunk(unsigned r, unsigned c) {
+    return (int)(r * N + (c ^ f(r)) * EPC);
   }
 };
 
@@ -233,6 +235,7 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   R sgn = R(1);
   if (A.shift < 0 && t_out != 0) sgn = R(-1);
   if (A.shift > 0 && t_out != ntau - 1) sgn = R(-1);
+  const R sa = sgn * R(acoef);
   const R* gid = A.id ? A.id + off : nullptr;
   const R* gpost = A.post ? A.post + off : nullptr;
   const R* gpost2 = A.post2 ? A.post2 + off : nullptr;
@@ -252,8 +255,8 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
     const size_t obase = (size_t)t_out * VOL + q;
     line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_z, [&](int zp, R val) {
       const size_t g = obase + (size_t)zp * NN;
-      R b = sgn * val;
       if constexpr (EPI == EPI_ANY || (EPI & E_UV)) {
+        R b = sgn * val;
         if (A.bkpost != nullptr) b *= A.bkpost[zp * NN + q];
         if (gpost != nullptr) b *= gpost[g];
         if (gpost2 != nullptr) b *= gpost2[g];
@@ -270,11 +273,16 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
         const R* __restrict__ rpost2 = gpost2;
         const R* __restrict__ rdot = gdot;
         R* __restrict__ rout = gout;
+        R b = val;
         if constexpr (EPI & E_BK) b *= __ldg(A.bkpost + zp * NN + q);
         if constexpr (EPI & E_POST) b *= __ldg(rpost + g);
         if constexpr (EPI & E_POST2) b *= __ldg(rpost2 + g);
-        if constexpr (EPI & E_ID) b += __ldg(rid + g);
-        const R o = R(acoef) * b;
+        R o;
+        if constexpr (EPI & E_ID) {
+          o = R(acoef) * fmadd(sgn, b, __ldg(rid + g));
+        } else {
+          o = sa * b;  // sign folded into the scale
+        }
         rout[g] = o;
         if constexpr (EPI & E_DOT) {
           if (A.want_dotP) acc_dot += o * __ldg(rdot + g);
@@ -451,6 +459,215 @@ inline cudaError_t tma_launch_fam(const SliceCall& c, cudaStream_t st) {
     }
   }
   return tma_launch_epi<N, R, C, FAM, EPI_ANY>(c, st);
+}
+
+// ---- fused WCE term: inverse transform, site multiplier, forward transform -----------------
+// One slice per CTA (C = 1).  With x the momentum-space vector, F the real Fourier basis, s the
+// per-site multiplier sin(sigma), b the per-mode kinetic factor and the time shift S:
+//   DIR 0 (the M1 term of Sec. 3):  y_t = -A sgn(t) b .* F^T( s_{t-1} .* F x_{t-1} )
+//   DIR 1 (its transpose): y_t = F^T( -A sgn(t) s_t .* F( b .* x_{t+1} ) )
+// with sgn(t) = -1 except at the antiperiodic wrap.  The inverse transform's result never leaves
+// shared memory: the z pass multiplies it by s in place and the forward passes follow.
+template <int N, typename R>
+struct M1wArgs {
+  CUtensorMap tm_in;  // momentum-space input arena
+  CUtensorMap tm_s;   // site multiplier arena
+  CUtensorMap tm_k;   // per-mode factor (one slice), DIR 1
+  LineCoef<N, R> ci_x, ci_y, ci_z;  // inverse transform, one copy per pass (see TmaArgs)
+  LineCoef<N, R> cf_x, cf_y, cf_z;  // forward transform
+  const R* bk;                      // per-mode factor, DIR 0 (applied to the output)
+  R* out;
+  double a;
+  const int* done;
+  int exec_if;
+  const BatchTile* tiles;
+  const BatchProb* probs;
+  int scale_by_A;
+  int ntau;
+  int* err;
+};
+
+template <int N, typename R>
+constexpr int m1w_min_blocks() {
+  return sizeof(R) == 4 ? 4 : (N <= 8 ? 4 : 2);
+}
+
+// Line passes over one swizzled slice box (all N planes in this CTA).
+template <int N, typename R, bool IN_SPEC, bool OUT_SPEC, bool MUL>
+__device__ __forceinline__ void swz_xpass(R* xs, const R* mul, const LineCoef<N, R>& cf) {
+  using G = SwzGeom<N, R>;
+  constexpr int CPR = G::RB / 16, EPC = 16 / (int)sizeof(R);
+  for (int r = threadIdx.x; r < N * N; r += TMA_NT) {
+    R v[N];
+#pragma unroll
+    for (int c = 0; c < CPR; ++c) {
+      const int o = G::chunk(r, c);
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) v[c * EPC + e] = MUL ? xs[o + e] * mul[o + e] : xs[o + e];
+    }
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, cf, [&](int i, R val) { xs[G::off(r, i)] = val; });
+  }
+}
+
+template <int N, typename R, bool IN_SPEC, bool OUT_SPEC>
+__device__ __forceinline__ void swz_ypass(R* xs, const LineCoef<N, R>& cf) {
+  using G = SwzGeom<N, R>;
+  for (int l = threadIdx.x; l < N * N; l += TMA_NT) {
+    const int p = l / N, x = l - (l / N) * N;
+    R v[N];
+#pragma unroll
+    for (int y = 0; y < N; ++y) v[y] = xs[G::off(p * N + y, x)];
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, cf, [&](int i, R val) { xs[G::off(p * N + i, x)] = val; });
+  }
+}
+
+template <int N, typename R, int DIR>
+__global__ void __launch_bounds__(TMA_NT, (m1w_min_blocks<N, R>()))
+slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
+  using G = SwzGeom<N, R>;
+  constexpr int NN = N * N;
+  constexpr int VOL = N * NN;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ alignas(8) uint64_t bar;
+  const int tid = threadIdx.x;
+  int t_out, ntau;
+  size_t off = 0;
+  const int* done = A.done;
+  double acoef = A.a;
+  if (A.tiles != nullptr) {
+    const BatchTile tl = A.tiles[blockIdx.x];
+    const BatchProb& pr = A.probs[tl.prob];
+    t_out = tl.t0;
+    ntau = pr.ntau;
+    off = (size_t)pr.off;
+    done = pr.done;
+    if (A.scale_by_A) acoef *= pr.A;
+  } else {
+    t_out = blockIdx.x;
+    ntau = A.ntau;
+  }
+  if (done != nullptr && A.exec_if >= 0 && *done != A.exec_if) return;
+  const int t_in = DIR == 0 ? (t_out == 0 ? ntau - 1 : t_out - 1)
+                            : (t_out == ntau - 1 ? 0 : t_out + 1);
+  const R sgn = (DIR == 0 ? t_out != 0 : t_out != ntau - 1) ? R(-1) : R(1);
+  const int t_s = DIR == 0 ? t_in : t_out;  // slice of the site multiplier
+  unsigned char* const base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  R* const xs = reinterpret_cast<R*>(base);
+  R* const ss = xs + VOL;
+  R* const ks = ss + VOL;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&bar, (uint32_t)(VOL * sizeof(R)) * (DIR == 1 ? 3u : 2u));
+    tma_load_rows(xs, &A.tm_in, (int)((off + (size_t)t_in * VOL) / N), &bar);
+    tma_load_rows(ss, &A.tm_s, (int)((off + (size_t)t_s * VOL) / N), &bar);
+    if (DIR == 1) tma_load_rows(ks, &A.tm_k, 0, &bar);
+  }
+  __syncthreads();
+  {
+    uint32_t n = 0;
+    while (!mbar_try_wait(&bar, 0u)) {
+      if (++n > TMA_WAIT_LIMIT) {
+        if (A.err != nullptr) atomicExch(A.err, 1);
+        break;
+      }
+    }
+  }
+  // inverse transform (spectral input); DIR 1 weights the modes by b on the way in
+  swz_xpass<N, R, true, false, DIR == 1>(xs, ks, A.ci_x);
+  __syncthreads();
+  swz_ypass<N, R, true, false>(xs, A.ci_y);
+  __syncthreads();
+  const R f1 = DIR == 1 ? sgn * R(acoef) : R(1);
+  for (int q = tid; q < NN; q += TMA_NT) {  // z pass, times the site multiplier, in place
+    const int y = q / N, x = q - (q / N) * N;
+    R v[N];
+#pragma unroll
+    for (int z = 0; z < N; ++z) v[z] = xs[G::off(z * N + y, x)];
+    line_op<N, R, true, false>(v, A.ci_z, [&](int zp, R val) {
+      const int o = G::off(zp * N + y, x);
+      xs[o] = (f1 * ss[o]) * val;
+    });
+  }
+  __syncthreads();
+  // forward transform (spectral output)
+  swz_xpass<N, R, false, true, false>(xs, nullptr, A.cf_x);
+  __syncthreads();
+  swz_ypass<N, R, false, true>(xs, A.cf_y);
+  __syncthreads();
+  const R f2 = DIR == 0 ? sgn * R(acoef) : R(1);
+  R* const gout = A.out + off + (size_t)t_out * VOL;
+  for (int q = tid; q < NN; q += TMA_NT) {
+    const int y = q / N, x = q - (q / N) * N;
+    R v[N];
+#pragma unroll
+    for (int z = 0; z < N; ++z) v[z] = xs[G::off(z * N + y, x)];
+    line_op<N, R, false, true>(v, A.cf_z, [&](int zp, R val) {
+      R o = f2 * val;
+      if constexpr (DIR == 0) o *= __ldg(A.bk + zp * NN + q);
+      gout[zp * NN + q] = o;
+    });
+  }
+}
+
+template <int N, typename R, int DIR>
+inline cudaError_t m1w_launch(const SliceCall& c, cudaStream_t st) {
+  constexpr int VOL = N * N * N;
+  M1wArgs<N, R> a;
+  std::memset(&a, 0, sizeof(a));
+  const long long nelem = c.nelem > 0 ? c.nelem : (long long)c.ntau * VOL;
+  if (c.in == nullptr || c.pre == nullptr || c.out == nullptr || c.coef == nullptr ||
+      c.coef2 == nullptr || (DIR == 1 ? c.bkpre : c.bkpost) == nullptr)
+    return cudaErrorInvalidValue;
+  if (encode_rows<R>(&a.tm_in, c.in, nelem, N, N * N) != cudaSuccess ||
+      encode_rows<R>(&a.tm_s, c.pre, nelem, N, N * N) != cudaSuccess ||
+      (DIR == 1 && encode_rows<R>(&a.tm_k, c.bkpre, VOL, N, N * N) != cudaSuccess))
+    return cudaErrorNotSupported;
+  a.ci_x = *reinterpret_cast<const LineCoef<N, R>*>(c.coef);
+  a.ci_y = a.ci_x;
+  a.ci_z = a.ci_x;
+  a.cf_x = *reinterpret_cast<const LineCoef<N, R>*>(c.coef2);
+  a.cf_y = a.cf_x;
+  a.cf_z = a.cf_x;
+  a.bk = static_cast<const R*>(c.bkpost);
+  a.out = static_cast<R*>(c.out);
+  a.a = c.a;
+  a.done = c.done;
+  a.exec_if = c.exec_if;
+  a.tiles = c.tiles;
+  a.probs = c.probs;
+  a.scale_by_A = c.scale_by_A;
+  a.ntau = c.ntau;
+  a.err = c.err;
+  const size_t smem = (size_t)(DIR == 1 ? 3 : 2) * VOL * sizeof(R) + 1024;
+  auto kern = slice_m1w_kernel<N, R, DIR>;
+  static int configured = 0;
+  if (!configured) {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(3 * VOL * sizeof(R) + 1024));
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
+    if (err != cudaSuccess) return err;
+    configured = 1;
+  }
+  const int units = c.tiles != nullptr ? c.ntiles : c.ntau;
+  if (c.grid_out) *c.grid_out = units;
+  kern<<<units, TMA_NT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N>
+inline cudaError_t slice_m1w_try(const SliceCall& c, cudaStream_t st) {
+  if (!slice_m1w_supported(N, c.prec) || c.shift == 0) return cudaErrorNotSupported;
+  if constexpr (N == 16) {
+    if (c.prec == 1)
+      return c.shift < 0 ? m1w_launch<16, float, 0>(c, st) : m1w_launch<16, float, 1>(c, st);
+    return c.shift < 0 ? m1w_launch<16, double, 0>(c, st) : m1w_launch<16, double, 1>(c, st);
+  } else if constexpr (N == 8) {
+    return c.shift < 0 ? m1w_launch<8, double, 0>(c, st) : m1w_launch<8, double, 1>(c, st);
+  }
+  return cudaErrorNotSupported;
 }
 
 // TMA path for one N: cudaErrorNotSupported when the call is outside what it covers.

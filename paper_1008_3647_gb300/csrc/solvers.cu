@@ -243,8 +243,8 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
   VecSet& V = S->vs[prec];
   const void* bk = prec ? (const void*)L->bk32 : (const void*)L->bk64;
   const int* done = &S->sc->done;
-  auto rec = [&](double coef, int acc_mode, bool write_out) -> ufg_status {
-    cudaError_t e = launch_recurrence(prec, V.spec, write_out ? V.spec : nullptr, bk, L->V,
+  auto rec = [&](const void* in, double coef, int acc_mode, bool write_out) -> ufg_status {
+    cudaError_t e = launch_recurrence(prec, in, write_out ? V.spec : nullptr, bk, L->V,
                                       L->ntau, tr ? 1 : 0, 1.0, V.acc, coef, acc_mode, done,
                                       S->st);
     if (e != cudaSuccess) return cuda_fail(e, "recurrence kernel");
@@ -258,9 +258,24 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
   fw.done = done;
   cudaError_t e = sdisp(L->nx, fw, S->st);
   if (e != cudaSuccess) return cuda_fail(e, "forward transform");
-  UFG_TRY(rec(cw[0], 1, d > 0));
+  UFG_TRY(rec(V.spec, cw[0], 1, d > 0));
+  const bool fused = slice_m1w_supported(L->nx, prec);
   for (int nn = 1; nn <= d; ++nn) {
-    if (!tr) {
+    if (fused) {  // -A M1 (or M1^T) in momentum space in one kernel: spec -> wr
+      SliceCall m = base_call(L, FAM_INV, prec);
+      m.fam = FAM_M1W;
+      m.coef2 = base_call(L, FAM_FWD, prec).coef;
+      m.in = V.spec;
+      m.pre = fld(f, 's', prec);
+      if (tr) m.bkpre = bk; else m.bkpost = bk;
+      m.shift = tr ? +1 : -1;
+      m.a = -L->A;
+      m.out = V.wr;
+      m.done = done;
+      e = sdisp(L->nx, m, S->st);
+      if (e != cudaSuccess) return cuda_fail(e, "fused M1 term");
+      if (tr) S->counts.M1T++; else S->counts.M1++;
+    } else if (!tr) {
       SliceCall iv = base_call(L, FAM_INV, prec);  // w = F spec
       iv.in = V.spec;
       iv.out = V.wr;
@@ -297,7 +312,7 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
       if (e != cudaSuccess) return cuda_fail(e, "forward transform");
       S->counts.M1T++;
     }
-    UFG_TRY(rec(cw[nn], 2, nn < d));
+    UFG_TRY(rec(fused ? V.wr : V.spec, cw[nn], 2, nn < d));
   }
   SliceCall iv = base_call(L, FAM_INV, prec);
   iv.in = V.acc;

@@ -54,6 +54,22 @@ def test_uneven_batch_converges_and_matches_solo(ufg, precision):
         assert float((xs - pr["x"]).norm() / xs.norm()) < 1e-7
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_with_16_cubed(ufg, precision):
+    # 16^3 slices take the TMA-staged and fused momentum-space kernels in both precisions.  Shapes
+    # on which the FP64 oracle's BiCGStab converges (16^3 x 24 seed 11 and 16^3 x 40 seed 13 break
+    # down there too, restarts exhausted)
+    shapes = [(16, 64, 11), (8, 40, 12), (16, 48, 14)]
+    probs = _problems(shapes)
+    prec = ufg.UFG_FP64 if precision == "fp64" else ufg.UFG_MIXED
+    stats = ufg.ufg_solve_batch(probs, "wce", {"order": 2}, tol=1e-10, precision=prec)
+    for pr, st in zip(probs, stats):
+        assert st["status"] == ufg.UFG_OK, st
+        olat = O.Lattice(pr["nx"], pr["ntau"])
+        r = pr["b_h"] - O.apply_Q(olat, pr["sigma_h"], pr["x"].cpu().numpy())
+        assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(pr["b_h"])
+
+
 def test_batch_96_problems_shapes(ufg):
     shapes = batch_shapes(96)
     assert len(shapes) == 96
