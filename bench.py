@@ -6,9 +6,11 @@ Headline (one JSON line on rank 0): solves/s to a true relative residual ||b - M
 solved by the paper's method of choice -- two-step BiCGStab (M^T y = b, M x = y) with the
 order-2 weak-coupling preconditioner -- in mixed precision (FP32 inner solves, FP64 defect
 correction).  One step = 8 independent problems per rank (field set-up + solve each), inputs
-resident in HBM; the same step in plain FP64 is reported beside it ("fp64").  The roofline
-object reports the fused M apply (FP32) on the 32^3 x 512 lattice, the HBM-bound form of the
-slice kernel that dominates every step, timed live with CUDA events on its stream.
+resident in HBM; the same step in plain FP64 is reported beside it ("fp64").  After the timed
+steps one more step runs with the library's per-kernel timing enabled (CUDA events around every
+launch on the library's stream, algorithmic bytes of the problems still running): "kernels"
+lists the classes by device time and "roofline" is the dominant one against the measured HBM
+copy bandwidth.  The fused M apply on 32^3 x 512 (FP32 and FP64) is timed alone as well.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ufg|reference]
 Under torchrun each rank solves its own 8 problems (weak scaling, no collective on the data
@@ -38,6 +40,12 @@ WORKLOAD = ("16^3x256 lattice (tau=0.05, g=5), 8 seeded problems per rank solved
             "ufg_solve_batch: two-step BiCGStab + WCE order 2, mixed FP32-inner/FP64-outer, "
             "tol 1e-10")
 ORACLE_COUNTS = os.path.join(ROOT, "tests", "golden", "oracle_counts_16x256.json")
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of kernel classes from
+# one ncu capture of the timed step's launches; a class is listed only while its kernel is
+# unchanged since the capture (the command is in the profile summary under profiles/).
+NCU_TRAFFIC = {}
 
 
 def peaks():
@@ -220,11 +228,17 @@ def run_ufg(args, rank, world, local_rank):
             raise RuntimeError("batched solve failed: %s" % bad[0])
         return stats
 
-    def step(precision, host=False, pc=("wce", {"order": 2}), kind="bicg"):
+    solver_cheb = ufg.Solver(lat)
+    solver_cheb.ufg_set_preconditioner("cheb", degree=16)
+
+    def step(precision, host=False, kind="bicg"):
+        """The rank's problems one call each: two-step BiCGStab + WCE2 ("bicg") or CG on
+        M^T M + Chebyshev degree 16 ("cg")."""
         stats = []
         for i in range(PER_RANK):
             field.update(sig_h[i] if host else sig_d[i])
-            fn = solver.ufg_solve_bicgstab_two_step if kind == "bicg" else solver.ufg_solve_cg_normal
+            fn = (solver.ufg_solve_bicgstab_two_step if kind == "bicg"
+                  else solver_cheb.ufg_solve_cg_normal)
             b = b_h[i] if host else b_d[i]
             x = x_h[i] if host else x_d[i]
             _, st = fn(field, b, x, tol=TOL, precision=precision, inner_tol=1e-5, check_every=8)
@@ -273,6 +287,11 @@ def run_ufg(args, rank, world, local_rank):
     # the same problems one at a time through the single-problem entry point
     step(ufg.UFG_MIXED)
     t_solo = timed(1, lambda: step(ufg.UFG_MIXED), "step_solo")
+    # the other method of the paper on the same problems: CG on M^T M + Chebyshev degree 16
+    step(ufg.UFG_MIXED, kind="cg")
+    cheb_box = {}
+    t_cheb = timed(1, lambda: cheb_box.__setitem__("st", step(ufg.UFG_MIXED, kind="cg")),
+                   "step_cg_cheb16")
 
     solves = PER_RANK * world
     value = solves * args.steps / t_mixed
@@ -280,8 +299,25 @@ def run_ufg(args, rank, world, local_rank):
     fp64 = solves * n64 / t_fp64
     solo = solves / t_solo
 
-    # roofline of the dominant kernel: fused M apply (slice kernel, KIN family) at 32^3 x 512
+    # one instrumented step: per-kernel device time and algorithmic bytes inside the real solve
     hbm, peak_src = peaks()
+    ufg.ufg_profile_enable(True)
+    step_batch(ufg.UFG_MIXED)
+    ufg.ufg_profile_enable(False)
+    kstats = ufg.ufg_profile_read()
+    ktotal = sum(k["total_ms"] for k in kstats) or 1.0
+    top = kstats[0]
+    roofline = {"kernel": top["name"] + " (dominant kernel of the step)", "bound": "hbm",
+                "achieved": top["gbs"], "peak": hbm, "unit": "GB/s", "frac": top["gbs"] / hbm,
+                "traffic": NCU_TRAFFIC.get(top["name"]), "peak_source": peak_src,
+                "us_per_launch": top["us_per_launch"],
+                "algorithmic_bytes_per_launch": top["bytes"] / max(1, top["launches"]),
+                "share_of_step": top["total_ms"] / ktotal}
+    kernels = [{"name": k["name"], "launches": k["launches"],
+                "us_per_launch": round(k["us_per_launch"], 2), "gbs": round(k["gbs"], 1),
+                "frac_hbm": round(k["gbs"] / hbm, 3), "share": round(k["total_ms"] / ktotal, 4)}
+               for k in kstats[:12]]
+    # the fused M apply alone on 32^3 x 512 (16.8M sites), FP32 and FP64
     roof = apply_roofline(ufg, torch, dev, stream, hbm, peak_src)
     if rank != 0:
         return
@@ -295,7 +331,8 @@ def run_ufg(args, rank, world, local_rank):
                    "precision": "mixed (FP32 inner, FP64 outer)", "tol": TOL,
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
-        "roofline": roof["fp32"],
+        "roofline": roofline,
+        "kernels": kernels,
         "e2e": {"value": e2e, "unit": "solves/s",
                 "h2d_bytes_per_step": PER_RANK * 2 * lat.ntau * lat.nx ** 3 * 8,
                 "d2h_bytes_per_step": PER_RANK * lat.ntau * lat.nx ** 3 * 8},
@@ -306,10 +343,17 @@ def run_ufg(args, rank, world, local_rank):
                  "true_residual_max": max(s["true_residual"] for s in stats_box["fp64"])},
         "solo_mixed": {"value": solo, "unit": "solves/s",
                        "note": "same problems, one ufg_solve_bicgstab_two_step call each"},
+        "cg_cheb16_mixed": {"value": solves / t_cheb, "unit": "solves/s",
+                            "iterations_mean": statistics.mean(s["iterations"]
+                                                               for s in cheb_box["st"]),
+                            "true_residual_max": max(s["true_residual"] for s in cheb_box["st"]),
+                            "note": "same problems, CG on M^T M + Chebyshev degree 16, mixed, "
+                                    "one ufg_solve_cg_normal call each"},
         "mixed": {"iterations_mean": statistics.mean(s["iterations"] for s in sm),
                   "outer_mean": statistics.mean(s["outer_iterations"] for s in sm),
                   "true_residual_max": max(s["true_residual"] for s in sm),
                   "mv_paper_mean": statistics.mean(s["mv_paper"] for s in sm)},
+        "apply_fp32_32x512": roof["fp32"],
         "apply_fp64_32x512": roof["fp64"],
     }
     if world == 1 and not args.no_cpu_baseline:

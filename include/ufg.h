@@ -123,6 +123,29 @@ const char* ufg_supported_nx(void);
  * captured kernels); for benchmarks and launch-overhead accounting. */
 long long ufg_kernel_launches(void);
 
+/* Per-kernel device timing of instrumented runs.  The paper has no counterpart: this is
+ * measurement support (roofline accounting of the kernels inside a real solve).  While enabled
+ * (process-wide), every kernel launch is bracketed by a pair of CUDA events on its own stream;
+ * solver loops capture and replay separate CUDA graphs that contain these event nodes, so the
+ * kernels are timed as they run in an ordinary solve, and each replay is read back once it has
+ * finished (one extra host synchronisation per replay).  Each record carries the launch's
+ * algorithmic bytes: the operand elements read and written by the work items that run (a
+ * stream-ordered copy of the solver flags taken just before the launch tells which problems
+ * still run), times the element size; per-mode tables of one slice are included, scalars are
+ * not.  ufg_profile_enable(1) clears earlier results; (0) stops recording and keeps them.
+ * Captures made while enabled must not overlap between host threads. */
+typedef struct {
+  char name[64];       /* kernel class, e.g. "slice fwd N16 f32" */
+  long long launches;
+  double total_ms;     /* sum of the CUDA-event durations */
+  double bytes;        /* sum of the algorithmic bytes */
+} ufg_kernel_stat;
+ufg_status ufg_profile_enable(int on);
+/* Synchronises the device and aggregates the records by name into out[0 .. min(max, n) - 1],
+ * sorted by total time (largest first); *n receives the number of distinct names.  out may be
+ * NULL with max = 0 to query n. */
+ufg_status ufg_profile_read(ufg_kernel_stat* out, int max, int* n);
+
 /* Lattice N_x^3 x N_tau with time step tau and coupling g (Sec. 1; the paper uses tau = 0.05,
  * g in {2.5, 5, 7.5}).  dispersion 0: E(k) = k^2/2 (the paper's choice, hbar = m = 1);
  * dispersion 1: E(k) = sum_i (1 - cos k_i), a Hubbard-type lattice dispersion (Sec. 6).

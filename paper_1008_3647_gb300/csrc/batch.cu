@@ -82,7 +82,10 @@ struct Batch {
   std::map<std::string, long long> graph_kernels;
   std::vector<void*> allocs;
   ~Batch() {
-    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : graphs) {
+      profile_graph_destroyed(kv.second);
+      cudaGraphExecDestroy(kv.second);
+    }
     for (void* p : allocs) cudaFree(p);
     if (scs_h) cudaFreeHost(scs_h);
     if (scale_h) cudaFreeHost(scale_h);
@@ -106,6 +109,23 @@ const void* fldb(Batch& B, char w, int prec) {
   return nullptr;
 }
 
+// The work of a batched launch for the kernel timer: per_site bytes for every site of the
+// problems in `idx` (all problems when null) that run under exec_if, per_problem bytes each.
+LaunchWork batch_work(Batch& B, const std::vector<int>* idx, int exec_if, double per_site,
+                      double per_problem = 0.0) {
+  LaunchWork w;
+  if (!profiling()) return w;
+  w.flag_dev = &B.scs[0].done;
+  w.stride = sizeof(DevScalars);
+  w.exec_if = exec_if;
+  w.site_bytes.assign(B.n, 0.0);
+  for (int i = 0; i < B.n; ++i) {
+    if (idx && std::find(idx->begin(), idx->end(), i) == idx->end()) continue;
+    w.site_bytes[i] = per_site * (double)B.probs_h[i].V * B.probs_h[i].ntau + per_problem;
+  }
+  return w;
+}
+
 ufg_status slice(Batch& B, Group& g, SliceCall c, int exec_if) {
   c.tiles = g.tiles;
   c.ntiles = g.ntiles;
@@ -114,6 +134,9 @@ ufg_status slice(Batch& B, Group& g, SliceCall c, int exec_if) {
   c.nelem = B.S;
   if (c.partials) c.partials += 2 * (size_t)g.cta_base;
   note_launches(1);
+  KTimer kt(slice_kernel_name(c, g.lat->nx), B.st,
+            batch_work(B, &g.probs, exec_if, slice_bytes_per_site(c),
+                       slice_bytes_per_problem(c, g.lat->nx)));
   cudaError_t e = slice_dispatch(g.lat->nx, c, B.st);
   if (e != cudaSuccess) return cuda_fail(e, "batched slice kernel");
   return UFG_OK;
@@ -149,6 +172,9 @@ ufg_status apply_b(Batch& B, int prec, int op, const void* in, void* out, double
 ufg_status vecb(Batch& B, int prec, int op, int exec_if, const void* a, const void* b,
                 const void* c, const void* d, const void* e, const void* f, double* part) {
   note_launches(1);
+  KTimer kt(vec_op_name(op, prec), B.st,
+            batch_work(B, nullptr, exec_if,
+                       (prec ? 4.0 : 8.0) * vec_op_arrays(op, a != nullptr, c != nullptr)));
   cudaError_t err = launch_vec_batch(prec, op, B.vtiles, B.nvtiles, B.scs, exec_if, (void*)a,
                                      (void*)b, (void*)c, (void*)d, (void*)e, (void*)f, part, B.st);
   if (err != cudaSuccess) return cuda_fail(err, "batched vector kernel");
@@ -158,6 +184,7 @@ ufg_status vecb(Batch& B, int prec, int op, int exec_if, const void* a, const vo
 ufg_status scalb(Batch& B, int op, const double* part, int kind, const double* part2, int kind2,
                  int exec_if) {
   note_launches(1);
+  KTimer kt("scalar", B.st, LaunchWork{});
   cudaError_t err = launch_scalar_batch(op, B.scs, B.probs, B.n, part, kind, part2, kind2, exec_if,
                                         B.st);
   if (err != cudaSuccess) return cuda_fail(err, "batched scalar kernel");
@@ -188,6 +215,12 @@ ufg_status wce_b(Batch& B, int prec, const void* r, void* z, bool tr) {
     const void* bk = prec ? (const void*)g.lat->bk32 : (const void*)g.lat->bk64;
     auto rec = [&](const void* in, double coef, int mode, bool write_out) -> ufg_status {
       note_launches(1);
+      KTimer kt(std::string("recurrence acc") + std::to_string(mode) + (write_out ? "+out" : "") +
+                    (prec ? " f32" : " f64"),
+                B.st,
+                batch_work(B, &g.probs, 0,
+                           (prec ? 4.0 : 8.0) *
+                               (1 + (mode == 1 ? 1 : mode == 2 ? 2 : 0) + (write_out ? 1 : 0))));
       cudaError_t e = launch_recurrence_batch(prec, in, write_out ? V.spec : nullptr, bk,
                                               g.max_ntau, tr ? 1 : 0, 1.0, V.acc, coef, mode, 0,
                                               g.rtiles, g.nrtiles, B.probs, B.st);
@@ -350,9 +383,16 @@ ufg_status bicg_b(Batch& B, int prec, int op, const std::vector<double>& tol,
       continue;
     }
     if (!any_run) break;
-    auto it = B.graphs.find(key);
+    if (!graphs_enabled()) {
+      for (int i = 0; i < check_every; ++i) UFG_TRY(body());
+      continue;
+    }
+    // instrumented runs replay their own graphs, which carry the kernel timer's event nodes
+    const std::string gkey = profiling() ? std::string(key) + "|prof" : std::string(key);
+    auto it = B.graphs.find(gkey);
     if (it == B.graphs.end()) {
       const long long l0 = launches_so_far();
+      profile_capture_begin();
       UFG_CUDA(cudaStreamBeginCapture(B.st, cudaStreamCaptureModeThreadLocal));
       ufg_status s = UFG_OK;
       for (int i = 0; i < check_every && s == UFG_OK; ++i) s = body();
@@ -362,18 +402,24 @@ ufg_status bicg_b(Batch& B, int prec, int op, const std::vector<double>& tol,
       note_launches(-captured);
       if (s != UFG_OK) {
         if (gr) cudaGraphDestroy(gr);
+        profile_capture_end(nullptr);
         return s;
       }
-      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture (batch)");
+      if (e != cudaSuccess) {
+        profile_capture_end(nullptr);
+        return cuda_fail(e, "cudaStreamEndCapture (batch)");
+      }
       cudaGraphExec_t ex = nullptr;
       e = cudaGraphInstantiate(&ex, gr, 0);
       cudaGraphDestroy(gr);
+      profile_capture_end(e == cudaSuccess ? ex : nullptr);
       if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate (batch)");
-      it = B.graphs.emplace(key, ex).first;
-      B.graph_kernels[key] = captured;
+      it = B.graphs.emplace(gkey, ex).first;
+      B.graph_kernels[gkey] = captured;
     }
     UFG_CUDA(cudaGraphLaunch(it->second, B.st));
-    note_launches(B.graph_kernels[key]);
+    note_launches(B.graph_kernels[gkey]);
+    profile_after_replay(it->second, B.st);
   }
   res->iters.assign(B.n, 0);
   res->restarts = restarts;
@@ -389,6 +435,7 @@ ufg_status bicg_b(Batch& B, int prec, int op, const std::vector<double>& tol,
 ufg_status norms_b(Batch& B, const double* v, std::vector<double>& out) {
   UFG_TRY(vecb(B, 0, V_DOT, -1, nullptr, nullptr, v, v, nullptr, nullptr, B.slot(B_RES)));
   note_launches(1);
+  KTimer kt("scalar", B.st, LaunchWork{});
   cudaError_t e = launch_scalar_batch(OP_NORM2, B.scs, B.probs, B.n, B.slot(B_RES), 1, nullptr, 1,
                                       -1, B.st);
   if (e != cudaSuccess) return cuda_fail(e, "batched norms");
@@ -423,6 +470,7 @@ ufg_status axpy_b(Batch& B, double* x, const double* y, const std::vector<double
   std::memcpy(B.scale_h, sc.data(), B.n * sizeof(double));
   UFG_CUDA(cudaMemcpyAsync(B.scale, B.scale_h, B.n * sizeof(double), cudaMemcpyHostToDevice, B.st));
   note_launches(1);
+  KTimer kt("batch axpy f64", B.st, batch_work(B, nullptr, -1, copy ? 16.0 : 24.0));
   axpy_batch_kernel<<<B.nvtiles, 256, 0, B.st>>>(B.vtiles, B.scale, x, y, copy);
   UFG_CUDA(cudaGetLastError());
   return UFG_OK;
@@ -432,6 +480,7 @@ ufg_status mixed_glue(Batch& B, int mode, double* x64, float* y32, const std::ve
   std::memcpy(B.scale_h, sc.data(), B.n * sizeof(double));
   UFG_CUDA(cudaMemcpyAsync(B.scale, B.scale_h, B.n * sizeof(double), cudaMemcpyHostToDevice, B.st));
   note_launches(1);
+  KTimer kt("batch mixed glue", B.st, batch_work(B, nullptr, -1, mode ? 20.0 : 12.0));
   mixed_batch_kernel<<<B.nvtiles, 256, 0, B.st>>>(B.vtiles, B.scale, x64, y32, mode);
   UFG_CUDA(cudaGetLastError());
   return UFG_OK;

@@ -9,6 +9,26 @@ namespace ufg {
 
 constexpr int VEC_NT = 256;
 
+std::string vec_op_name(int op, int prec) {
+  static const char* n[] = {"cg_update", "cg_p", "bi_p", "bi_s", "bi_x", "dot", "copy", "zero", "add"};
+  return std::string("vec ") + ((op >= 0 && op <= V_ADD) ? n[op] : "?") + (prec ? " f32" : " f64");
+}
+
+int vec_op_arrays(int op, bool a_present, bool c_present) {
+  switch (op) {
+    case V_CG_UPDATE: return 6;  // x, p, r, q read; x, r written
+    case V_CG_P: return 3;
+    case V_BI_P: return 4;
+    case V_BI_S: return 6;       // r, v, x, y read; s, x written
+    case V_BI_X: return 7;       // x, z, s, t, rhat read; x, r written
+    case V_DOT: return 2 * ((a_present ? 1 : 0) + (c_present ? 1 : 0));
+    case V_COPY: return 2;
+    case V_ZERO: return 1;
+    case V_ADD: return 3;
+  }
+  return 0;
+}
+
 int vec_grid(long long n) {
   long long g = (n + VEC_NT * 4 - 1) / (VEC_NT * 4);
   if (g < 1) g = 1;

@@ -6,6 +6,7 @@
 // kernels read alpha/beta/omega from there, so a whole iteration runs without the host and can be
 // captured in a CUDA graph.  All kernels return immediately once `done` is set.
 #pragma once
+#include <string>
 #include <cuda_runtime.h>
 
 #include "slice_call.h"
@@ -65,6 +66,10 @@ cudaError_t launch_vec(int prec, int op, long long n, const DevScalars* sc, void
                        void* c, void* d, void* e, void* f, double* part, int* nparts,
                        cudaStream_t st);
 int vec_grid(long long n);
+// Instrumentation: "vec <op> f32|f64" and the vectors one element of the op reads plus writes
+// (V_DOT: each present pair; a: first pair present, c: second pair present).
+std::string vec_op_name(int op, int prec);
+int vec_op_arrays(int op, bool a_present, bool c_present);
 
 // Batched form: CTA i works on tiles[i] = (problem, start, length) of the packed arenas with
 // the scalars scs[problem]; it runs while scs[problem].done == exec_if (exec_if < 0: always).

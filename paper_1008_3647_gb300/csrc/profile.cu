@@ -1,0 +1,269 @@
+// Per-kernel device timing of instrumented runs: CUDA-event pairs around each launch, with the
+// launch's algorithmic bytes, aggregated by kernel class on request (ufg_profile_*).
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ufg_internal.h"
+
+namespace ufg {
+
+namespace {
+struct Rec {
+  std::string name;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LaunchWork work;
+  int* flags = nullptr;  // pinned snapshot of the solver flags (work.site_bytes.size() ints)
+};
+// Process-lifetime state (never destroyed): graph owners release their records from their own
+// static destructors at exit, in an order relative to this file that C++ leaves open.
+std::atomic<int> g_on{0};
+std::mutex& g_mu = *new std::mutex;
+std::vector<Rec>& g_recs = *new std::vector<Rec>;
+
+// Pinned host ints handed out in order; reset when recording restarts (and only then: earlier
+// snapshots may still be in flight until the next synchronisation).
+struct PinnedPool {
+  std::vector<int*> chunks;
+  size_t used = 0;  // ints used in the last chunk
+  static constexpr size_t CHUNK = 1 << 20;
+  int* take(size_t n) {
+    if (n > CHUNK) return nullptr;
+    if (chunks.empty() || used + n > CHUNK) {
+      int* p = nullptr;
+      if (cudaMallocHost(&p, CHUNK * sizeof(int)) != cudaSuccess) return nullptr;
+      chunks.push_back(p);
+      used = 0;
+    }
+    int* r = chunks.back() + used;
+    used += n;
+    return r;
+  }
+  void reset() {
+    for (int* p : chunks) cudaFreeHost(p);
+    chunks.clear();
+    used = 0;
+  }
+};
+PinnedPool& g_pool = *new PinnedPool;
+
+// Direct-launch records (their flag snapshots stay in the pool: captured graphs may still
+// point into it).
+void drop_records() {
+  for (Rec& r : g_recs) {
+    if (r.e0) cudaEventDestroy(r.e0);
+    if (r.e1) cudaEventDestroy(r.e1);
+  }
+  g_recs.clear();
+}
+
+double resolve_bytes(const Rec& r) {
+  const LaunchWork& w = r.work;
+  double b = w.fixed_bytes;
+  for (size_t i = 0; i < w.site_bytes.size(); ++i) {
+    const bool runs = w.flag_dev == nullptr || w.exec_if < 0 || r.flags == nullptr ||
+                      r.flags[i] == w.exec_if;
+    if (runs) b += w.site_bytes[i];
+  }
+  return b;
+}
+}  // namespace
+
+bool profiling() { return g_on.load(std::memory_order_relaxed) != 0; }
+
+namespace {
+// Records made while a stream is being captured become event-record (and flag-copy) nodes of
+// that graph; they are re-timed after each replay of it.
+std::vector<Rec>& g_pending = *new std::vector<Rec>;
+std::map<cudaGraphExec_t, std::vector<Rec>>& g_graph_recs =
+    *new std::map<cudaGraphExec_t, std::vector<Rec>>;
+struct Agg {
+  long long launches = 0;
+  double ms = 0.0, bytes = 0.0;
+};
+std::map<std::string, Agg>& g_agg = *new std::map<std::string, Agg>;  // harvested replays
+
+void destroy(std::vector<Rec>& v) {
+  for (Rec& r : v) {
+    if (r.e0) cudaEventDestroy(r.e0);
+    if (r.e1) cudaEventDestroy(r.e1);
+  }
+  v.clear();
+}
+
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive;
+}
+}  // namespace
+
+KTimer::KTimer(const std::string& name, cudaStream_t st, LaunchWork work) : st_(st) {
+  if (!profiling()) return;
+  Rec r;
+  r.name = name;
+  r.work = std::move(work);
+  const bool cap = capturing(st);
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (r.work.flag_dev != nullptr && r.work.exec_if >= 0 && !r.work.site_bytes.empty()) {
+    r.flags = g_pool.take(r.work.site_bytes.size());
+    if (r.flags != nullptr &&
+        cudaMemcpy2DAsync(r.flags, sizeof(int), r.work.flag_dev, r.work.stride, sizeof(int),
+                          r.work.site_bytes.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      r.flags = nullptr;
+  }
+  if (cudaEventCreate(&r.e0) != cudaSuccess || cudaEventCreate(&r.e1) != cudaSuccess) {
+    if (r.e0) cudaEventDestroy(r.e0);
+    return;  // timing is best effort: the launch itself proceeds
+  }
+  cap_ = cap;
+  if (cap) {
+    cudaEventRecordWithFlags(r.e0, st, cudaEventRecordExternal);
+    idx_ = (long long)g_pending.size();
+    g_pending.push_back(std::move(r));
+  } else {
+    cudaEventRecord(r.e0, st);
+    idx_ = (long long)g_recs.size();
+    g_recs.push_back(std::move(r));
+  }
+}
+
+KTimer::~KTimer() {
+  if (idx_ < 0) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (cap_) {
+    if (idx_ < (long long)g_pending.size())
+      cudaEventRecordWithFlags(g_pending[(size_t)idx_].e1, st_, cudaEventRecordExternal);
+  } else if (idx_ < (long long)g_recs.size()) {
+    cudaEventRecord(g_recs[(size_t)idx_].e1, st_);
+  }
+}
+
+void profile_capture_begin() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  destroy(g_pending);
+}
+
+void profile_capture_end(cudaGraphExec_t ex) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (ex == nullptr || g_pending.empty()) {
+    destroy(g_pending);
+    return;
+  }
+  destroy(g_graph_recs[ex]);
+  g_graph_recs[ex] = std::move(g_pending);
+  g_pending.clear();
+}
+
+void profile_after_replay(cudaGraphExec_t ex, cudaStream_t st) {
+  if (!profiling()) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_graph_recs.find(ex);
+  if (it == g_graph_recs.end() || cudaStreamSynchronize(st) != cudaSuccess) return;
+  for (const Rec& r : it->second) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) continue;
+    Agg& a = g_agg[r.name];
+    a.launches += 1;
+    a.ms += ms;
+    a.bytes += resolve_bytes(r);
+  }
+}
+
+void profile_graph_destroyed(cudaGraphExec_t ex) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_graph_recs.find(ex);
+  if (it == g_graph_recs.end()) return;
+  destroy(it->second);
+  g_graph_recs.erase(it);
+}
+
+std::string slice_kernel_name(const SliceCall& c, int N) {
+  static const char* fam[] = {"kin", "fwd", "inv", "m1w"};
+  std::string s = "slice ";
+  s += (c.fam >= 0 && c.fam <= 3) ? fam[c.fam] : "?";
+  if (c.fam != FAM_M1W) {
+    if (c.pre) s += "+pre";
+    if (c.bkpre) s += "+bkpre";
+    if (c.bkpost) s += "+bkpost";
+    if (c.id) s += "+id";
+    if (c.post) s += "+post";
+    if (c.post2) s += "+post2";
+    if (c.U || c.V) s += "+uv";
+    if (c.want_dotP || c.want_self) s += "+dot";
+  } else {
+    s += c.shift > 0 ? "T" : "";
+  }
+  s += " N" + std::to_string(N) + (c.prec ? " f32" : " f64");
+  return s;
+}
+
+double slice_bytes_per_site(const SliceCall& c) {
+  const double es = c.prec ? 4.0 : 8.0;
+  int site_arrays = 2;  // input and output
+  if (c.pre) ++site_arrays;
+  if (c.id) ++site_arrays;
+  if (c.post) ++site_arrays;
+  if (c.post2) ++site_arrays;
+  if (c.U) ++site_arrays;
+  if (c.V) ++site_arrays;
+  if (c.want_dotP && c.dotP) ++site_arrays;
+  return es * site_arrays;
+}
+
+double slice_bytes_per_problem(const SliceCall& c, int N) {
+  const int mode_tables = (c.bkpre ? 1 : 0) + (c.bkpost ? 1 : 0);
+  return (c.prec ? 4.0 : 8.0) * mode_tables * (double)N * N * N;
+}
+
+}  // namespace ufg
+
+using namespace ufg;
+
+extern "C" ufg_status ufg_profile_enable(int on) {
+  clear_error();
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (on) {
+    cudaDeviceSynchronize();
+    drop_records();
+    g_agg.clear();
+  }
+  g_on.store(on ? 1 : 0);
+  return UFG_OK;
+}
+
+extern "C" ufg_status ufg_profile_read(ufg_kernel_stat* out, int max, int* n) {
+  clear_error();
+  if (n == nullptr || max < 0 || (max > 0 && out == nullptr)) {
+    set_error("profile_read: need n, and out when max > 0");
+    return UFG_INVALID_ARG;
+  }
+  UFG_CUDA(cudaDeviceSynchronize());
+  std::map<std::string, Agg> agg;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    agg = g_agg;
+    for (const Rec& r : g_recs) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) continue;
+      Agg& a = agg[r.name];
+      a.launches += 1;
+      a.ms += ms;
+      a.bytes += resolve_bytes(r);
+    }
+  }
+  std::vector<std::pair<std::string, Agg>> v(agg.begin(), agg.end());
+  std::sort(v.begin(), v.end(), [](const auto& x, const auto& y) { return x.second.ms > y.second.ms; });
+  *n = (int)v.size();
+  for (int i = 0; i < max && i < (int)v.size(); ++i) {
+    std::memset(&out[i], 0, sizeof(ufg_kernel_stat));
+    std::strncpy(out[i].name, v[(size_t)i].first.c_str(), sizeof(out[i].name) - 1);
+    out[i].launches = v[(size_t)i].second.launches;
+    out[i].total_ms = v[(size_t)i].second.ms;
+    out[i].bytes = v[(size_t)i].second.bytes;
+  }
+  return UFG_OK;
+}

@@ -64,11 +64,40 @@ struct ufg_solver {
   Counts counts;
 };
 
+bool ufg::graphs_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("UFG_NO_GRAPH");
+    v = (e && e[0] == '1') ? 0 : 1;
+  }
+  return v == 1;
+}
+
 namespace {
+
+// the kernel timer's view of a single-problem launch: `bytes` when the flag lets it run
+LaunchWork solo_work(const int* done, int exec_if, double bytes) {
+  LaunchWork w;
+  if (!profiling()) return w;
+  w.flag_dev = done;
+  w.exec_if = done ? exec_if : -1;
+  w.site_bytes.assign(1, bytes);
+  return w;
+}
 
 cudaError_t sdisp(int nx, const SliceCall& c, cudaStream_t st) {
   note_launches(1);
+  KTimer kt(slice_kernel_name(c, nx), st,
+            solo_work(c.done, c.exec_if,
+                      slice_bytes_per_site(c) * c.ntau * nx * nx * nx +
+                          slice_bytes_per_problem(c, nx)));
   return slice_dispatch(nx, c, st);
+}
+
+LaunchWork vec_work(const ufg_solver* S, int prec, int op, long long n, const void* a,
+                    const void* c, bool gated) {
+  return solo_work(gated ? &S->sc->done : nullptr, 0,
+                   (double)n * (prec ? 4.0 : 8.0) * vec_op_arrays(op, a != nullptr, c != nullptr));
 }
 
 double* slot(ufg_solver* S, int k) { return S->parts + (size_t)k * 2 * MAX_PARTIAL_CTAS; }
@@ -126,6 +155,7 @@ ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const v
 
 #define VEC(prec, op, n, a, b, c, d, e, f, part, np)                                         \
   do {                                                                                        \
+    KTimer kt_(vec_op_name(op, prec), S->st, vec_work(S, prec, op, n, a, c, true));           \
     cudaError_t err_ = launch_vec(prec, op, n, S->sc, (void*)(a), (void*)(b), (void*)(c),     \
                                   (void*)(d), (void*)(e), (void*)(f), part, np, S->st);       \
     if (err_ != cudaSuccess) return cuda_fail(err_, "vector kernel");                         \
@@ -134,6 +164,7 @@ ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const v
 
 #define VEC_NODONE(prec, op, n, a, b, c, d, e, f, part, np)                                  \
   do {                                                                                        \
+    KTimer kt_(vec_op_name(op, prec), S->st, vec_work(S, prec, op, n, a, c, false));          \
     cudaError_t err_ = launch_vec(prec, op, n, nullptr, (void*)(a), (void*)(b), (void*)(c),   \
                                   (void*)(d), (void*)(e), (void*)(f), part, np, S->st);       \
     if (err_ != cudaSuccess) return cuda_fail(err_, "vector kernel");                         \
@@ -142,6 +173,7 @@ ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const v
 
 #define SCALAR(op, part, np, part2, np2)                                                      \
   do {                                                                                        \
+    KTimer kt_("scalar", S->st, LaunchWork{});                                                \
     cudaError_t err_ = launch_scalar(op, S->sc, part, np, part2, np2, S->st);                 \
     if (err_ != cudaSuccess) return cuda_fail(err_, "scalar kernel");                         \
     note_launches(1);                                                                         \
@@ -244,6 +276,12 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
   const void* bk = prec ? (const void*)L->bk32 : (const void*)L->bk64;
   const int* done = &S->sc->done;
   auto rec = [&](const void* in, double coef, int acc_mode, bool write_out) -> ufg_status {
+    KTimer kt(std::string("recurrence acc") + std::to_string(acc_mode) + (write_out ? "+out" : "") +
+                  (prec ? " f32" : " f64"),
+              S->st,
+              solo_work(done, 0,
+                        (double)L->S * (prec ? 4.0 : 8.0) *
+                            (1 + (acc_mode == 1 ? 1 : acc_mode == 2 ? 2 : 0) + (write_out ? 1 : 0))));
     cudaError_t e = launch_recurrence(prec, in, write_out ? V.spec : nullptr, bk, L->V,
                                       L->ntau, tr ? 1 : 0, 1.0, V.acc, coef, acc_mode, done,
                                       S->st);
@@ -355,14 +393,6 @@ ufg_status pc_apply(ufg_solver* S, ufg_field* f, int prec, const void* r, void* 
 }
 
 // ---- graph replay ---------------------------------------------------------------------------
-bool graphs_enabled() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = std::getenv("UFG_NO_GRAPH");
-    v = (e && e[0] == '1') ? 0 : 1;
-  }
-  return v == 1;
-}
 
 template <class Body>
 ufg_status run_body(ufg_solver* S, const std::string& key, int reps, Body&& body) {
@@ -370,14 +400,20 @@ ufg_status run_body(ufg_solver* S, const std::string& key, int reps, Body&& body
     for (int i = 0; i < reps; ++i) UFG_TRY(body());
     return UFG_OK;
   }
-  auto it = S->graphs.find(key);
+  // instrumented runs replay their own graphs, which carry the kernel timer's event nodes
+  const std::string gkey = profiling() ? key + "|prof" : key;
+  auto it = S->graphs.find(gkey);
   if (it == S->graphs.end()) {
     if (S->graphs.size() > 64) {
-      for (auto& kv : S->graphs) cudaGraphExecDestroy(kv.second.exec);
+      for (auto& kv : S->graphs) {
+        profile_graph_destroyed(kv.second.exec);
+        cudaGraphExecDestroy(kv.second.exec);
+      }
       S->graphs.clear();
     }
     const Counts saved = S->counts;
     const long long l0 = launches_so_far();
+    profile_capture_begin();
     UFG_CUDA(cudaStreamBeginCapture(S->st, cudaStreamCaptureModeThreadLocal));
     ufg_status s = UFG_OK;
     for (int i = 0; i < reps && s == UFG_OK; ++i) s = body();
@@ -388,17 +424,23 @@ ufg_status run_body(ufg_solver* S, const std::string& key, int reps, Body&& body
     note_launches(-captured);
     if (s != UFG_OK) {
       if (g) cudaGraphDestroy(g);
+      profile_capture_end(nullptr);
       return s;
     }
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    if (e != cudaSuccess) {
+      profile_capture_end(nullptr);
+      return cuda_fail(e, "cudaStreamEndCapture");
+    }
     cudaGraphExec_t ex = nullptr;
     e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
+    profile_capture_end(e == cudaSuccess ? ex : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-    it = S->graphs.emplace(key, ufg_solver::GraphEntry{ex, captured}).first;
+    it = S->graphs.emplace(gkey, ufg_solver::GraphEntry{ex, captured}).first;
   }
   UFG_CUDA(cudaGraphLaunch(it->second.exec, S->st));
   note_launches(it->second.kernels);
+  profile_after_replay(it->second.exec, S->st);
   return UFG_OK;
 }
 
@@ -879,7 +921,10 @@ ufg_status ufg_solver_create(const ufg_lattice* L, ufg_solver** out) {
 void ufg_solver_destroy(ufg_solver* S) {
   if (!S) return;
   if (S->st) cudaStreamSynchronize(S->st);
-  for (auto& kv : S->graphs) cudaGraphExecDestroy(kv.second.exec);
+  for (auto& kv : S->graphs) {
+    profile_graph_destroyed(kv.second.exec);
+    cudaGraphExecDestroy(kv.second.exec);
+  }
   for (int prec = 0; prec < 2; ++prec) {
     VecSet& V = S->vs[prec];
     void** all[] = {&V.r, &V.rhat, &V.p, &V.v, &V.s, &V.t, &V.y, &V.z, &V.q, &V.tmp, &V.u,

@@ -35,6 +35,47 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 void note_launches(long long n);
 long long launches_so_far();
 
+// ---- per-kernel timing of instrumented runs (ufg_profile_enable) ---------------------------
+bool profiling();
+// CUDA-graph replay of solver loops (off with UFG_NO_GRAPH=1)
+bool graphs_enabled();
+// Which work a launch does, for its algorithmic bytes: site_bytes[i] bytes for each problem i
+// whose solver flag lets it run (exec_if < 0: always), plus fixed_bytes.  The flags are copied on
+// the launch's stream just before it (flag i at flag_dev + i * stride bytes), so the stream is
+// never drained and the events time the kernel alone; the bytes are resolved when read.
+struct LaunchWork {
+  const int* flag_dev = nullptr;  // nullptr: every problem runs
+  size_t stride = sizeof(int);
+  int exec_if = -1;
+  std::vector<double> site_bytes;
+  double fixed_bytes = 0.0;
+};
+// Brackets the launches issued during its lifetime with CUDA events on `st` (no-op unless
+// profiling).
+class KTimer {
+ public:
+  KTimer(const std::string& name, cudaStream_t st, LaunchWork work);
+  ~KTimer();
+  KTimer(const KTimer&) = delete;
+  KTimer& operator=(const KTimer&) = delete;
+
+ private:
+  long long idx_ = -1;
+  cudaStream_t st_ = nullptr;
+  bool cap_ = false;
+};
+// Graph hooks: records made between capture_begin and capture_end belong to that graph and are
+// timed again after each replay (after_replay synchronises the stream while profiling).
+void profile_capture_begin();
+void profile_capture_end(cudaGraphExec_t ex);
+void profile_after_replay(cudaGraphExec_t ex, cudaStream_t st);
+void profile_graph_destroyed(cudaGraphExec_t ex);
+// "slice <family>[+epilogue operands] N<n> f32|f64" and the algorithmic bytes of one slice launch
+// per site and per problem (its per-mode tables).
+std::string slice_kernel_name(const SliceCall& c, int N);
+double slice_bytes_per_site(const SliceCall& c);
+double slice_bytes_per_problem(const SliceCall& c, int N);
+
 // ---- small device buffers -----------------------------------------------------------------
 template <typename T>
 ufg_status dev_alloc(T** p, size_t n) {

@@ -60,6 +60,11 @@ class Stats(ctypes.Structure):
         return d
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 64), ("launches", ctypes.c_longlong),
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 class Problem(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ntau", ctypes.c_int), ("tau", ctypes.c_double),
                 ("g", ctypes.c_double), ("sigma", ctypes.c_void_p), ("b", ctypes.c_void_p),
@@ -74,6 +79,8 @@ _SIGS = {
     "ufg_version": (ctypes.c_char_p, []),
     "ufg_supported_nx": (ctypes.c_char_p, []),
     "ufg_kernel_launches": (ctypes.c_longlong, []),
+    "ufg_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "ufg_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ufg_lattice_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp)]),
     "ufg_lattice_destroy": (None, [_vp]),
@@ -137,6 +144,30 @@ def load(path: str | None = None):
 
 def ufg_kernel_launches():
     return int(load().ufg_kernel_launches())
+
+
+def ufg_profile_enable(on=True):
+    """Per-kernel CUDA-event timing of the library's launches (direct launches, no graph replay)
+    until disabled; enabling clears earlier records."""
+    _check(load().ufg_profile_enable(1 if on else 0))
+
+
+def ufg_profile_read():
+    """[{name, launches, total_ms, bytes, us_per_launch, gbs}] sorted by total time."""
+    lib = load()
+    n = ctypes.c_int(0)
+    _check(lib.ufg_profile_read(None, 0, ctypes.byref(n)))
+    arr = (KernelStat * max(1, n.value))()
+    _check(lib.ufg_profile_read(ctypes.cast(arr, ctypes.c_void_p), n.value, ctypes.byref(n)))
+    out = []
+    for i in range(n.value):
+        k = arr[i]
+        ms = float(k.total_ms)
+        out.append({"name": k.name.decode(), "launches": int(k.launches), "total_ms": ms,
+                    "bytes": float(k.bytes),
+                    "us_per_launch": 1e3 * ms / max(1, k.launches),
+                    "gbs": float(k.bytes) / (ms * 1e-3) / 1e9 if ms > 0 else 0.0})
+    return out
 
 
 def _check(status):
