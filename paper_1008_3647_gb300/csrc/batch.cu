@@ -61,6 +61,7 @@ struct Batch {
   int nslice_ctas = 0;
   DevScalars* scs = nullptr;
   DevScalars* scs_h = nullptr;    // pinned
+  unsigned* counters = nullptr;   // per-problem CTA counters of fused scalar updates
   int* done_dummy = nullptr;
   double* w64 = nullptr;
   double* s64 = nullptr;
@@ -133,6 +134,11 @@ ufg_status slice(Batch& B, Group& g, SliceCall c, int exec_if) {
   c.exec_if = exec_if;
   c.nelem = B.S;
   if (c.partials) c.partials += 2 * (size_t)g.cta_base;
+  if (c.fop >= 0) {
+    c.scs = B.scs;
+    c.counters = B.counters;
+    c.part_base = g.cta_base;
+  }
   note_launches(1);
   KTimer kt(slice_kernel_name(c, g.lat->nx), B.st,
             batch_work(B, &g.probs, exec_if, slice_bytes_per_site(c),
@@ -142,9 +148,11 @@ ufg_status slice(Batch& B, Group& g, SliceCall c, int exec_if) {
   return UFG_OK;
 }
 
-// out = a * (A in) + bU * U with partials (out.dotP, out.out), all groups
+// out = a * (A in) + bU * U with partials (out.dotP, out.out), all groups; fop >= 0 applies that
+// scalar op to each problem from the partials in the same launch
 ufg_status apply_b(Batch& B, int prec, int op, const void* in, void* out, double a, const void* U,
-                   double bU, const void* dotP, bool self, double* part, int exec_if) {
+                   double bU, const void* dotP, bool self, double* part, int exec_if,
+                   int fop = -1) {
   for (auto& g : B.groups) {
     SliceCall c = base_call(g.lat, FAM_KIN, prec);
     c.in = in;
@@ -164,19 +172,22 @@ ufg_status apply_b(Batch& B, int prec, int op, const void* in, void* out, double
     c.want_dotP = dotP != nullptr;
     c.want_self = self;
     c.partials = part;
+    c.fop = fop;
     UFG_TRY(slice(B, g, c, exec_if));
   }
   return UFG_OK;
 }
 
 ufg_status vecb(Batch& B, int prec, int op, int exec_if, const void* a, const void* b,
-                const void* c, const void* d, const void* e, const void* f, double* part) {
+                const void* c, const void* d, const void* e, const void* f, double* part,
+                int fop = -1) {
   note_launches(1);
   KTimer kt(vec_op_name(op, prec), B.st,
             batch_work(B, nullptr, exec_if,
                        (prec ? 4.0 : 8.0) * vec_op_arrays(op, a != nullptr, c != nullptr)));
   cudaError_t err = launch_vec_batch(prec, op, B.vtiles, B.nvtiles, B.scs, exec_if, (void*)a,
-                                     (void*)b, (void*)c, (void*)d, (void*)e, (void*)f, part, B.st);
+                                     (void*)b, (void*)c, (void*)d, (void*)e, (void*)f, part, B.st,
+                                     fop, B.probs, B.counters);
   if (err != cudaSuccess) return cuda_fail(err, "batched vector kernel");
   return UFG_OK;
 }
@@ -331,31 +342,32 @@ ufg_status bicg_b(Batch& B, int prec, int op, const std::vector<double>& tol,
     UFG_TRY(vecb(B, prec, V_DOT, ex, V.rhat, V.r, V.r, V.r, nullptr, nullptr, B.slot(B_VEC2)));
     UFG_TRY(vecb(B, prec, V_DOT, ex, V.rhat, V.rhat, V.rhs, V.rhs, nullptr, nullptr,
                  B.slot(B_DOT)));
-    UFG_TRY(scalb(B, OP_BI_INIT, B.slot(B_VEC2), 1, B.slot(B_DOT), 1, ex));
+    // with the first iteration's rho (later ones come with each iteration's residual check)
+    UFG_TRY(scalb(B, OP_BI_INIT_RHO, B.slot(B_VEC2), 1, B.slot(B_DOT), 1, ex));
     return UFG_OK;
   };
   UFG_TRY(init(0, false));
+  // Each scalar step is applied by the last CTA of the kernel that produces its partials.
   auto body = [&]() -> ufg_status {
-    UFG_TRY(scalb(B, OP_BI_RHO, B.slot(B_VEC2), 1, nullptr, 1, 0));
     UFG_TRY(vecb(B, prec, V_BI_P, 0, V.p, V.r, V.v, nullptr, nullptr, nullptr, nullptr));
     const void* y = V.p;
     if (pc) {
       UFG_TRY(wce_b(B, prec, V.p, V.y, tr));
       y = V.y;
     }
-    UFG_TRY(apply_b(B, prec, op, y, V.v, 1.0, nullptr, 0.0, V.rhat, false, B.slot(B_SLICE1), 0));
-    UFG_TRY(scalb(B, OP_BI_ALPHA, B.slot(B_SLICE1), 0, nullptr, 0, 0));
-    UFG_TRY(vecb(B, prec, V_BI_S, 0, V.s, V.r, V.v, V.x, y, nullptr, B.slot(B_VEC1)));
-    UFG_TRY(scalb(B, OP_BI_SCHECK, B.slot(B_VEC1), 1, nullptr, 1, 0));
+    UFG_TRY(apply_b(B, prec, op, y, V.v, 1.0, nullptr, 0.0, V.rhat, false, B.slot(B_SLICE1), 0,
+                    OP_BI_ALPHA));
+    UFG_TRY(vecb(B, prec, V_BI_S, 0, V.s, V.r, V.v, V.x, y, nullptr, B.slot(B_VEC1),
+                 OP_BI_SCHECK));
     const void* z = V.s;
     if (pc) {
       UFG_TRY(wce_b(B, prec, V.s, V.z, tr));
       z = V.z;
     }
-    UFG_TRY(apply_b(B, prec, op, z, V.t, 1.0, nullptr, 0.0, V.s, true, B.slot(B_SLICE2), 0));
-    UFG_TRY(scalb(B, OP_BI_OMEGA, B.slot(B_SLICE2), 0, nullptr, 0, 0));
-    UFG_TRY(vecb(B, prec, V_BI_X, 0, V.x, z, V.r, V.s, V.t, V.rhat, B.slot(B_VEC2)));
-    UFG_TRY(scalb(B, OP_BI_RCHECK, B.slot(B_VEC2), 1, nullptr, 1, 0));
+    UFG_TRY(apply_b(B, prec, op, z, V.t, 1.0, nullptr, 0.0, V.s, true, B.slot(B_SLICE2), 0,
+                    OP_BI_OMEGA));
+    UFG_TRY(vecb(B, prec, V_BI_X, 0, V.x, z, V.r, V.s, V.t, V.rhat, B.slot(B_VEC2),
+                 OP_BI_RCHECK_RHO));
     return UFG_OK;
   };
   char key[128];
@@ -634,6 +646,8 @@ ufg_status setup(Batch& B, int n, const ufg_problem* probs) {
   }
   B.probs_h.assign(n, BatchProb{});
   UFG_TRY(B.alloc(&B.scs, (size_t)n));
+  UFG_TRY(B.alloc(&B.counters, (size_t)n));
+  UFG_CUDA(cudaMemset(B.counters, 0, n * sizeof(unsigned)));
   if (cudaMallocHost(&B.scs_h, n * sizeof(DevScalars)) != cudaSuccess ||
       cudaMallocHost(&B.scale_h, n * sizeof(double)) != cudaSuccess) {
     set_error("pinned allocation failed");

@@ -3,11 +3,13 @@
 #include <cstdint>
 
 #include "blas.cuh"
+#include "scalar_ops.cuh"
 #include "ufg_internal.h"
 
 namespace ufg {
 
 constexpr int VEC_NT = 256;
+static_assert(VEC_NT == SCAL_NT, "fused scalar updates reduce over SCAL_NT threads");
 
 std::string vec_op_name(int op, int prec) {
   static const char* n[] = {"cg_update", "cg_p", "bi_p", "bi_s", "bi_x", "dot", "copy", "zero", "add"};
@@ -159,10 +161,12 @@ __device__ __forceinline__ void vec_step(long long i, R al, R be, R om, R* a, R*
 
 // VECW: every operand is 16-byte aligned and each CTA's range is a whole number of 16-byte
 // vectors (the batched tiles always are); otherwise element by element.
+// Batched launches may also apply a scalar op (fop >= 0) to each problem from the partials
+// (last CTA of the problem's tiles, see last_block_update).
 template <typename R, int OP, bool VECW>
 __global__ void __launch_bounds__(VEC_NT)
-vec_kernel(long long n, const DevScalars* __restrict__ sc, R* a, R* b, R* c, R* d, R* e, R* f,
-           double* part, const int4* tiles, int exec_if) {
+vec_kernel(long long n, DevScalars* sc, R* a, R* b, R* c, R* d, R* e, R* f, double* part,
+           const int4* tiles, int exec_if, int fop, const BatchProb* probs, unsigned* counters) {
   constexpr int W = VECW ? 16 / (int)sizeof(R) : 1;
   long long lo = 0, hi = n, step = (long long)gridDim.x * VEC_NT * W;
   long long i0 = ((long long)blockIdx.x * VEC_NT + threadIdx.x) * W;
@@ -183,13 +187,20 @@ vec_kernel(long long n, const DevScalars* __restrict__ sc, R* a, R* b, R* c, R* 
 #pragma unroll 2
   for (long long i = i0; i < hi; i += step)
     vec_step<R, OP, W>(i, al, be, om, a, b, c, d, e, f, d1, d2);
-  if (part != nullptr) block_pair_store((double)d1, (double)d2, part);
+  if (part != nullptr) {
+    block_pair_store((double)d1, (double)d2, part);
+    if (fop >= 0 && tiles != nullptr) {
+      const int prob = tiles[blockIdx.x].x;
+      last_block_update(fop, sc, part, probs[prob].vt0, probs[prob].vt1, counters + prob);
+    }
+  }
 }
 
 template <typename R>
-static cudaError_t vec_dispatch(int op, long long n, const DevScalars* sc, R* a, R* b, R* c, R* d,
+static cudaError_t vec_dispatch(int op, long long n, DevScalars* sc, R* a, R* b, R* c, R* d,
                                 R* e, R* f, double* part, int grid, cudaStream_t st,
-                                const int4* tiles = nullptr, int exec_if = 0) {
+                                const int4* tiles = nullptr, int exec_if = 0, int fop = -1,
+                                const BatchProb* probs = nullptr, unsigned* counters = nullptr) {
   // 16-byte vectors when every operand is aligned and the ranges split into whole vectors
   // (batched tiles start on 256-element boundaries and have lengths divisible by 8)
   const uintptr_t al = reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
@@ -202,10 +213,11 @@ static cudaError_t vec_dispatch(int op, long long n, const DevScalars* sc, R* a,
   case OPC:                                                                                \
     if (vecw)                                                                              \
       vec_kernel<R, OPC, true><<<grid, VEC_NT, 0, st>>>(n, sc, a, b, c, d, e, f, part, tiles, \
-                                                        exec_if);                          \
+                                                        exec_if, fop, probs, counters);    \
     else                                                                                   \
       vec_kernel<R, OPC, false><<<grid, VEC_NT, 0, st>>>(n, sc, a, b, c, d, e, f, part,     \
-                                                         tiles, exec_if);                  \
+                                                         tiles, exec_if, fop, probs,       \
+                                                         counters);                        \
     break;
     CASE(V_CG_UPDATE)
     CASE(V_CG_P)
@@ -228,69 +240,36 @@ cudaError_t launch_vec(int prec, int op, long long n, const DevScalars* sc, void
                        cudaStream_t st) {
   const int grid = vec_grid(n);
   if (nparts) *nparts = grid;
+  DevScalars* s = const_cast<DevScalars*>(sc);  // read only (no fused scalar op here)
   if (prec == 0)
-    return vec_dispatch<double>(op, n, sc, (double*)a, (double*)b, (double*)c, (double*)d,
+    return vec_dispatch<double>(op, n, s, (double*)a, (double*)b, (double*)c, (double*)d,
                                 (double*)e, (double*)f, part, grid, st);
-  return vec_dispatch<float>(op, n, sc, (float*)a, (float*)b, (float*)c, (float*)d, (float*)e,
+  return vec_dispatch<float>(op, n, s, (float*)a, (float*)b, (float*)c, (float*)d, (float*)e,
                              (float*)f, part, grid, st);
 }
 
-cudaError_t launch_vec_batch(int prec, int op, const int4* tiles, int ntiles, const DevScalars* scs,
+cudaError_t launch_vec_batch(int prec, int op, const int4* tiles, int ntiles, DevScalars* scs,
                              int exec_if, void* a, void* b, void* c, void* d, void* e, void* f,
-                             double* part, cudaStream_t st) {
+                             double* part, cudaStream_t st, int fop, const BatchProb* probs,
+                             unsigned* counters) {
   if (ntiles <= 0) return cudaSuccess;
+  if (fop >= 0 && (part == nullptr || probs == nullptr || counters == nullptr))
+    return cudaErrorInvalidValue;
   if (prec == 0)
     return vec_dispatch<double>(op, 0, scs, (double*)a, (double*)b, (double*)c, (double*)d,
-                                (double*)e, (double*)f, part, ntiles, st, tiles, exec_if);
+                                (double*)e, (double*)f, part, ntiles, st, tiles, exec_if, fop,
+                                probs, counters);
   return vec_dispatch<float>(op, 0, scs, (float*)a, (float*)b, (float*)c, (float*)d, (float*)e,
-                             (float*)f, part, ntiles, st, tiles, exec_if);
+                             (float*)f, part, ntiles, st, tiles, exec_if, fop, probs, counters);
 }
 
 // ---- scalar kernels ------------------------------------------------------------------------
-// The four sums (pairs [i0, i1) of part, pairs [j0, j1) of part2) in one sweep: each thread adds
-// its strided share, the warps fold with shuffles and thread 0 adds the warp results in order
-// (a fixed, launch-independent order: the result is deterministic).  Valid in thread 0.
-__device__ void block_sums4(const double* part, int i0, int i1, const double* part2, int j0,
-                            int j1, double (&out)[4]) {
-  __shared__ double red[VEC_NT / 32][4];
-  double s[4] = {0.0, 0.0, 0.0, 0.0};
-  if (part != nullptr)
-    for (int i = i0 + (int)threadIdx.x; i < i1; i += VEC_NT) {
-      s[0] += part[2 * i];
-      s[1] += part[2 * i + 1];
-    }
-  if (part2 != nullptr)
-    for (int i = j0 + (int)threadIdx.x; i < j1; i += VEC_NT) {
-      s[2] += part2[2 * i];
-      s[3] += part2[2 * i + 1];
-    }
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], off);
-  if ((threadIdx.x & 31) == 0)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) red[threadIdx.x >> 5][k] = s[k];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      double t = 0.0;
-      for (int w = 0; w < VEC_NT / 32; ++w) t += red[w][k];
-      out[k] = t;
-    }
-  }
-}
 
-__device__ __forceinline__ bool bad(double v) { return !isfinite(v); }
-
-__device__ void scalar_update(int op, DevScalars* sc, const double* part, double a0, double a1,
-                              const double* part2, double b0, double b1);
 
 __global__ void __launch_bounds__(VEC_NT)
 scalar_kernel(int op, DevScalars* sc, const double* part, int nparts, const double* part2,
               int nparts2) {
-  if (op != OP_CG_INIT && op != OP_BI_INIT && sc->done) return;
+  if (op != OP_CG_INIT && op != OP_BI_INIT && op != OP_BI_INIT_RHO && sc->done) return;
   // every thread takes part in the block sums; thread 0 then updates the scalars
   double r[4];
   block_sums4(part, 0, nparts, part2, 0, nparts2, r);
@@ -310,90 +289,6 @@ scalar_batch_kernel(int op, DevScalars* scs, const BatchProb* probs, const doubl
   block_sums4(part, i0, i1, part2, j0, j1, r);
   if (threadIdx.x != 0) return;
   scalar_update(op, sc, part, r[0], r[1], part2, r[2], r[3]);
-}
-
-__device__ void scalar_update(int op, DevScalars* sc, const double* part, double a0, double a1,
-                              const double* part2, double b0, double b1) {
-  if ((op == OP_CG_INIT || op == OP_BI_INIT) && part2 != nullptr) sc->bn = sqrt(b1);  // rhs.rhs
-  const double tb = sc->tol * sc->bn;
-  switch (op) {
-    case OP_CG_INIT:  // part = (r.z, r.r), part2 = (-, rhs.rhs)
-      sc->rz = a0;
-      sc->rr = a1;
-      sc->done = 0;
-      if (bad(a0) || bad(a1)) sc->done = 4;
-      else if (sqrt(a1) <= tb) sc->done = 1;
-      break;
-    case OP_CG_ALPHA:  // part = slice partials (p.q, -)
-      sc->pq = a0;
-      sc->alpha = sc->rz / a0;
-      if (bad(sc->alpha)) sc->done = 4;
-      break;
-    case OP_CG_CHECK:  // part = (-, r.r)
-      sc->iters += 1;
-      sc->rr = a1;
-      if (bad(a1)) sc->done = 4;
-      else if (sqrt(a1) <= tb) sc->done = 1;
-      else if (sc->div_limit > 0 && sqrt(a1) > sc->div_limit * sc->bn) sc->done = 6;
-      else if (sc->iters >= sc->maxit) sc->done = 5;
-      break;
-    case OP_CG_BETA: {  // part = (r.z, -) or, without preconditioner, part2 = (-, r.r)
-      const double rz_new = part != nullptr ? a0 : b1;
-      sc->beta = rz_new / sc->rz;
-      sc->rz = rz_new;
-      if (bad(sc->beta)) sc->done = 4;
-      break;
-    }
-    case OP_BI_INIT:  // part = (rhat.r, r.r), part2 = (rhat.rhat, rhs.rhs)
-      sc->rho = a0;
-      sc->rr = a1;
-      sc->rhatn2 = b0;
-      sc->rho_old = 1.0;
-      sc->alpha = 1.0;
-      sc->omega = 1.0;
-      sc->done = 0;
-      if (bad(a0) || bad(a1)) sc->done = 4;
-      else if (sqrt(a1) <= tb) sc->done = 1;
-      break;
-    case OP_BI_RHO: {  // part = (rhat.r, r.r) of the last residual update (or of the init)
-      const double rho = a0;
-      if (fabs(rho) <= sc->restart_cos * sqrt(sc->rhatn2 * a1)) {
-        sc->done = 2;  // near-breakdown: the host restarts from the true residual
-        break;
-      }
-      sc->iters += 1;
-      sc->rho = rho;
-      sc->beta = (rho / sc->rho_old) * (sc->alpha / sc->omega);
-      if (bad(sc->beta)) sc->done = 4;
-      break;
-    }
-    case OP_BI_ALPHA:  // part = slice partials (v.rhat, -)
-      sc->alpha = sc->rho / a0;
-      if (bad(sc->alpha)) sc->done = 4;
-      break;
-    case OP_BI_SCHECK:  // part = (-, s.s)
-      sc->ss = a1;
-      if (bad(a1)) sc->done = 4;
-      else if (sqrt(a1) <= tb) sc->done = 1;
-      else if (sc->div_limit > 0 && sqrt(a1) > sc->div_limit * sc->bn) sc->done = 6;
-      break;
-    case OP_BI_OMEGA:  // part = slice partials (t.s, t.t)
-      sc->omega = a1 > 0.0 ? a0 / a1 : 0.0;
-      if (bad(sc->omega)) sc->done = 4;
-      break;
-    case OP_NORM2:  // part = (-, v.v)
-      sc->rr = a1;
-      break;
-    case OP_BI_RCHECK:  // part = (rhat.r, r.r)
-      sc->rr = a1;
-      sc->rho_old = sc->rho;
-      if (bad(a1)) sc->done = 4;
-      else if (sqrt(a1) <= tb) sc->done = 1;
-      else if (sc->div_limit > 0 && sqrt(a1) > sc->div_limit * sc->bn) sc->done = 6;
-      else if (sc->omega == 0.0) sc->done = 2;
-      else if (sc->iters >= sc->maxit) sc->done = 5;
-      break;
-  }
 }
 
 cudaError_t launch_scalar(int op, DevScalars* sc, const double* part, int nparts,

@@ -41,6 +41,8 @@ enum ScalarOp {
   OP_BI_OMEGA,      // omega = (t.s) / (t.t)
   OP_BI_RCHECK,     // rr = r.r, converged?, rho_old = rho
   OP_NORM2,         // rr = v.v only (no other state touched)
+  OP_BI_RCHECK_RHO, // OP_BI_RCHECK, then OP_BI_RHO on the same partials if still running
+  OP_BI_INIT_RHO,   // OP_BI_INIT, then OP_BI_RHO on the same partials if still running
 };
 
 // Partial pairs per producing CTA: up to this many CTAs per producer.
@@ -73,9 +75,12 @@ int vec_op_arrays(int op, bool a_present, bool c_present);
 
 // Batched form: CTA i works on tiles[i] = (problem, start, length) of the packed arenas with
 // the scalars scs[problem]; it runs while scs[problem].done == exec_if (exec_if < 0: always).
-cudaError_t launch_vec_batch(int prec, int op, const int4* tiles, int ntiles, const DevScalars* scs,
+// fop >= 0 also applies scalar op fop to each problem once all of its tiles have written their
+// partials (the last of them does it; counters: one per problem, zero between launches).
+cudaError_t launch_vec_batch(int prec, int op, const int4* tiles, int ntiles, DevScalars* scs,
                              int exec_if, void* a, void* b, void* c, void* d, void* e, void* f,
-                             double* part, cudaStream_t st);
+                             double* part, cudaStream_t st, int fop = -1,
+                             const BatchProb* probs = nullptr, unsigned* counters = nullptr);
 // Batched scalar kernel: CTA p reduces problem p's partials (kind 0: slice CTAs [st0, st1),
 // kind 1: vector CTAs [vt0, vt1)) and updates scs[p], while scs[p].done == exec_if.
 cudaError_t launch_scalar_batch(int op, DevScalars* scs, const BatchProb* probs, int nprob,

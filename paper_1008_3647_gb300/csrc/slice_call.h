@@ -28,6 +28,8 @@ struct BatchTile {
 // Run policy on the done flag: run while the flag equals exec_if (0: running, 2: restart
 // requested); exec_if = -1 runs unconditionally.
 
+struct DevScalars;
+
 // Runtime description of one slice launch (host side, type-erased pointers).
 struct SliceCall {
   int fam = FAM_KIN;
@@ -63,6 +65,11 @@ struct SliceCall {
   int spc = 1;                 // time slices per CTA (cluster)
   int C = 1;                   // cluster size (1, 2 or 4; N = 32 only uses 2 or 4)
   int nt = 256;                // threads per CTA (fixed at 256 in this build)
+  // batched mode: scalar op applied to each problem from the partials by its last CTA
+  int fop = -1;                // ScalarOp, -1: none
+  DevScalars* scs = nullptr;   // per-problem solver scalars
+  unsigned* counters = nullptr;  // per-problem CTA counters (zero between launches)
+  int part_base = 0;           // CTA index of this launch's first CTA in the problems' ranges
 };
 
 // Launches the slice kernel for lattice extent N (explicitly instantiated per N).

@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include "line_ops.cuh"
+#include "scalar_ops.cuh"
 #include "slice_call.h"
 
 namespace ufg {
@@ -59,6 +60,10 @@ struct SliceArgs {
   const BatchProb* probs;
   int scale_by_A;
   int ntau, shift, spc;
+  int fop;       // batched: scalar op of the problem's last CTA (-1: none), see SliceCall
+  DevScalars* scs;
+  unsigned* counters;
+  int part_base;
 };
 
 template <typename R> struct Vec16;
@@ -73,6 +78,7 @@ __device__ __forceinline__ void ld16(const R* p, R (&o)[Vec16<R>::W]) {
 }
 
 constexpr int SLICE_NT = 256;
+static_assert(SLICE_NT == SCAL_NT, "fused scalar updates reduce over SCAL_NT threads");
 
 // Epilogue operand mask: the specialised variants know at compile time which operands exist;
 // EPI_ANY tests every optional pointer at run time.
@@ -299,6 +305,11 @@ slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
       A.partials[2 * blockIdx.x] = d;
       A.partials[2 * blockIdx.x + 1] = q2;
     }
+    if (A.fop >= 0 && A.tiles != nullptr) {
+      const int prob = A.tiles[unit].prob;
+      last_block_update(A.fop, A.scs + prob, A.partials, A.probs[prob].st0 - A.part_base,
+                        A.probs[prob].st1 - A.part_base, A.counters + prob);
+    }
   }
   if constexpr (C > 1) cg::this_cluster().sync();  // peers may still read this CTA's planes
 }
@@ -330,6 +341,10 @@ inline void fill_args(SliceArgs<N, R>& a, const SliceCall& c) {
   a.tiles = c.tiles;
   a.probs = c.probs;
   a.scale_by_A = c.scale_by_A;
+  a.fop = c.fop;
+  a.scs = c.scs;
+  a.counters = c.counters;
+  a.part_base = c.part_base;
   a.ntau = c.ntau;
   a.shift = c.shift;
   a.spc = c.spc;

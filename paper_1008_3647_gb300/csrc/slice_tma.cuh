@@ -21,6 +21,7 @@
 
 #include "line_ops.cuh"
 #include "slice_call.h"
+#include "scalar_ops.cuh"
 #include "slice_kernel.cuh"
 
 namespace ufg {
@@ -53,6 +54,10 @@ struct TmaArgs {
   int scale_by_A;
   int ntau, shift, units, has_pre;
   int pre_mode;  // the multiplier box is a per-mode table (one slice, the same for every t)
+  int fop;       // batched: scalar op of the problem's last CTA (-1: none), see SliceCall
+  DevScalars* scs;
+  unsigned* counters;
+  int part_base;
   int* err;  // set on an mbarrier wait that ran out (never expected)
 };
 
@@ -112,6 +117,7 @@ __device__ __forceinline__ void tma_load_rows(void* dst, const CUtensorMap* tm, 
 }
 
 constexpr int TMA_NT = 256;
+static_assert(TMA_NT == SCAL_NT, "fused scalar updates reduce over SCAL_NT threads");
 constexpr uint32_t TMA_WAIT_LIMIT = 1u << 22;  // try_wait rounds before giving up (< 1 s)
 
 // Resident CTAs per SM the register allocation must allow.
@@ -312,6 +318,11 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
       A.partials[2 * blockIdx.x] = d;
       A.partials[2 * blockIdx.x + 1] = q2;
     }
+    if (A.fop >= 0 && A.tiles != nullptr) {
+      const int prob = A.tiles[unit].prob;
+      last_block_update(A.fop, A.scs + prob, A.partials, A.probs[prob].st0 - A.part_base,
+                        A.probs[prob].st1 - A.part_base, A.counters + prob);
+    }
   }
   if constexpr (C > 1) cg::this_cluster().sync();  // peers may still read this CTA's planes
 }
@@ -404,6 +415,10 @@ inline cudaError_t tma_launch_epi(const SliceCall& c, cudaStream_t st) {
   a.shift = c.shift;
   a.units = c.tiles != nullptr ? c.ntiles : c.ntau;
   a.err = c.err;
+  a.fop = c.fop;
+  a.scs = c.scs;
+  a.counters = c.counters;
+  a.part_base = c.part_base;
   const size_t smem = (size_t)(a.has_pre ? 2 : 1) * BUF * sizeof(R) + 1024;
   auto kern = slice_tma_kernel<N, R, C, FAM, EPI>;
   static int configured = 0;
