@@ -125,13 +125,95 @@ static bool reduce(int N, const std::vector<double>& A, bool in_spec, bool out_s
   return cross <= 1e-13 * std::fmax(scale, 1.0);
 }
 
+// Second-level split of one first-level block (see line_ops.cuh): M (n x n, row = output) maps
+// the block's inputs to its outputs; P_in rebuilds the block's inputs from (s, a), R_out takes the
+// block's outputs to (U, W).  Returns the U<-s and W<-a blocks of R_out M P_in, or false if its
+// cross blocks do not vanish.
+static bool split_block(int H, const std::vector<double>& M, bool sine, bool in_spec,
+                        bool out_spec, std::vector<double>& Bs, std::vector<double>& Ba) {
+  const int Q = H / 2;
+  const int n = sine ? H - 1 : H + 1;  // block indices: j0 .. j0 + n - 1
+  const int j0 = sine ? 1 : 0;
+  const int ns = sine ? Q : Q + 1, na = sine ? Q - 1 : Q;
+  // columns of P_in (n x (ns + na)) and rows of R_out ((ns + na) x n), in block-local indices
+  std::vector<double> P((size_t)n * (ns + na), 0.0), Rm((size_t)(ns + na) * n, 0.0);
+  auto at = [&](std::vector<double>& X, int rows_or_cols, int r, int c) -> double& {
+    return X[(size_t)r * rows_or_cols + c];
+  };
+  const int ncol = ns + na;
+  if (in_spec) {  // spectral side: parity selection
+    for (int m = 0; m < ns; ++m) at(P, ncol, (sine ? 2 * m + 1 : 2 * m) - j0, m) = 1.0;
+    for (int m = 0; m < na; ++m) at(P, ncol, (sine ? 2 * m + 2 : 2 * m + 1) - j0, ns + m) = 1.0;
+  } else {  // real side: pairs (j, H - j) and the centre Q
+    for (int m = 0; m < na; ++m) {
+      const int j = j0 + m;
+      at(P, ncol, j - j0, m) += 0.5;
+      at(P, ncol, H - j - j0, m) += 0.5;
+      at(P, ncol, j - j0, ns + m) += 0.5;
+      at(P, ncol, H - j - j0, ns + m) -= 0.5;
+    }
+    at(P, ncol, Q - j0, ns - 1) = 1.0;
+  }
+  if (out_spec) {
+    for (int m = 0; m < ns; ++m) at(Rm, n, m, (sine ? 2 * m + 1 : 2 * m) - j0) = 1.0;
+    for (int m = 0; m < na; ++m) at(Rm, n, ns + m, (sine ? 2 * m + 2 : 2 * m + 1) - j0) = 1.0;
+  } else {
+    for (int m = 0; m < na; ++m) {
+      const int j = j0 + m;
+      at(Rm, n, m, j - j0) += 0.5;
+      at(Rm, n, m, H - j - j0) += 0.5;
+      at(Rm, n, ns + m, j - j0) += 0.5;
+      at(Rm, n, ns + m, H - j - j0) -= 0.5;
+    }
+    at(Rm, n, ns - 1, Q - j0) = 1.0;
+  }
+  // B = R_out M P_in
+  std::vector<double> MP((size_t)n * ncol, 0.0), B((size_t)ncol * ncol, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int c = 0; c < ncol; ++c) {
+      double acc = 0.0;
+      for (int k = 0; k < n; ++k) acc += M[(size_t)i * n + k] * P[(size_t)k * ncol + c];
+      MP[(size_t)i * ncol + c] = acc;
+    }
+  double scale = 0.0, cross = 0.0;
+  for (int r = 0; r < ncol; ++r)
+    for (int c = 0; c < ncol; ++c) {
+      double acc = 0.0;
+      for (int k = 0; k < n; ++k) acc += Rm[(size_t)r * n + k] * MP[(size_t)k * ncol + c];
+      B[(size_t)r * ncol + c] = acc;
+      scale = std::fmax(scale, std::fabs(acc));
+      if ((r < ns) != (c < ns)) cross = std::fmax(cross, std::fabs(acc));
+    }
+  Bs.assign((size_t)ns * ns, 0.0);
+  Ba.assign((size_t)na * na, 0.0);
+  for (int r = 0; r < ns; ++r)
+    for (int c = 0; c < ns; ++c) Bs[(size_t)r * ns + c] = B[(size_t)r * ncol + c];
+  for (int r = 0; r < na; ++r)
+    for (int c = 0; c < na; ++c) Ba[(size_t)r * na + c] = B[(size_t)(ns + r) * ncol + ns + c];
+  return cross <= 1e-13 * std::fmax(scale, 1.0);
+}
+
+bool line_coef_flat(int N, const std::vector<double>& ce, const std::vector<double>& co,
+                    bool in_spec, bool out_spec, std::vector<double>& flat) {
+  const int H = N / 2;
+  flat.clear();
+  const bool two = (H % 2 == 0) && N >= 8;
+  if (!two) {
+    flat.insert(flat.end(), ce.begin(), ce.end());
+    flat.insert(flat.end(), co.begin(), co.end());
+    return true;
+  }
+  std::vector<double> cs, ca, ss, sa;
+  if (!split_block(H, ce, false, in_spec, out_spec, cs, ca) ||
+      !split_block(H, co, true, in_spec, out_spec, ss, sa))
+    return false;
+  for (auto* b : {&cs, &ca, &ss, &sa}) flat.insert(flat.end(), b->begin(), b->end());
+  return true;
+}
+
 template <typename R>
-static void pack(const std::vector<double>& ce, const std::vector<double>& co,
-                 std::vector<unsigned char>& out) {
-  std::vector<R> v;
-  v.reserve(ce.size() + co.size());
-  for (double d : ce) v.push_back((R)d);
-  for (double d : co) v.push_back((R)d);
+static void pack(const std::vector<double>& flat, std::vector<unsigned char>& out) {
+  std::vector<R> v(flat.begin(), flat.end());
   out.resize(v.size() * sizeof(R));
   std::memcpy(out.data(), v.data(), out.size());
 }
@@ -163,8 +245,13 @@ static ufg_status build_tables(ufg_lattice* L) {
       set_error("line operator of family %d does not split into even and odd parts", sp.fam);
       return UFG_INTERNAL;
     }
-    pack<double>(ce, co, L->coef[sp.fam][0]);
-    pack<float>(ce, co, L->coef[sp.fam][1]);
+    std::vector<double> flat;
+    if (!line_coef_flat(N, ce, co, sp.in_spec, sp.out_spec, flat)) {
+      set_error("line operator of family %d does not split at the second level", sp.fam);
+      return UFG_INTERNAL;
+    }
+    pack<double>(flat, L->coef[sp.fam][0]);
+    pack<float>(flat, L->coef[sp.fam][1]);
   }
   // per-mode table in spectral layout [sz][sy][sx]
   std::vector<double> bk((size_t)L->V);

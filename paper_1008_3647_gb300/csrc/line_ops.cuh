@@ -13,31 +13,69 @@
 //   REAL output: y_0 = E_0, y_H = E_H, y_i = E_i + O_i, y_{N-i} = E_i - O_i
 //   SPEC output: y_i = E_i (i = 0..H), y_{H+i} = O_i
 //
-// The reduced matrices ce ((H+1)^2) and co ((H-1)^2) are built on the host in FP64 for each operator
-// and live in the kernel's parameter space, so the compiler feeds them to FMA straight from the
-// constant bank.
+// When H = N/2 is even (N = 8, 12, 16, 32) each block splits once more.  The reflection
+// x -> H - x (mod N) also commutes with every operator here; on the cosine block it pairs e_j with
+// e_{H-j} and on the sine block o_j with o_{H-j}, while on the spectral side it is the sign
+// (-1)^k, so cosines of even k and sines of odd k are its symmetric part.  With Q = H/2:
+//
+//   cosine block, REAL side : s_m = e_m + e_{H-m}, a_m = e_m - e_{H-m} (m < Q), s_Q = e_Q
+//                 SPEC side : s_m = e_{2m} (m <= Q), a_m = e_{2m+1} (m < Q)
+//   sine block,   REAL side : s_m = o_{m+1} + o_{H-m-1}, a_m = o_{m+1} - o_{H-m-1} (m < Q-1),
+//                             s_{Q-1} = o_Q
+//                 SPEC side : s_m = o_{2m+1} (m < Q), a_m = o_{2m+2} (m < Q-1)
+//
+// (outputs recombine the same way, e.g. E_m = U_m + W_m, E_{H-m} = U_m - W_m), leaving four
+// blocks of (Q+1)^2, Q^2, Q^2 and (Q-1)^2 multiply-adds: 66 instead of 130 per line for N = 16,
+// 258 instead of 514 for N = 32.
+//
+// The reduced matrices are built on the host in FP64 for each operator and live in the kernel's
+// parameter space, so the compiler feeds them to FMA straight from the constant bank.  Layout of
+// LineCoef::c: one level: ce ((H+1)^2, row-major, row = output), then co ((H-1)^2); two levels:
+// the cosine-symmetric, cosine-antisymmetric, sine-symmetric and sine-antisymmetric blocks.
 #pragma once
 #include <cuda_runtime.h>
 
 namespace ufg {
 
-template <int N, typename R>
-struct LineCoef {
+template <int N>
+struct LineShape {
   static_assert(N >= 4 && N % 2 == 0, "line operators need an even N >= 4");
   static constexpr int H = N / 2;
-  R ce[(H + 1) * (H + 1)];
-  R co[(H - 1) * (H - 1)];
+  static constexpr int Q = H / 2;
+  static constexpr bool TWO = (H % 2 == 0) && N >= 8;  // two-level split
+  static constexpr int NC = TWO ? (Q + 1) * (Q + 1) + 2 * Q * Q + (Q - 1) * (Q - 1)
+                                : (H + 1) * (H + 1) + (H - 1) * (H - 1);
+  // block offsets (two levels)
+  static constexpr int B_CS = 0;
+  static constexpr int B_CA = (Q + 1) * (Q + 1);
+  static constexpr int B_SS = B_CA + Q * Q;
+  static constexpr int B_SA = B_SS + Q * Q;
+};
+
+template <int N, typename R>
+struct LineCoef {
+  R c[LineShape<N>::NC];
 };
 
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// row i of the n x n row-major block at c[off] times x
+template <int n, int off, typename R, int NC>
+__device__ __forceinline__ R block_row(const R (&c)[NC], const R* x, int i) {
+  R acc = c[off + i * n] * x[0];
+#pragma unroll
+  for (int j = 1; j < n; ++j) acc = fmadd(c[off + i * n + j], x[j], acc);
+  return acc;
+}
+
 // Applies the reduced operator to the line v[0..N) and hands every output (index, value) to st.
 template <int N, typename R, bool IN_SPEC, bool OUT_SPEC, class Store>
-__device__ __forceinline__ void line_op(const R (&v)[N], const LineCoef<N, R>& c, Store&& st) {
-  constexpr int H = N / 2;
+__device__ __forceinline__ void line_op(const R (&v)[N], const LineCoef<N, R>& cf, Store&& st) {
+  using S = LineShape<N>;
+  constexpr int H = S::H;
   R e[H + 1];
-  R o[H - 1];
+  R o[H - 1];  // o[j - 1] holds index j = 1 .. H-1
   if constexpr (IN_SPEC) {
 #pragma unroll
     for (int j = 0; j <= H; ++j) e[j] = v[j];
@@ -52,23 +90,90 @@ __device__ __forceinline__ void line_op(const R (&v)[N], const LineCoef<N, R>& c
       o[j - 1] = v[j] - v[N - j];
     }
   }
+  if constexpr (S::TWO) {
+    constexpr int Q = S::Q;
+    R cs[Q + 1], ca[Q], ss[Q], sa[Q - 1 > 0 ? Q - 1 : 1];
+    if constexpr (IN_SPEC) {
 #pragma unroll
-  for (int i = 0; i <= H; ++i) {
-    R E = c.ce[i * (H + 1)] * e[0];
+      for (int m = 0; m <= Q; ++m) cs[m] = e[2 * m];
 #pragma unroll
-    for (int j = 1; j <= H; ++j) E = fmadd(c.ce[i * (H + 1) + j], e[j], E);
-    if (i == 0 || i == H) {
-      st(i, E);
+      for (int m = 0; m < Q; ++m) ca[m] = e[2 * m + 1];
+#pragma unroll
+      for (int m = 0; m < Q; ++m) ss[m] = o[2 * m];  // k = 2m+1
+#pragma unroll
+      for (int m = 0; m < Q - 1; ++m) sa[m] = o[2 * m + 1];  // k = 2m+2
     } else {
-      R O = c.co[(i - 1) * (H - 1)] * o[0];
 #pragma unroll
-      for (int j = 2; j < H; ++j) O = fmadd(c.co[(i - 1) * (H - 1) + j - 1], o[j - 1], O);
-      if constexpr (OUT_SPEC) {
+      for (int m = 0; m < Q; ++m) {
+        cs[m] = e[m] + e[H - m];
+        ca[m] = e[m] - e[H - m];
+      }
+      cs[Q] = e[Q];
+#pragma unroll
+      for (int m = 0; m < Q - 1; ++m) {
+        ss[m] = o[m] + o[H - m - 2];  // o_{m+1} + o_{H-m-1}
+        sa[m] = o[m] - o[H - m - 2];
+      }
+      ss[Q - 1] = o[Q - 1];  // o_Q
+    }
+    // rows of the four blocks, each output emitted as soon as its rows are done
+    if constexpr (OUT_SPEC) {
+#pragma unroll
+      for (int m = 0; m <= Q; ++m) st(2 * m, block_row<Q + 1, S::B_CS>(cf.c, cs, m));
+#pragma unroll
+      for (int m = 0; m < Q; ++m) st(2 * m + 1, block_row<Q, S::B_CA>(cf.c, ca, m));
+#pragma unroll
+      for (int m = 0; m < Q; ++m) st(H + 2 * m + 1, block_row<Q, S::B_SS>(cf.c, ss, m));
+#pragma unroll
+      for (int m = 0; m < Q - 1; ++m) st(H + 2 * m + 2, block_row<Q - 1, S::B_SA>(cf.c, sa, m));
+    } else {
+      // E_m = U_m + W_m, E_{H-m} = U_m - W_m, E_Q = U_Q; O_m = Us_{m-1} + Ws_{m-1},
+      // O_{H-m} = Us_{m-1} - Ws_{m-1}, O_Q = Us_{Q-1}; y_i = E_i + O_i, y_{N-i} = E_i - O_i
+      {
+        const R U = block_row<Q + 1, S::B_CS>(cf.c, cs, 0);
+        const R W = block_row<Q, S::B_CA>(cf.c, ca, 0);
+        st(0, U + W);
+        st(H, U - W);
+      }
+#pragma unroll
+      for (int m = 1; m < Q; ++m) {
+        const R U = block_row<Q + 1, S::B_CS>(cf.c, cs, m);
+        const R W = block_row<Q, S::B_CA>(cf.c, ca, m);
+        const R Us = block_row<Q, S::B_SS>(cf.c, ss, m - 1);
+        const R Ws = block_row<Q - 1, S::B_SA>(cf.c, sa, m - 1);
+        const R Em = U + W, Eh = U - W, Om = Us + Ws, Oh = Us - Ws;
+        st(m, Em + Om);
+        st(N - m, Em - Om);
+        st(H - m, Eh + Oh);
+        st(H + m, Eh - Oh);  // N - (H - m)
+      }
+      {
+        const R U = block_row<Q + 1, S::B_CS>(cf.c, cs, Q);
+        const R Us = block_row<Q, S::B_SS>(cf.c, ss, Q - 1);
+        st(Q, U + Us);
+        st(N - Q, U - Us);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i <= H; ++i) {
+      R E = cf.c[i * (H + 1)] * e[0];
+#pragma unroll
+      for (int j = 1; j <= H; ++j) E = fmadd(cf.c[i * (H + 1) + j], e[j], E);
+      if (i == 0 || i == H) {
         st(i, E);
-        st(H + i, O);
       } else {
-        st(i, E + O);
-        st(N - i, E - O);
+        constexpr int OFF = (H + 1) * (H + 1);
+        R O = cf.c[OFF + (i - 1) * (H - 1)] * o[0];
+#pragma unroll
+        for (int j = 2; j < H; ++j) O = fmadd(cf.c[OFF + (i - 1) * (H - 1) + j - 1], o[j - 1], O);
+        if constexpr (OUT_SPEC) {
+          st(i, E);
+          st(H + i, O);
+        } else {
+          st(i, E + O);
+          st(N - i, E - O);
+        }
       }
     }
   }

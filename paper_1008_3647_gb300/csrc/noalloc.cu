@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "line_ops.cuh"
 #include "ufg_internal.h"
@@ -58,12 +59,13 @@ __global__ void noalloc_w_kernel(const double* __restrict__ sigma, double A, lon
   }
 }
 
-// exp(-tau K) along one axis as the even/odd reduced matrices, computed on the stack: the
-// circulant T[d] = (1/N) sum_n exp(-tau E1(k_n)) cos(k_n d), then
+// exp(-tau K) along one axis as the even/odd reduced matrices: the circulant
+// T[d] = (1/N) sum_n exp(-tau E1(k_n)) cos(k_n d), then
 //   ce[i][0] = T[i], ce[i][H] = T[i-H], ce[i][j] = (T[i-j] + T[i+j]) / 2,
-//   co[i][j] = (T[i-j] - T[i+j]) / 2   (indices mod N).
+//   co[i][j] = (T[i-j] - T[i+j]) / 2   (indices mod N),
+// split further into the kernel's coefficient layout (host memory only).
 template <int N>
-void kinetic_coef(double tau, int dispersion, LineCoef<N, double>* c) {
+bool kinetic_coef(double tau, int dispersion, LineCoef<N, double>* c) {
   constexpr int H = N / 2;
   const double pi = 3.14159265358979323846;
   double T[N];
@@ -78,18 +80,26 @@ void kinetic_coef(double tau, int dispersion, LineCoef<N, double>* c) {
     T[d] = acc / N;
   }
   auto t = [&](int d) { return T[((d % N) + N) % N]; };
+  std::vector<double> ce((H + 1) * (H + 1)), co((H - 1) * (H - 1)), flat;
   for (int i = 0; i <= H; ++i)
     for (int j = 0; j <= H; ++j)
-      c->ce[i * (H + 1) + j] = (j == 0 || j == H) ? t(i - j) : 0.5 * (t(i - j) + t(i + j));
+      ce[i * (H + 1) + j] = (j == 0 || j == H) ? t(i - j) : 0.5 * (t(i - j) + t(i + j));
   for (int i = 1; i < H; ++i)
-    for (int j = 1; j < H; ++j) c->co[(i - 1) * (H - 1) + (j - 1)] = 0.5 * (t(i - j) - t(i + j));
+    for (int j = 1; j < H; ++j) co[(i - 1) * (H - 1) + (j - 1)] = 0.5 * (t(i - j) - t(i + j));
+  if (!line_coef_flat(N, ce, co, false, false, flat) || (int)flat.size() != LineShape<N>::NC)
+    return false;
+  for (int i = 0; i < LineShape<N>::NC; ++i) c->c[i] = flat[i];
+  return true;
 }
 
 template <int N>
 ufg_status run_q(int ntau, double tau, int dispersion, double A, const double* x, double* y,
                  double* w, double* t, cudaStream_t st) {
   LineCoef<N, double> coef;
-  kinetic_coef<N>(tau, dispersion, &coef);
+  if (!kinetic_coef<N>(tau, dispersion, &coef)) {
+    set_error("apply_Q_noalloc: kinetic line operator does not split");
+    return UFG_INTERNAL;
+  }
   SliceCall c;
   c.fam = FAM_KIN;
   c.prec = 0;

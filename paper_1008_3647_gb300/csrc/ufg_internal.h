@@ -76,6 +76,11 @@ std::string slice_kernel_name(const SliceCall& c, int N);
 double slice_bytes_per_site(const SliceCall& c);
 double slice_bytes_per_problem(const SliceCall& c, int N);
 
+// Flat line-operator coefficients (LineCoef layout, line_ops.cuh) from the first-level blocks ce,
+// co of an operator; false if the second-level split does not hold.
+bool line_coef_flat(int N, const std::vector<double>& ce, const std::vector<double>& co,
+                    bool in_spec, bool out_spec, std::vector<double>& flat);
+
 // ---- small device buffers -----------------------------------------------------------------
 template <typename T>
 ufg_status dev_alloc(T** p, size_t n) {
