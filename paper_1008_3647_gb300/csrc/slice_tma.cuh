@@ -143,7 +143,7 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   constexpr int EPC = 16 / (int)sizeof(R);
   constexpr bool IN_SPEC = (FAM == FAM_INV);
   constexpr bool OUT_SPEC = (FAM == FAM_FWD);
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  extern __shared__ __align__(1024) unsigned char tma_smem[];
   __shared__ double red[TMA_NT / 32][2];
   __shared__ alignas(8) uint64_t bar;
 
@@ -172,7 +172,7 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   if (A.shift < 0) t_in = (t_out == 0) ? ntau - 1 : t_out - 1;
   if (A.shift > 0) t_in = (t_out == ntau - 1) ? 0 : t_out + 1;
   // swizzled boxes need a 1024-byte aligned destination: align the dynamic region explicitly
-  unsigned char* const base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  unsigned char* const base = tma_smem + ((1024u - (smem_addr(tma_smem) & 1023u)) & 1023u);
   R* const xs = reinterpret_cast<R*>(base);
   const R* const ws = reinterpret_cast<R*>(base) + BUF;
 
@@ -212,29 +212,46 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
     }
     line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_x, [&](int i, R val) { xs[G::off(r, i)] = val; });
   }
-  __syncthreads();
-  // ---- y-pass ----
-  for (int l = tid; l < NP * N; l += TMA_NT) {
-    const int p = l / N, x = l - (l / N) * N;
-    R v[N];
-#pragma unroll
-    for (int y = 0; y < N; ++y) v[y] = xs[G::off(p * N + y, x)];
-    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_y,
-                                     [&](int i, R val) { xs[G::off(p * N + i, x)] = val; });
-  }
+  // Clusters exchange by pushing: the y-pass stores each result straight into the CTA that owns
+  // its z-column (rows [o RY, (o+1) RY) of every plane belong to CTA o), in that CTA's
+  // multiplier box, so the z-pass reads local shared memory only.  The first cluster barrier
+  // frees every multiplier box, the second publishes the pushed columns.
+  constexpr int RY = N / C;
+  R* const recv = xs + BUF;  // [plane z][row y - rank RY][x], plain layout
   if constexpr (C > 1) {
     cg::this_cluster().sync();
   } else {
     __syncthreads();
   }
-  const R* owner[C];
+  // ---- y-pass ----
+  R* rdst[C];
 #pragma unroll
   for (int o = 0; o < C; ++o) {
     if constexpr (C > 1) {
-      owner[o] = (o == rank) ? xs : cg::this_cluster().map_shared_rank(xs, o);
+      rdst[o] = cg::this_cluster().map_shared_rank(recv, o);
     } else {
-      owner[o] = xs;
+      rdst[o] = recv;
     }
+  }
+  for (int l = tid; l < NP * N; l += TMA_NT) {
+    const int p = l / N, x = l - (l / N) * N;
+    R v[N];
+#pragma unroll
+    for (int y = 0; y < N; ++y) v[y] = xs[G::off(p * N + y, x)];
+    if constexpr (C > 1) {
+      const int zrow = (rank * NP + p) * RY;
+      line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_y, [&](int i, R val) {
+        rdst[i / RY][(zrow + i % RY) * N + x] = val;
+      });
+    } else {
+      line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_y,
+                                       [&](int i, R val) { xs[G::off(p * N + i, x)] = val; });
+    }
+  }
+  if constexpr (C > 1) {
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
   }
   // ---- z-pass + epilogue ----
   constexpr int COLS = NN / C;
@@ -256,8 +273,14 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
     const int q = rank * COLS + l;
     const int y = q / N, x = q - (q / N) * N;
     R v[N];
+    if constexpr (C > 1) {
+      const int yl = y - rank * RY;
 #pragma unroll
-    for (int z = 0; z < N; ++z) v[z] = owner[z / NP][G::off((z % NP) * N + y, x)];
+      for (int z = 0; z < N; ++z) v[z] = recv[(z * RY + yl) * N + x];
+    } else {
+#pragma unroll
+      for (int z = 0; z < N; ++z) v[z] = xs[G::off(z * N + y, x)];
+    }
     const size_t obase = (size_t)t_out * VOL + q;
     line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_z, [&](int zp, R val) {
       const size_t g = obase + (size_t)zp * NN;
@@ -324,7 +347,6 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
                         A.probs[prob].st1 - A.part_base, A.counters + prob);
     }
   }
-  if constexpr (C > 1) cg::this_cluster().sync();  // peers may still read this CTA's planes
 }
 
 }  // namespace ufg
@@ -419,7 +441,8 @@ inline cudaError_t tma_launch_epi(const SliceCall& c, cudaStream_t st) {
   a.scs = c.scs;
   a.counters = c.counters;
   a.part_base = c.part_base;
-  const size_t smem = (size_t)(a.has_pre ? 2 : 1) * BUF * sizeof(R) + 1024;
+  // clusters need the second box as the z-column receive buffer
+  const size_t smem = (size_t)((a.has_pre || C > 1) ? 2 : 1) * BUF * sizeof(R) + 1024;
   auto kern = slice_tma_kernel<N, R, C, FAM, EPI>;
   static int configured = 0;
   if (!configured) {
@@ -542,7 +565,7 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
   using G = SwzGeom<N, R>;
   constexpr int NN = N * N;
   constexpr int VOL = N * NN;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  extern __shared__ __align__(1024) unsigned char tma_smem[];
   __shared__ alignas(8) uint64_t bar;
   const int tid = threadIdx.x;
   int t_out, ntau;
@@ -566,7 +589,7 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
                             : (t_out == ntau - 1 ? 0 : t_out + 1);
   const R sgn = (DIR == 0 ? t_out != 0 : t_out != ntau - 1) ? R(-1) : R(1);
   const int t_s = DIR == 0 ? t_in : t_out;  // slice of the site multiplier
-  unsigned char* const base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  unsigned char* const base = tma_smem + ((1024u - (smem_addr(tma_smem) & 1023u)) & 1023u);
   R* const xs = reinterpret_cast<R*>(base);
   R* const ss = xs + VOL;
   R* const ks = ss + VOL;
