@@ -20,6 +20,7 @@
 
 #include "blas.cuh"
 #include "ufg_internal.h"
+#include "launch.cuh"
 
 using namespace ufg;
 
@@ -459,6 +460,7 @@ ufg_status norms_b(Batch& B, const double* v, std::vector<double>& out) {
 
 __global__ void mixed_batch_kernel(const int4* tiles, const double* scale, double* x64, float* y32,
                                    int mode) {
+  pdl_begin();
   const int4 tl = tiles[blockIdx.x];
   const double sc = scale[tl.x];
   for (long long i = (long long)tl.y + threadIdx.x; i < (long long)tl.y + tl.z; i += blockDim.x) {
@@ -469,6 +471,7 @@ __global__ void mixed_batch_kernel(const int4* tiles, const double* scale, doubl
 
 __global__ void axpy_batch_kernel(const int4* tiles, const double* scale, double* x,
                                   const double* y, int copy) {
+  pdl_begin();
   const int4 tl = tiles[blockIdx.x];
   const double sc = scale[tl.x];
   if (sc == 0.0) return;
@@ -483,8 +486,8 @@ ufg_status axpy_b(Batch& B, double* x, const double* y, const std::vector<double
   UFG_CUDA(cudaMemcpyAsync(B.scale, B.scale_h, B.n * sizeof(double), cudaMemcpyHostToDevice, B.st));
   note_launches(1);
   KTimer kt("batch axpy f64", B.st, batch_work(B, nullptr, -1, copy ? 16.0 : 24.0));
-  axpy_batch_kernel<<<B.nvtiles, 256, 0, B.st>>>(B.vtiles, B.scale, x, y, copy);
-  UFG_CUDA(cudaGetLastError());
+  UFG_CUDA(launch_k(axpy_batch_kernel, dim3(B.nvtiles), dim3(256), 0, B.st, 1,
+                    (const int4*)B.vtiles, (const double*)B.scale, x, y, copy));
   return UFG_OK;
 }
 
@@ -493,8 +496,8 @@ ufg_status mixed_glue(Batch& B, int mode, double* x64, float* y32, const std::ve
   UFG_CUDA(cudaMemcpyAsync(B.scale, B.scale_h, B.n * sizeof(double), cudaMemcpyHostToDevice, B.st));
   note_launches(1);
   KTimer kt("batch mixed glue", B.st, batch_work(B, nullptr, -1, mode ? 20.0 : 12.0));
-  mixed_batch_kernel<<<B.nvtiles, 256, 0, B.st>>>(B.vtiles, B.scale, x64, y32, mode);
-  UFG_CUDA(cudaGetLastError());
+  UFG_CUDA(launch_k(mixed_batch_kernel, dim3(B.nvtiles), dim3(256), 0, B.st, 1,
+                    (const int4*)B.vtiles, (const double*)B.scale, x64, y32, mode));
   return UFG_OK;
 }
 

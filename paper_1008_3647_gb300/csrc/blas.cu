@@ -5,6 +5,7 @@
 #include "blas.cuh"
 #include "scalar_ops.cuh"
 #include "ufg_internal.h"
+#include "launch.cuh"
 
 namespace ufg {
 
@@ -167,6 +168,7 @@ template <typename R, int OP, bool VECW>
 __global__ void __launch_bounds__(VEC_NT)
 vec_kernel(long long n, DevScalars* sc, R* a, R* b, R* c, R* d, R* e, R* f, double* part,
            const int4* tiles, int exec_if, int fop, const BatchProb* probs, unsigned* counters) {
+  pdl_begin();
   constexpr int W = VECW ? 16 / (int)sizeof(R) : 1;
   long long lo = 0, hi = n, step = (long long)gridDim.x * VEC_NT * W;
   long long i0 = ((long long)blockIdx.x * VEC_NT + threadIdx.x) * W;
@@ -211,14 +213,11 @@ static cudaError_t vec_dispatch(int op, long long n, DevScalars* sc, R* a, R* b,
   switch (op) {
 #define CASE(OPC)                                                                          \
   case OPC:                                                                                \
-    if (vecw)                                                                              \
-      vec_kernel<R, OPC, true><<<grid, VEC_NT, 0, st>>>(n, sc, a, b, c, d, e, f, part, tiles, \
-                                                        exec_if, fop, probs, counters);    \
-    else                                                                                   \
-      vec_kernel<R, OPC, false><<<grid, VEC_NT, 0, st>>>(n, sc, a, b, c, d, e, f, part,     \
-                                                         tiles, exec_if, fop, probs,       \
-                                                         counters);                        \
-    break;
+    return vecw ? launch_k(vec_kernel<R, OPC, true>, dim3(grid), dim3(VEC_NT), 0, st, 1, n, sc, \
+                           a, b, c, d, e, f, part, tiles, exec_if, fop, probs, counters)   \
+                : launch_k(vec_kernel<R, OPC, false>, dim3(grid), dim3(VEC_NT), 0, st, 1, n,  \
+                           sc, a, b, c, d, e, f, part, tiles, exec_if, fop, probs,         \
+                           counters);
     CASE(V_CG_UPDATE)
     CASE(V_CG_P)
     CASE(V_BI_P)
@@ -269,6 +268,7 @@ cudaError_t launch_vec_batch(int prec, int op, const int4* tiles, int ntiles, De
 __global__ void __launch_bounds__(VEC_NT)
 scalar_kernel(int op, DevScalars* sc, const double* part, int nparts, const double* part2,
               int nparts2) {
+  pdl_begin();
   if (op != OP_CG_INIT && op != OP_BI_INIT && op != OP_BI_INIT_RHO && sc->done) return;
   // every thread takes part in the block sums; thread 0 then updates the scalars
   double r[4];
@@ -280,6 +280,7 @@ scalar_kernel(int op, DevScalars* sc, const double* part, int nparts, const doub
 __global__ void __launch_bounds__(VEC_NT)
 scalar_batch_kernel(int op, DevScalars* scs, const BatchProb* probs, const double* part, int kind,
                     const double* part2, int kind2, int exec_if) {
+  pdl_begin();
   DevScalars* sc = scs + blockIdx.x;
   const BatchProb& pr = probs[blockIdx.x];
   if (exec_if >= 0 && sc->done != exec_if) return;
@@ -293,52 +294,51 @@ scalar_batch_kernel(int op, DevScalars* scs, const BatchProb* probs, const doubl
 
 cudaError_t launch_scalar(int op, DevScalars* sc, const double* part, int nparts,
                           const double* part2, int nparts2, cudaStream_t st) {
-  scalar_kernel<<<1, VEC_NT, 0, st>>>(op, sc, part, nparts, part2, nparts2);
-  return cudaGetLastError();
+  return launch_k(scalar_kernel, dim3(1), dim3(VEC_NT), 0, st, 1, op, sc, part, nparts, part2,
+                  nparts2);
 }
 
 cudaError_t launch_scalar_batch(int op, DevScalars* scs, const BatchProb* probs, int nprob,
                                 const double* part, int kind, const double* part2, int kind2,
                                 int exec_if, cudaStream_t st) {
   if (nprob <= 0) return cudaSuccess;
-  scalar_batch_kernel<<<nprob, VEC_NT, 0, st>>>(op, scs, probs, part, kind, part2, kind2,
-                                                exec_if);
-  return cudaGetLastError();
+  return launch_k(scalar_batch_kernel, dim3(nprob), dim3(VEC_NT), 0, st, 1, op, scs, probs, part,
+                  kind, part2, kind2, exec_if);
 }
 
 // ---- mixed precision glue ------------------------------------------------------------------
 __global__ void to_f32_kernel(const double* x, double scale, float* y, long long n) {
+  pdl_begin();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     y[i] = (float)(scale * x[i]);
 }
 
 __global__ void axpy_mixed_kernel(double* x, const float* e, double scale, long long n) {
+  pdl_begin();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     x[i] += scale * (double)e[i];
 }
 
 cudaError_t launch_to_f32(const double* x, double scale, float* y, long long n, cudaStream_t st) {
-  to_f32_kernel<<<vec_grid(n), VEC_NT, 0, st>>>(x, scale, y, n);
-  return cudaGetLastError();
+  return launch_k(to_f32_kernel, dim3(vec_grid(n)), dim3(VEC_NT), 0, st, 1, x, scale, y, n);
 }
 
 cudaError_t launch_axpy_f32_to_f64(double* x, const float* e, double scale, long long n,
                                    cudaStream_t st) {
-  axpy_mixed_kernel<<<vec_grid(n), VEC_NT, 0, st>>>(x, e, scale, n);
-  return cudaGetLastError();
+  return launch_k(axpy_mixed_kernel, dim3(vec_grid(n)), dim3(VEC_NT), 0, st, 1, x, e, scale, n);
 }
 
 __global__ void reduce_to_kernel(const double* part, int nparts, int k, double* out) {
+  pdl_begin();
   double r[4];
   block_sums4(part, 0, nparts, nullptr, 0, 0, r);
   if (threadIdx.x == 0) *out = r[k];
 }
 
 cudaError_t launch_reduce_to(const double* part, int nparts, int k, double* out, cudaStream_t st) {
-  reduce_to_kernel<<<1, VEC_NT, 0, st>>>(part, nparts, k, out);
-  return cudaGetLastError();
+  return launch_k(reduce_to_kernel, dim3(1), dim3(VEC_NT), 0, st, 1, part, nparts, k, out);
 }
 
 }  // namespace ufg

@@ -14,6 +14,7 @@
 
 #include "line_ops.cuh"
 #include "ufg_internal.h"
+#include "launch.cuh"
 
 namespace ufg {
 
@@ -51,6 +52,7 @@ ufg_status scratch_for_current_device(double** out) {
 
 __global__ void noalloc_w_kernel(const double* __restrict__ sigma, double A, long long S,
                                  double* w) {
+  pdl_begin();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S;
        i += (long long)gridDim.x * blockDim.x) {
     double sn, cs;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "ufg_internal.h"
+#include "launch.cuh"
 
 namespace ufg {
 
@@ -10,6 +11,7 @@ namespace ufg {
 __global__ void potentials_kernel(const double* __restrict__ sigma, double A, long long S,
                                   double* w64, double* s64, double* c64, float* w32, float* s32,
                                   float* c32) {
+  pdl_begin();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S;
        i += (long long)gridDim.x * blockDim.x) {
     double sn, cs;
@@ -29,8 +31,8 @@ cudaError_t launch_potentials(const double* sigma, double A, long long S, double
   const int nt = 256;
   long long blocks = (S + nt - 1) / nt;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  potentials_kernel<<<(unsigned)blocks, nt, 0, st>>>(sigma, A, S, w64, s64, c64, w32, s32, c32);
-  return cudaGetLastError();
+  return launch_k(potentials_kernel, dim3((unsigned)blocks), dim3(nt), 0, st, 1, sigma, A, S, w64,
+                  s64, c64, w32, s32, c32);
 }
 
 // ---- exact M0^{-1} per momentum mode ------------------------------------------------------
@@ -69,6 +71,7 @@ struct RecArgs {
 
 template <typename R, int ACC, bool OUT>  // ACC = acc_mode; OUT: write out
 __global__ void __launch_bounds__(32 * REC_NCH, sizeof(R) == 4 ? 8 : 5) recurrence_kernel(const RecArgs<R> a) {
+  pdl_begin();
   __shared__ R Es[REC_NCH][32];
   __shared__ R Ps[REC_NCH][32];
   __shared__ R Is[REC_NCH][32];
@@ -149,14 +152,13 @@ static cudaError_t rec_launch(const RecArgs<R>& a, unsigned grid, cudaStream_t s
   const bool out = a.out != nullptr;
   if (a.acc_mode != 0 && a.acc == nullptr) return cudaErrorInvalidValue;
   switch (a.acc_mode * 2 + (out ? 1 : 0)) {
-    case 1: recurrence_kernel<R, 0, true><<<grid, blk, 0, st>>>(a); break;
-    case 2: recurrence_kernel<R, 1, false><<<grid, blk, 0, st>>>(a); break;
-    case 3: recurrence_kernel<R, 1, true><<<grid, blk, 0, st>>>(a); break;
-    case 4: recurrence_kernel<R, 2, false><<<grid, blk, 0, st>>>(a); break;
-    case 5: recurrence_kernel<R, 2, true><<<grid, blk, 0, st>>>(a); break;
-    default: return cudaErrorInvalidValue;  // nothing to write
+    case 1: return launch_k(recurrence_kernel<R, 0, true>, dim3(grid), blk, 0, st, 1, a);
+    case 2: return launch_k(recurrence_kernel<R, 1, false>, dim3(grid), blk, 0, st, 1, a);
+    case 3: return launch_k(recurrence_kernel<R, 1, true>, dim3(grid), blk, 0, st, 1, a);
+    case 4: return launch_k(recurrence_kernel<R, 2, false>, dim3(grid), blk, 0, st, 1, a);
+    case 5: return launch_k(recurrence_kernel<R, 2, true>, dim3(grid), blk, 0, st, 1, a);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;  // nothing to write
 }
 
 cudaError_t launch_recurrence(int prec, const void* in, void* out, const void* bk, long long V,
@@ -198,6 +200,7 @@ cudaError_t launch_recurrence_batch(int prec, const void* in, void* out, const v
 // Stored: L and 1/D, FP64 and FP32.
 __global__ void sca_setup_kernel(const double* __restrict__ w, long long V, int ntau, double alpha,
                                  double* L64, double* Di64, float* L32, float* Di32) {
+  pdl_begin();
   const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (r >= V) return;
   const double w0 = w[r];
@@ -235,6 +238,7 @@ cudaError_t launch_sca_setup(const double* w64, long long V, int ntau, double al
 template <typename R>
 __global__ void sca_apply_kernel(const R* __restrict__ L, const R* __restrict__ Di, const R* y,
                                  R* z, long long V, int ntau, const int* done) {
+  pdl_begin();
   if (done != nullptr && *done) return;
   const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (r >= V) return;

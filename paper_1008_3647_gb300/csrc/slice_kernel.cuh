@@ -28,6 +28,7 @@
 #include "line_ops.cuh"
 #include "scalar_ops.cuh"
 #include "slice_call.h"
+#include "launch.cuh"
 
 namespace ufg {
 
@@ -93,6 +94,7 @@ constexpr int slice_min_blocks() {
 template <int N, typename R, int C, int FAM, int EPI>
 __global__ void __launch_bounds__(SLICE_NT, (slice_min_blocks<N, R>()))
 slice_kernel(const __grid_constant__ SliceArgs<N, R> A) {
+  pdl_begin();
   constexpr int NP = N / C;          // z-planes of one slice held by this CTA
   constexpr int PITCH = N + 1;       // padded row
   constexpr int PLANE = N * PITCH;   // shared-memory elements per plane
@@ -370,21 +372,7 @@ inline cudaError_t launch_epi(const SliceCall& c, cudaStream_t st) {
   }
   const int units = c.tiles != nullptr ? c.ntiles : (c.ntau + c.spc - 1) / c.spc;
   if (c.grid_out) *c.grid_out = units * C;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(units * C);
-  cfg.blockDim = dim3(SLICE_NT);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  if (C > 1) {
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-  }
-  return cudaLaunchKernelEx(&cfg, kern, a);
+  return launch_k(kern, dim3(units * C), dim3(SLICE_NT), smem, st, C, a);
 }
 
 template <int N, typename R, int C, int FAM>

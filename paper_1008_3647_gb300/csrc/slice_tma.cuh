@@ -23,6 +23,7 @@
 #include "slice_call.h"
 #include "scalar_ops.cuh"
 #include "slice_kernel.cuh"
+#include "launch.cuh"
 
 namespace ufg {
 
@@ -132,6 +133,7 @@ constexpr int tma_min_blocks() {
 template <int N, typename R, int C, int FAM, int EPI>
 __global__ void __launch_bounds__(TMA_NT, (tma_min_blocks<N, R>()))
 slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
+  pdl_begin();
   namespace cg = cooperative_groups;
   using G = SwzGeom<N, R>;
   constexpr int NP = N / C;
@@ -456,21 +458,7 @@ inline cudaError_t tma_launch_epi(const SliceCall& c, cudaStream_t st) {
   }
   const int clusters = a.units;
   if (c.grid_out) *c.grid_out = clusters * C;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(clusters * C);
-  cfg.blockDim = dim3(TMA_NT);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  if (C > 1) {
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-  }
-  return cudaLaunchKernelEx(&cfg, kern, a);
+  return launch_k(kern, dim3(clusters * C), dim3(TMA_NT), smem, st, C, a);
 }
 
 template <int N, typename R, int C, int FAM>
@@ -562,6 +550,7 @@ __device__ __forceinline__ void swz_ypass(R* xs, const LineCoef<N, R>& cf) {
 template <int N, typename R, int DIR>
 __global__ void __launch_bounds__(TMA_NT, (m1w_min_blocks<N, R>()))
 slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
+  pdl_begin();
   using G = SwzGeom<N, R>;
   constexpr int NN = N * N;
   constexpr int VOL = N * NN;
@@ -691,8 +680,7 @@ inline cudaError_t m1w_launch(const SliceCall& c, cudaStream_t st) {
   }
   const int units = c.tiles != nullptr ? c.ntiles : c.ntau;
   if (c.grid_out) *c.grid_out = units;
-  kern<<<units, TMA_NT, smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_k(kern, dim3(units), dim3(TMA_NT), smem, st, 1, a);
 }
 
 template <int N>
