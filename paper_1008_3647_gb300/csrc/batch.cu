@@ -9,6 +9,7 @@
 // iteration body is captured once in a CUDA graph and replayed between host checks.  Tiles are
 // ordered largest problem first so that the tail of every launch is made of small problems.
 #include <algorithm>
+#include <functional>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -313,9 +314,13 @@ struct BRes {
 
 // BiCGStab on A x = rhs for every problem whose scalars say running (tol set per problem by the
 // caller in scs_h before the call); prec selects the arena.
+// hook (optional): called at every host check with the scalars just read; it may act on the
+// problems (e.g. replace residuals) and sets *changed when the scalars must be read again.
+using CheckHook = std::function<ufg_status(bool* changed)>;
+
 ufg_status bicg_b(Batch& B, int prec, int op, const std::vector<double>& tol,
                   const std::vector<char>& active, int maxit, int check_every, BRes* res,
-                  double div_limit = 0.0) {
+                  double div_limit = 0.0, const CheckHook* hook = nullptr) {
   Arena& V = B.ar[prec];
   const bool pc = B.pc_kind == UFG_PC_WCE;
   const bool tr = op == BOP_MDAG;
@@ -395,6 +400,11 @@ ufg_status bicg_b(Batch& B, int prec, int op, const std::vector<double>& tol,
       UFG_TRY(init(2, true));
       continue;
     }
+    if (hook != nullptr) {
+      bool changed = false;
+      UFG_TRY((*hook)(&changed));
+      if (changed) continue;
+    }
     if (!any_run) break;
     if (!graphs_enabled()) {
       for (int i = 0; i < check_every; ++i) UFG_TRY(body());
@@ -463,6 +473,7 @@ __global__ void mixed_batch_kernel(const int4* tiles, const double* scale, doubl
   pdl_begin();
   const int4 tl = tiles[blockIdx.x];
   const double sc = scale[tl.x];
+  if (sc == 0.0) return;  // problem not selected
   for (long long i = (long long)tl.y + threadIdx.x; i < (long long)tl.y + tl.z; i += blockDim.x) {
     if (mode == 0) y32[i] = (float)(sc * x64[i]);
     else x64[i] += sc * (double)y32[i];
@@ -525,69 +536,126 @@ ufg_status solve_b(Batch& B, int op, const double* rhs, double* x, const std::ve
     return axpy_b(B, x, (const double*)V.x, sel, 1);
   };
   if (p->precision != UFG_MIXED) return fp64(want);
-  std::vector<char> fallback(B.n, 0);
+  // Mixed precision with reliable updates: one FP32 BiCGStab per problem on rhs / ||rhs||, whose
+  // FP32 solution x32 is an increment to the FP64 solution x.  When a problem's recursive
+  // residual has fallen by RU_DELTA since its last update (or has met the target), the
+  // increment is folded into x (x += ||rhs|| x32, x32 = 0), the true residual b - A x is
+  // recomputed in FP64, and the solve either stops (true residual within tol) or continues
+  // from that residual without a restart: r and the restart right-hand side are replaced, the
+  // search directions kept, rho and beta recomputed.
+  constexpr double RU_DELTA = 1e-2;
+  constexpr int RU_BUSY = 7;  // solver flag of the problems inside an update
+  // FP32 too coarse for the problem: the true residual stops following the recursive one.  After
+  // RU_STALLS consecutive updates that do not halve it, or RU_MAX updates, the problem is
+  // finished in FP64.
+  constexpr int RU_STALLS = 3, RU_MAX = 60;
+  std::vector<char> fallback(B.n, 0), verified(B.n, 0);
+  std::vector<int> stalls(B.n, 0);
+  std::vector<double> rlast(B.n, 0.0);
   std::vector<double> bn;
   UFG_TRY(norms_b(B, rhs, bn));
   UFG_CUDA(cudaMemsetAsync(x, 0, bytes, B.st));
-  UFG_CUDA(cudaMemcpyAsync(B.r64, rhs, bytes, cudaMemcpyDeviceToDevice, B.st));
-  std::vector<double> rn = bn;
-  const double inner = p->inner_tol > 0 ? p->inner_tol : 1e-5;
-  for (int i = 0; i < B.n; ++i)
-    if (want[i]) done[i] = 5;
-  for (int round = 0; round < 60; ++round) {
-    if (round > 0) {
-      // r64 = rhs - A x64 for every problem (FP64)
-      for (int i = 0; i < B.n; ++i) {
-        B.scs_h[i].done = 0;
-      }
-      UFG_TRY(write_scs(B));
-      UFG_TRY(apply_b(B, 0, op, x, B.r64, -1.0, rhs, 1.0, nullptr, false, nullptr, -1));
-      UFG_TRY(norms_b(B, B.r64, rn));
+  Arena& V = B.ar[1];
+  std::vector<double> inv(B.n, 0.0), rmax(B.n, 1.0), tin(B.n, 1.0);
+  bool any = false;
+  for (int i = 0; i < B.n; ++i) {
+    active[i] = 0;
+    if (!want[i]) continue;
+    if (!std::isfinite(bn[i])) {
+      done[i] = 4;
+      continue;
     }
-    bool any = false;
-    std::vector<double> inv(B.n, 0.0), tin(B.n, 1.0);
-    for (int i = 0; i < B.n; ++i) {
-      active[i] = 0;
-      if (!want[i]) continue;
-      if (!std::isfinite(rn[i])) {
-        done[i] = 4;
-        continue;
-      }
-      if (rn[i] <= tol[i] * bn[i] || bn[i] == 0.0) {
-        done[i] = 1;
-        continue;
-      }
-      if (iters[i] >= p->maxit) {
-        done[i] = 5;
-        continue;
-      }
-      active[i] = 1;
-      any = true;
-      inv[i] = 1.0 / rn[i];
-      tin[i] = std::fmax(inner, 0.5 * tol[i] * bn[i] / rn[i]);
-      outer[i] += 1;
+    if (bn[i] == 0.0) {
+      done[i] = 1;
+      continue;
     }
-    if (!any) break;
-    UFG_TRY(mixed_glue(B, 0, B.r64, (float*)B.ar[1].rhs, inv));
-    BRes r;
-    UFG_TRY(bicg_b(B, 1, op, tin, active, std::min(p->maxit, 1000), ce, &r, 1e8));
-    std::vector<double> sc(B.n, 0.0);
-    for (int i = 0; i < B.n; ++i) {
-      if (!active[i]) continue;
-      iters[i] += r.iters[i];
-      restarts[i] += r.restarts[i];
-      if (r.done[i] == 1) {
-        sc[i] = rn[i];
-      } else {  // failed inner solve: not applied; the problem is finished in FP64
-        fallback[i] = 1;
-        rn[i] = 0.0;
-      }
-    }
-    UFG_TRY(mixed_glue(B, 1, x, (float*)B.ar[1].x, sc));
-    // problems in fallback leave the mixed loop (their residual check is skipped below)
-    for (int i = 0; i < B.n; ++i)
-      if (fallback[i]) bn[i] = 0.0;
+    active[i] = 1;
+    any = true;
+    inv[i] = 1.0 / bn[i];
+    tin[i] = tol[i];
+    outer[i] = 1;
+    rlast[i] = bn[i];
   }
+  if (!any) return UFG_OK;
+  UFG_TRY(mixed_glue(B, 0, const_cast<double*>(rhs), (float*)V.rhs, inv));  // mode 0 reads only
+  std::vector<double> rn;
+  CheckHook hook = [&](bool* changed) -> ufg_status {
+    *changed = false;
+    std::vector<double> sc(B.n, 0.0);
+    bool upd = false;
+    for (int i = 0; i < B.n; ++i) {
+      if (!active[i] || verified[i]) continue;
+      const DevScalars& h = B.scs_h[i];
+      if (h.done != 0 && h.done != 1) continue;
+      const double rr = std::sqrt(std::fmax(h.rr, 0.0));
+      rmax[i] = std::fmax(rmax[i], rr);
+      if (h.done == 1 || rr < RU_DELTA * rmax[i]) {
+        sc[i] = bn[i];
+        upd = true;
+      }
+    }
+    if (!upd) return UFG_OK;
+    *changed = true;
+    // fold the increments into x and clear them
+    UFG_TRY(mixed_glue(B, 1, x, (float*)V.x, sc));
+    for (int i = 0; i < B.n; ++i)
+      if (sc[i] != 0.0) B.scs_h[i].done = RU_BUSY;
+    UFG_TRY(write_scs(B));
+    UFG_TRY(vecb(B, 1, V_ZERO, RU_BUSY, V.x, nullptr, nullptr, nullptr, nullptr, nullptr,
+                 nullptr));
+    // true residual in FP64
+    UFG_TRY(apply_b(B, 0, op, x, B.r64, -1.0, rhs, 1.0, nullptr, false, nullptr, RU_BUSY));
+    UFG_TRY(norms_b(B, B.r64, rn));  // reads the scalars back
+    std::vector<double> inv2(B.n, 0.0);
+    bool cont = false;
+    for (int i = 0; i < B.n; ++i) {
+      if (sc[i] == 0.0) continue;
+      if (!std::isfinite(rn[i])) {
+        B.scs_h[i].done = 4;
+      } else if (rn[i] <= tol[i] * bn[i]) {
+        B.scs_h[i].done = 1;
+        verified[i] = 1;
+      } else {
+        stalls[i] = rn[i] > 0.5 * rlast[i] ? stalls[i] + 1 : 0;
+        rlast[i] = rn[i];
+        if (stalls[i] >= RU_STALLS || outer[i] >= RU_MAX) {
+          B.scs_h[i].done = 6;  // handed to the FP64 solver after this one
+          continue;
+        }
+        inv2[i] = 1.0 / bn[i];
+        rmax[i] = rn[i] / bn[i];
+        outer[i] += 1;
+        cont = true;
+      }
+    }
+    UFG_TRY(write_scs(B));
+    if (!cont) return UFG_OK;
+    // continue from the true residual: rhs32 = r = (b - A x) / ||b||, then rho and beta again
+    UFG_TRY(mixed_glue(B, 0, B.r64, (float*)V.rhs, inv2));
+    UFG_TRY(vecb(B, 1, V_COPY, RU_BUSY, V.r, V.rhs, nullptr, nullptr, nullptr, nullptr,
+                 nullptr));
+    UFG_TRY(vecb(B, 1, V_DOT, RU_BUSY, V.rhat, V.r, V.r, V.r, nullptr, nullptr,
+                 B.slot(B_VEC2)));
+    UFG_TRY(scalb(B, OP_BI_RHO_REDO, B.slot(B_VEC2), 1, nullptr, 1, RU_BUSY));
+    return UFG_OK;
+  };
+  BRes r;
+  UFG_TRY(bicg_b(B, 1, op, tin, active, p->maxit, ce, &r, 1e8, &hook));
+  std::vector<double> sc(B.n, 0.0);
+  for (int i = 0; i < B.n; ++i) {
+    if (!active[i]) continue;
+    iters[i] += r.iters[i];
+    restarts[i] += r.restarts[i];
+    if (verified[i]) {
+      done[i] = 1;
+    } else if (r.done[i] == 5) {  // iteration cap: keep the progress, report not converged
+      sc[i] = bn[i];
+      done[i] = 5;
+    } else {  // diverged, non-finite or persistent breakdown: finished in FP64
+      fallback[i] = 1;
+    }
+  }
+  UFG_TRY(mixed_glue(B, 1, x, (float*)V.x, sc));
   bool any_fb = false;
   for (int i = 0; i < B.n; ++i) any_fb = any_fb || fallback[i];
   if (any_fb) UFG_TRY(fp64(fallback));

@@ -43,6 +43,8 @@ enum ScalarOp {
   OP_NORM2,         // rr = v.v only (no other state touched)
   OP_BI_RCHECK_RHO, // OP_BI_RCHECK, then OP_BI_RHO on the same partials if still running
   OP_BI_INIT_RHO,   // OP_BI_INIT, then OP_BI_RHO on the same partials if still running
+  OP_BI_RHO_REDO,   // after a residual replacement: rho = rhat.r, beta again (no iteration
+                    // counted); done = 0, or 2 on near-breakdown
 };
 
 // Partial pairs per producing CTA: up to this many CTAs per producer.

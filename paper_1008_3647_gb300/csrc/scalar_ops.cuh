@@ -124,6 +124,16 @@ static __device__ __noinline__ void scalar_update(int op, DevScalars* sc, const 
       else if (sqrt(a1) <= tb) sc->done = 1;
       else bi_rho(sc, a0, a1);
       break;
+    case OP_BI_RHO_REDO:  // part = (rhat.r, r.r) of the replaced residual
+      sc->rr = a1;
+      if (fabs(a0) <= sc->restart_cos * sqrt(sc->rhatn2 * a1)) {
+        sc->done = 2;
+        break;
+      }
+      sc->rho = a0;
+      sc->beta = (a0 / sc->rho_old) * (sc->alpha / sc->omega);
+      sc->done = bad(sc->beta) ? 4 : 0;
+      break;
     case OP_BI_RHO:  // part = (rhat.r, r.r) of the last residual update (or of the init)
       bi_rho(sc, a0, a1);
       break;
