@@ -45,7 +45,10 @@ ORACLE_COUNTS = os.path.join(ROOT, "tests", "golden", "oracle_counts_16x256.json
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of kernel classes from
 # one ncu capture of the timed step's launches; a class is listed only while its kernel is
 # unchanged since the capture (the command is in the profile summary under profiles/).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/slice_m1w_kernel_fp32_16x256x8.md: 67.17 MB read + 4.36 MB written
+    "slice m1w N16 f32": 71.53e6,
+}
 
 
 def peaks():
