@@ -51,6 +51,10 @@ cudaError_t launch_potentials(const double* sigma, double A, long long S, double
 // is held in registers across the passes, so eight 256-thread blocks fit on an SM and a batch of
 // 8 x 16^3 x 256 sites (1024 blocks) runs as a single wave; N_tau is unbounded.
 constexpr int REC_NCH = 8;
+// Loads each thread keeps in flight (unroll depth of the streaming loops): with 4 the kernel was
+// latency-bound (long-scoreboard stalls, ~1/3 of HBM); 16 measured best of 4/8/16.
+constexpr int REC_UNROLL = 16;
+constexpr int REC_MINB = 7;  // 7 x 152 CTA slots still hold a batch of 1024 CTAs in one wave
 
 template <typename R>
 struct RecArgs {
@@ -70,7 +74,7 @@ struct RecArgs {
 };
 
 template <typename R, int ACC, bool OUT>  // ACC = acc_mode; OUT: write out
-__global__ void __launch_bounds__(32 * REC_NCH, sizeof(R) == 4 ? 8 : 5) recurrence_kernel(const RecArgs<R> a) {
+__global__ void __launch_bounds__(32 * REC_NCH, sizeof(R) == 4 ? REC_MINB : 5) recurrence_kernel(const RecArgs<R> a) {
   pdl_begin();
   __shared__ R Es[REC_NCH][32];
   __shared__ R Ps[REC_NCH][32];
@@ -106,7 +110,7 @@ __global__ void __launch_bounds__(32 * REC_NCH, sizeof(R) == 4 ? 8 : 5) recurren
   R e = R(0), p = R(1);
   {
     const R* q = in;
-#pragma unroll 4
+#pragma unroll(REC_UNROLL)
     for (int l = 0; l < n; ++l, q += step) {
       e = *q + b * e;
       p = p * b;
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(32 * REC_NCH, sizeof(R) == 4 ? 8 : 5) recurren
   R* acc = ACC ? a.acc + off + first : nullptr;
   const R oscale = R(a.out_scale), acoef = R(a.acc_coef);
   const R* q = in;
-#pragma unroll 4
+#pragma unroll(REC_UNROLL)
   for (int l = 0; l < n; ++l, q += step) {
     x = *q + b * x;
     if constexpr (ACC == 1) *acc = acoef * x;
