@@ -24,6 +24,7 @@
 #include "scalar_ops.cuh"
 #include "slice_kernel.cuh"
 #include "launch.cuh"
+#include "mbarrier.cuh"
 
 namespace ufg {
 
@@ -80,33 +81,6 @@ struct SwzGeom {
     return (int)(r * N + (c ^ f(r)) * EPC);
   }
 };
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 
 __device__ __forceinline__ void tma_load_rows(void* dst, const CUtensorMap* tm, int row,
                                               uint64_t* bar) {
@@ -492,16 +466,17 @@ inline cudaError_t tma_launch_fam(const SliceCall& c, cudaStream_t st) {
 // per-site multiplier sin(sigma), b the per-mode kinetic factor and the time shift S:
 //   DIR 0 (the M1 term of Sec. 3):  y_t = -A sgn(t) b .* F^T( s_{t-1} .* F x_{t-1} )
 //   DIR 1 (its transpose): y_t = F^T( -A sgn(t) s_t .* F( b .* x_{t+1} ) )
-// x and s arrive as TMA boxes; b (one 16 KB slice shared by every CTA) is read through L1.
+// x, s and (DIR 1) b arrive as TMA boxes (b through L1 instead measured 10 % slower).
 // with sgn(t) = -1 except at the antiperiodic wrap.  The inverse transform's result never leaves
 // shared memory: the z pass multiplies it by s in place and the forward passes follow.
 template <int N, typename R>
 struct M1wArgs {
   CUtensorMap tm_in;  // momentum-space input arena
   CUtensorMap tm_s;   // site multiplier arena
+  CUtensorMap tm_k;   // per-mode factor (one slice), DIR 1
   LineCoef<N, R> ci_x, ci_y, ci_z;  // inverse transform, one copy per pass (see TmaArgs)
   LineCoef<N, R> cf_x, cf_y, cf_z;  // forward transform
-  const R* bk;  // per-mode factor (one slice): DIR 0 scales the output, DIR 1 the input
+  const R* bk;                      // per-mode factor, DIR 0 (applied to the output)
   R* out;
   double a;
   const int* done;
@@ -515,15 +490,12 @@ struct M1wArgs {
 
 template <int N, typename R>
 constexpr int m1w_min_blocks() {
-  return sizeof(R) == 4 ? 5 : (N <= 8 ? 4 : 2);
+  return sizeof(R) == 4 ? 5 : (N <= 8 ? 4 : 2);  // DIR 1 (three boxes) fits 4 by shared memory
 }
 
 // Line passes over one swizzled slice box (all N planes in this CTA).
-// MUL: 0 none, 1 a per-mode table in global memory ([z][y][x], one slice; read through L1,
-// 16 bytes at a time).
-template <int N, typename R, bool IN_SPEC, bool OUT_SPEC, int MUL>
-__device__ __forceinline__ void swz_xpass(R* xs, const R* __restrict__ mul,
-                                          const LineCoef<N, R>& cf) {
+template <int N, typename R, bool IN_SPEC, bool OUT_SPEC, bool MUL>
+__device__ __forceinline__ void swz_xpass(R* xs, const R* mul, const LineCoef<N, R>& cf) {
   using G = SwzGeom<N, R>;
   constexpr int CPR = G::RB / 16, EPC = 16 / (int)sizeof(R);
   for (int r = threadIdx.x; r < N * N; r += TMA_NT) {
@@ -532,13 +504,7 @@ __device__ __forceinline__ void swz_xpass(R* xs, const R* __restrict__ mul,
     for (int c = 0; c < CPR; ++c) {
       const int o = G::chunk(r, c);
 #pragma unroll
-      for (int e = 0; e < EPC; ++e) v[c * EPC + e] = xs[o + e];
-      if constexpr (MUL == 1) {
-        R m[EPC];
-        ld16(mul + r * N + c * EPC, m);
-#pragma unroll
-        for (int e = 0; e < EPC; ++e) v[c * EPC + e] *= m[e];
-      }
+      for (int e = 0; e < EPC; ++e) v[c * EPC + e] = MUL ? xs[o + e] * mul[o + e] : xs[o + e];
     }
     line_op<N, R, IN_SPEC, OUT_SPEC>(v, cf, [&](int i, R val) { xs[G::off(r, i)] = val; });
   }
@@ -590,12 +556,14 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
   unsigned char* const base = tma_smem + ((1024u - (smem_addr(tma_smem) & 1023u)) & 1023u);
   R* const xs = reinterpret_cast<R*>(base);
   R* const ss = xs + VOL;
+  R* const ks = ss + VOL;
   if (tid == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    mbar_expect_tx(&bar, (uint32_t)(VOL * sizeof(R)) * 2u);
+    mbar_expect_tx(&bar, (uint32_t)(VOL * sizeof(R)) * (DIR == 1 ? 3u : 2u));
     tma_load_rows(xs, &A.tm_in, (int)((off + (size_t)t_in * VOL) / N), &bar);
     tma_load_rows(ss, &A.tm_s, (int)((off + (size_t)t_s * VOL) / N), &bar);
+    if (DIR == 1) tma_load_rows(ks, &A.tm_k, 0, &bar);
   }
   __syncthreads();
   {
@@ -608,7 +576,7 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
     }
   }
   // inverse transform (spectral input); DIR 1 weights the modes by b on the way in
-  swz_xpass<N, R, true, false, DIR == 1 ? 1 : 0>(xs, A.bk, A.ci_x);
+  swz_xpass<N, R, true, false, DIR == 1>(xs, ks, A.ci_x);
   __syncthreads();
   swz_ypass<N, R, true, false>(xs, A.ci_y);
   __syncthreads();
@@ -625,7 +593,7 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
   }
   __syncthreads();
   // forward transform (spectral output)
-  swz_xpass<N, R, false, true, 0>(xs, nullptr, A.cf_x);
+  swz_xpass<N, R, false, true, false>(xs, nullptr, A.cf_x);
   __syncthreads();
   swz_ypass<N, R, false, true>(xs, A.cf_y);
   __syncthreads();
@@ -654,7 +622,8 @@ inline cudaError_t m1w_launch(const SliceCall& c, cudaStream_t st) {
       c.coef2 == nullptr || (DIR == 1 ? c.bkpre : c.bkpost) == nullptr)
     return cudaErrorInvalidValue;
   if (encode_rows<R>(&a.tm_in, c.in, nelem, N, N * N) != cudaSuccess ||
-      encode_rows<R>(&a.tm_s, c.pre, nelem, N, N * N) != cudaSuccess)
+      encode_rows<R>(&a.tm_s, c.pre, nelem, N, N * N) != cudaSuccess ||
+      (DIR == 1 && encode_rows<R>(&a.tm_k, c.bkpre, VOL, N, N * N) != cudaSuccess))
     return cudaErrorNotSupported;
   a.ci_x = *reinterpret_cast<const LineCoef<N, R>*>(c.coef);
   a.ci_y = a.ci_x;
@@ -662,7 +631,7 @@ inline cudaError_t m1w_launch(const SliceCall& c, cudaStream_t st) {
   a.cf_x = *reinterpret_cast<const LineCoef<N, R>*>(c.coef2);
   a.cf_y = a.cf_x;
   a.cf_z = a.cf_x;
-  a.bk = static_cast<const R*>(DIR == 1 ? c.bkpre : c.bkpost);
+  a.bk = static_cast<const R*>(c.bkpost);
   a.out = static_cast<R*>(c.out);
   a.a = c.a;
   a.done = c.done;
@@ -672,12 +641,12 @@ inline cudaError_t m1w_launch(const SliceCall& c, cudaStream_t st) {
   a.scale_by_A = c.scale_by_A;
   a.ntau = c.ntau;
   a.err = c.err;
-  const size_t smem = (size_t)2 * VOL * sizeof(R) + 1024;
+  const size_t smem = (size_t)(DIR == 1 ? 3 : 2) * VOL * sizeof(R) + 1024;
   auto kern = slice_m1w_kernel<N, R, DIR>;
   static int configured = 0;
   if (!configured) {
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(2 * VOL * sizeof(R) + 1024));
+                                           (int)(3 * VOL * sizeof(R) + 1024));
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                cudaSharedmemCarveoutMaxShared);
