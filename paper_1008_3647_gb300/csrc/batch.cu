@@ -136,8 +136,8 @@ ufg_status slice(Batch& B, Group& g, SliceCall c, int exec_if) {
   c.exec_if = exec_if;
   c.nelem = B.S;
   if (c.partials) c.partials += 2 * (size_t)g.cta_base;
+  c.scs = B.scs;  // the fused scalar step and the fused direction update read them
   if (c.fop >= 0) {
-    c.scs = B.scs;
     c.counters = B.counters;
     c.part_base = g.cta_base;
   }
@@ -219,8 +219,11 @@ std::vector<double> weights(int d, bool euler) {
   return c;
 }
 
-// z = P_d r (tr: P_d^T) for every running problem, momentum-space evaluation (see solvers.cu)
-ufg_status wce_b(Batch& B, int prec, const void* r, void* z, bool tr) {
+// z = P_d r (tr: P_d^T) for every running problem, momentum-space evaluation (see solvers.cu).
+// prep_r != nullptr: r is BiCGStab's direction p, first updated in place to
+// p = prep_r + beta (p - omega prep_v) by the forward transform (slice_tma_prep_supported).
+ufg_status wce_b(Batch& B, int prec, const void* r, void* z, bool tr,
+                 const void* prep_r = nullptr, const void* prep_v = nullptr) {
   const int d = B.pc.order;
   const std::vector<double> cw = weights(d, B.pc.euler != 0);
   Arena& V = B.ar[prec];
@@ -243,6 +246,11 @@ ufg_status wce_b(Batch& B, int prec, const void* r, void* z, bool tr) {
     SliceCall fw = base_call(g.lat, FAM_FWD, prec);
     fw.in = r;
     fw.out = V.spec;
+    if (prep_r != nullptr) {
+      fw.prep_r = prep_r;
+      fw.prep_v = prep_v;
+      fw.prep_out = const_cast<void*>(r);
+    }
     UFG_TRY(slice(B, g, fw, 0));
     UFG_TRY(rec(V.spec, cw[0], 1, d > 0));
     const bool fused = slice_m1w_supported(g.lat->nx, prec);
@@ -324,6 +332,11 @@ ufg_status bicg_b(Batch& B, int prec, int op, const std::vector<double>& tol,
   Arena& V = B.ar[prec];
   const bool pc = B.pc_kind == UFG_PC_WCE;
   const bool tr = op == BOP_MDAG;
+  // the direction update rides on the preconditioner's first forward transform where every
+  // group runs it on the TMA kernel
+  bool fuse_p = pc;
+  for (auto& g : B.groups)
+    fuse_p = fuse_p && slice_tma_prep_supported(g.lat->nx, prec, g.lat->use_tma[prec]);
   for (int p = 0; p < B.n; ++p) {
     DevScalars& h = B.scs_h[p];
     std::memset(&h, 0, sizeof(DevScalars));
@@ -355,10 +368,11 @@ ufg_status bicg_b(Batch& B, int prec, int op, const std::vector<double>& tol,
   UFG_TRY(init(0, false));
   // Each scalar step is applied by the last CTA of the kernel that produces its partials.
   auto body = [&]() -> ufg_status {
-    UFG_TRY(vecb(B, prec, V_BI_P, 0, V.p, V.r, V.v, nullptr, nullptr, nullptr, nullptr));
+    if (!fuse_p)
+      UFG_TRY(vecb(B, prec, V_BI_P, 0, V.p, V.r, V.v, nullptr, nullptr, nullptr, nullptr));
     const void* y = V.p;
     if (pc) {
-      UFG_TRY(wce_b(B, prec, V.p, V.y, tr));
+      UFG_TRY(wce_b(B, prec, V.p, V.y, tr, fuse_p ? V.r : nullptr, V.v));
       y = V.y;
     }
     UFG_TRY(apply_b(B, prec, op, y, V.v, 1.0, nullptr, 0.0, V.rhat, false, B.slot(B_SLICE1), 0,

@@ -14,6 +14,19 @@ bool slice_m1w_supported(int N, int prec) {
   return prec == 1 ? N == 16 : (N == 8 || N == 16);
 }
 
+bool slice_tma_prep_supported(int N, int prec, int allow_tma) {
+  switch (N) {
+    case 4: return slice_tma_prep_ok<4>(prec, allow_tma);
+    case 6: return slice_tma_prep_ok<6>(prec, allow_tma);
+    case 8: return slice_tma_prep_ok<8>(prec, allow_tma);
+    case 10: return slice_tma_prep_ok<10>(prec, allow_tma);
+    case 12: return slice_tma_prep_ok<12>(prec, allow_tma);
+    case 16: return slice_tma_prep_ok<16>(prec, allow_tma);
+    case 32: return slice_tma_prep_ok<32>(prec, allow_tma);
+  }
+  return false;
+}
+
 cudaError_t slice_dispatch(int N, const SliceCall& c, cudaStream_t st) {
   switch (N) {
     case 4: return slice_launch<4>(c, st);

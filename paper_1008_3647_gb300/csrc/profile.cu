@@ -194,6 +194,7 @@ std::string slice_kernel_name(const SliceCall& c, int N) {
     if (c.post2) s += "+post2";
     if (c.U || c.V) s += "+uv";
     if (c.want_dotP || c.want_self) s += "+dot";
+    if (c.prep_out) s += "+prep";
   } else {
     s += c.shift > 0 ? "T" : "";
   }
@@ -211,6 +212,7 @@ double slice_bytes_per_site(const SliceCall& c) {
   if (c.U) ++site_arrays;
   if (c.V) ++site_arrays;
   if (c.want_dotP && c.dotP) ++site_arrays;
+  if (c.prep_out) site_arrays += 3;  // r and v read, p written
   return es * site_arrays;
 }
 

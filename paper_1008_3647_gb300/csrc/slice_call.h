@@ -70,11 +70,22 @@ struct SliceCall {
   DevScalars* scs = nullptr;   // per-problem solver scalars
   unsigned* counters = nullptr;  // per-problem CTA counters (zero between launches)
   int part_base = 0;           // CTA index of this launch's first CTA in the problems' ranges
+  // batched forward transform fused with the BiCGStab direction update (TMA kernel only):
+  // in = p, p' = prep_r + beta (p - omega prep_v) written to prep_out, scalars from scs
+  const void* prep_r = nullptr;
+  const void* prep_v = nullptr;
+  void* prep_out = nullptr;
 };
 
 // Launches the slice kernel for lattice extent N (explicitly instantiated per N).
 template <int N>
 cudaError_t slice_launch(const SliceCall& c, cudaStream_t st);
+
+// Whether the TMA forward transform with the fused direction update (SliceCall::prep_out) runs
+// for N, precision and the lattice's TMA setting (per N, and by runtime dispatch).
+template <int N>
+bool slice_tma_prep_ok(int prec, int allow_tma);
+bool slice_tma_prep_supported(int N, int prec, int allow_tma);
 
 // Runtime dispatch over the supported N (4, 6, 8, 10, 12, 16, 32).
 cudaError_t slice_dispatch(int N, const SliceCall& c, cudaStream_t st);

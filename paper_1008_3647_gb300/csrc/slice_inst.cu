@@ -28,7 +28,14 @@ cudaError_t slice_launch<UFG_N>(const SliceCall& c, cudaStream_t st) {
     const cudaError_t e = slice_tma_try<UFG_N>(c, st);
     if (e != cudaErrorNotSupported) return e;
   }
+  if (c.prep_out != nullptr) return cudaErrorInvalidValue;  // the fused update is TMA-only
   return slice_launch_plain<UFG_N>(c, st);
+}
+
+template <>
+bool slice_tma_prep_ok<UFG_N>(int prec, int allow_tma) {
+  if (!allow_tma || !tma_enabled()) return false;
+  return prec == 1 ? (UFG_N == 16 || UFG_N == 32) : (UFG_N == 8 || UFG_N == 16);
 }
 
 }  // namespace ufg

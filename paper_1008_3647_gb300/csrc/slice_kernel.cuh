@@ -78,12 +78,24 @@ __device__ __forceinline__ void ld16(const R* p, R (&o)[Vec16<R>::W]) {
   else { o[0] = v.x; o[1] = v.y; }
 }
 
+template <typename R>
+__device__ __forceinline__ void st16(R* p, const R (&v)[Vec16<R>::W]) {
+  typename Vec16<R>::T w;
+  if constexpr (Vec16<R>::W == 4) { w.x = v[0]; w.y = v[1]; w.z = v[2]; w.w = v[3]; }
+  else { w.x = v[0]; w.y = v[1]; }
+  *reinterpret_cast<typename Vec16<R>::T*>(p) = w;
+}
+
 constexpr int SLICE_NT = 256;
 static_assert(SLICE_NT == SCAL_NT, "fused scalar updates reduce over SCAL_NT threads");
 
 // Epilogue operand mask: the specialised variants know at compile time which operands exist;
 // EPI_ANY tests every optional pointer at run time.
 enum EpiBits { E_ID = 1, E_POST = 2, E_POST2 = 4, E_UV = 8, E_DOT = 16, E_BK = 32, EPI_ANY = 63 };
+// Load-side fusion of the TMA kernel (forward transform of batched BiCGStab): the input is p and
+// the kernel first forms p' = r + beta (p - omega v) (per-problem scalars), writes p' back and
+// transforms it.
+constexpr int E_PREP = 64;
 
 // Resident CTAs per SM the register allocation must allow (256 threads each).
 template <int N, typename R>

@@ -32,6 +32,8 @@ template <int N, typename R>
 struct TmaArgs {
   CUtensorMap tm_in;   // [rows][N] view of the input arena, box N x (N/C * N)
   CUtensorMap tm_pre;  // same view of the per-site multiplier (when has_pre)
+  CUtensorMap tm_r;    // E_PREP: r and v (boxes 1 and 2)
+  CUtensorMap tm_v;
   // The line operator once per pass: with a single copy the compiler keeps all of its
   // coefficients in registers from the first pass to the last (118 instead of 56 registers for
   // N = 16); separate copies stay constant-bank operands of the multiply-adds.
@@ -56,6 +58,7 @@ struct TmaArgs {
   int scale_by_A;
   int ntau, shift, units, has_pre;
   int pre_mode;  // the multiplier box is a per-mode table (one slice, the same for every t)
+  R* prep_out;   // E_PREP: p' (written at the input slice)
   int fop;       // batched: scalar op of the problem's last CTA (-1: none), see SliceCall
   DevScalars* scs;
   unsigned* counters;
@@ -157,8 +160,13 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     const int row = (int)((off + (size_t)t_in * VOL + (size_t)rank * NP * NN) / N);
-    mbar_expect_tx(&bar, (uint32_t)(BUF * sizeof(R)) * (A.has_pre ? 2u : 1u));
+    mbar_expect_tx(&bar, (uint32_t)(BUF * sizeof(R)) *
+                             ((A.has_pre ? 2u : 1u) + ((EPI & E_PREP) ? 2u : 0u)));
     tma_load_rows(xs, &A.tm_in, row, &bar);
+    if constexpr ((EPI & E_PREP) != 0) {
+      tma_load_rows(xs + BUF, &A.tm_r, row, &bar);
+      tma_load_rows(xs + 2 * BUF, &A.tm_v, row, &bar);
+    }
     if (A.has_pre)
       tma_load_rows(const_cast<R*>(ws), &A.tm_pre, A.pre_mode ? rank * NP * N : row, &bar);
   }
@@ -173,6 +181,14 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
     }
   }
 
+  R pbeta = R(0), pomega = R(0);
+  R* pdst = nullptr;
+  if constexpr ((EPI & E_PREP) != 0) {
+    const DevScalars& sc = A.scs[A.tiles[unit].prob];
+    pbeta = R(sc.beta);
+    pomega = R(sc.omega);
+    pdst = A.prep_out + off + (size_t)t_in * VOL + (size_t)rank * NP * NN;
+  }
   // ---- x-pass: one row per thread, read as 16-byte chunks ----
   for (int r = tid; r < ROWS; r += TMA_NT) {
     R v[N];
@@ -181,7 +197,15 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
       const int o = G::chunk(r, c);
 #pragma unroll
       for (int e = 0; e < EPC; ++e) v[c * EPC + e] = xs[o + e];
-      if (A.has_pre) {
+      if constexpr ((EPI & E_PREP) != 0) {  // p' = r + beta (p - omega v), written back
+        R pn[EPC];
+#pragma unroll
+        for (int e = 0; e < EPC; ++e) {
+          pn[e] = xs[BUF + o + e] + pbeta * (v[c * EPC + e] - pomega * xs[2 * BUF + o + e]);
+          v[c * EPC + e] = pn[e];
+        }
+        st16(pdst + r * N + c * EPC, pn);
+      } else if (A.has_pre) {
 #pragma unroll
         for (int e = 0; e < EPC; ++e) v[c * EPC + e] *= ws[o + e];
       }
@@ -413,17 +437,28 @@ inline cudaError_t tma_launch_epi(const SliceCall& c, cudaStream_t st) {
   a.shift = c.shift;
   a.units = c.tiles != nullptr ? c.ntiles : c.ntau;
   a.err = c.err;
+  if constexpr ((EPI & E_PREP) != 0) {
+    if (c.tiles == nullptr || c.scs == nullptr || c.prep_out == nullptr || a.has_pre)
+      return cudaErrorInvalidValue;
+    if (encode_rows<R>(&a.tm_r, c.prep_r, nelem, N, ROWS) != cudaSuccess ||
+        encode_rows<R>(&a.tm_v, c.prep_v, nelem, N, ROWS) != cudaSuccess)
+      return cudaErrorNotSupported;
+    a.prep_out = static_cast<R*>(c.prep_out);
+  }
   a.fop = c.fop;
   a.scs = c.scs;
   a.counters = c.counters;
   a.part_base = c.part_base;
-  // clusters need the second box as the z-column receive buffer
-  const size_t smem = (size_t)((a.has_pre || C > 1) ? 2 : 1) * BUF * sizeof(R) + 1024;
+  // clusters need the second box as the z-column receive buffer; E_PREP holds p, r and v
+  const size_t smem = (size_t)(((EPI & E_PREP) != 0) ? 3 : ((a.has_pre || C > 1) ? 2 : 1)) * BUF *
+                          sizeof(R) +
+                      1024;
   auto kern = slice_tma_kernel<N, R, C, FAM, EPI>;
   static int configured = 0;
   if (!configured) {
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(2 * BUF * sizeof(R) + 1024));
+    cudaError_t err = cudaFuncSetAttribute(
+        kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)((((EPI & E_PREP) != 0) ? 3 : 2) * BUF * sizeof(R) + 1024));
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                cudaSharedmemCarveoutMaxShared);
@@ -439,7 +474,13 @@ template <int N, typename R, int C, int FAM>
 inline cudaError_t tma_launch_fam(const SliceCall& c, cudaStream_t st) {
   const int mask = (c.id ? E_ID : 0) | (c.post ? E_POST : 0) | (c.post2 ? E_POST2 : 0) |
                    ((c.U || c.V) ? E_UV : 0) | ((c.want_dotP || c.want_self) ? E_DOT : 0) |
-                   (c.bkpost ? E_BK : 0);
+                   (c.bkpost ? E_BK : 0) | (c.prep_out ? E_PREP : 0);
+  if ((mask & E_PREP) != 0) {  // only the plain forward transform takes the direction update
+    if constexpr (FAM == FAM_FWD) {
+      if (mask == E_PREP) return tma_launch_epi<N, R, C, FAM, E_PREP>(c, st);
+    }
+    return cudaErrorInvalidValue;
+  }
   if constexpr (FAM == FAM_KIN) {
     switch (mask) {
       case E_ID: return tma_launch_epi<N, R, C, FAM, E_ID>(c, st);
