@@ -194,6 +194,20 @@ ufg_status ufg_apply_kinetic(ufg_field* f, const void* x, void* y, int precision
 ufg_status ufg_apply_M0inv(ufg_field* f, const void* x, void* y, int precision, void* stream);
 ufg_status ufg_apply_M0invT(ufg_field* f, const void* x, void* y, int precision, void* stream);
 
+/* The momentum basis of Sec. 3 (Fourier acceleration).  ufg_fourier: y = F x (inverse = 0) or
+ * y = F^T x (inverse = 1) on every slice, with F the orthogonal real Fourier basis in which
+ * exp(-tau K) is diagonal (F^T F = 1, so norms and inner products are those of position space).
+ * A momentum-space vector has the position-space shape [N_tau][N_x^3]; its modes are stored in
+ * the library's per-axis slot order (cos and sin slots of each 1-D momentum), not FFT order.
+ * ufg_apply_M_momentum: y^ = F M F^T x^ (transpose = 0) or F M^T F^T x^ (transpose = 1), one
+ * fused kernel per slice (inverse transform, site multiplier, forward transform, the M0 part of
+ * Sec. 3 and the identity).  Built for FP32 N_x = 16 and FP64 N_x = 8, 16; UFG_INVALID_ARG
+ * elsewhere.  Same precision, alignment and overlap rules as the applies above. */
+ufg_status ufg_fourier(ufg_field* f, const void* x, void* y, int precision, int inverse,
+                       void* stream);
+ufg_status ufg_apply_M_momentum(ufg_field* f, const void* x, void* y, int precision,
+                                int transpose, void* stream);
+
 /* Solver workspace for one lattice (all vectors the solvers and preconditioners need, FP64 and
  * FP32). */
 ufg_status ufg_solver_create(const ufg_lattice* lat, ufg_solver** out);

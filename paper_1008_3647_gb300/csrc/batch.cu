@@ -12,6 +12,7 @@
 #include <functional>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -73,6 +74,10 @@ struct Batch {
   float* c32 = nullptr;
   Arena ar[2];
   double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *y64 = nullptr;
+  // Momentum basis (Sec. 3): while `mom` is set, every arena vector holds F x per slice, the
+  // operator is the fused momentum-space M and the WCE preconditioner needs no transforms.
+  bool mom = false;
+  double *xm64 = nullptr, *bm64 = nullptr;  // the right-hand side and solution in that basis
   double *rc64 = nullptr, *cr64 = nullptr;  // correction round: residual copy and correction
   double* scale = nullptr;        // per-problem scale factors (mixed precision glue)
   double* scale_h = nullptr;      // pinned
@@ -155,6 +160,32 @@ ufg_status slice(Batch& B, Group& g, SliceCall c, int exec_if) {
 ufg_status apply_b(Batch& B, int prec, int op, const void* in, void* out, double a, const void* U,
                    double bU, const void* dotP, bool self, double* part, int exec_if,
                    int fop = -1) {
+  if (B.mom) {  // the fused momentum-space operator, one kernel per group
+    for (auto& g : B.groups) {
+      SliceCall c = base_call(g.lat, FAM_INV, prec);
+      c.fam = FAM_M1W;
+      c.coef2 = base_call(g.lat, FAM_FWD, prec).coef;
+      c.m1w_full = 1;
+      c.in = in;
+      c.pre = fldb(B, 'w', prec);
+      const void* bk = prec ? (const void*)g.lat->bk32 : (const void*)g.lat->bk64;
+      if (op == BOP_M) c.bkpost = bk;
+      else c.bkpre = bk;
+      c.shift = op == BOP_M ? -1 : +1;
+      c.a = 1.0;
+      c.full_scale = a;
+      c.out = out;
+      c.U = U;
+      c.bU = bU;
+      c.dotP = dotP;
+      c.want_dotP = dotP != nullptr;
+      c.want_self = self;
+      c.partials = part;
+      c.fop = fop;
+      UFG_TRY(slice(B, g, c, exec_if));
+    }
+    return UFG_OK;
+  }
   for (auto& g : B.groups) {
     SliceCall c = base_call(g.lat, FAM_KIN, prec);
     c.in = in;
@@ -227,6 +258,8 @@ ufg_status wce_b(Batch& B, int prec, const void* r, void* z, bool tr,
   const int d = B.pc.order;
   const std::vector<double> cw = weights(d, B.pc.euler != 0);
   Arena& V = B.ar[prec];
+  // in the momentum basis r is already spectral and the series accumulates straight into z
+  void* const acc = B.mom ? z : V.acc;
   for (auto& g : B.groups) {
     const void* bk = prec ? (const void*)g.lat->bk32 : (const void*)g.lat->bk64;
     auto rec = [&](const void* in, double coef, int mode, bool write_out) -> ufg_status {
@@ -238,22 +271,27 @@ ufg_status wce_b(Batch& B, int prec, const void* r, void* z, bool tr,
                            (prec ? 4.0 : 8.0) *
                                (1 + (mode == 1 ? 1 : mode == 2 ? 2 : 0) + (write_out ? 1 : 0))));
       cudaError_t e = launch_recurrence_batch(prec, in, write_out ? V.spec : nullptr, bk,
-                                              g.max_ntau, tr ? 1 : 0, 1.0, V.acc, coef, mode, 0,
+                                              g.max_ntau, tr ? 1 : 0, 1.0, acc, coef, mode, 0,
                                               g.rtiles, g.nrtiles, B.probs, B.st);
       if (e != cudaSuccess) return cuda_fail(e, "batched recurrence");
       return UFG_OK;
     };
-    SliceCall fw = base_call(g.lat, FAM_FWD, prec);
-    fw.in = r;
-    fw.out = V.spec;
-    if (prep_r != nullptr) {
-      fw.prep_r = prep_r;
-      fw.prep_v = prep_v;
-      fw.prep_out = const_cast<void*>(r);
+    if (B.mom) {
+      UFG_TRY(rec(r, cw[0], 1, d > 0));
+    } else {
+      SliceCall fw = base_call(g.lat, FAM_FWD, prec);
+      fw.in = r;
+      fw.out = V.spec;
+      if (prep_r != nullptr) {
+        fw.prep_r = prep_r;
+        fw.prep_v = prep_v;
+        fw.prep_out = const_cast<void*>(r);
+      }
+      UFG_TRY(slice(B, g, fw, 0));
+      UFG_TRY(rec(V.spec, cw[0], 1, d > 0));
     }
-    UFG_TRY(slice(B, g, fw, 0));
-    UFG_TRY(rec(V.spec, cw[0], 1, d > 0));
     const bool fused = slice_m1w_supported(g.lat->nx, prec);
+    if (B.mom && !fused) return cuda_fail(cudaErrorInvalidValue, "momentum-basis WCE");
     for (int nn = 1; nn <= d; ++nn) {
       if (fused) {  // -A M1 (or M1^T) in momentum space in one kernel: spec -> wr
         SliceCall m = base_call(g.lat, FAM_INV, prec);
@@ -298,10 +336,12 @@ ufg_status wce_b(Batch& B, int prec, const void* r, void* z, bool tr,
       }
       UFG_TRY(rec(fused ? V.wr : V.spec, cw[nn], 2, nn < d));
     }
-    SliceCall iv = base_call(g.lat, FAM_INV, prec);
-    iv.in = V.acc;
-    iv.out = z;
-    UFG_TRY(slice(B, g, iv, 0));
+    if (!B.mom) {
+      SliceCall iv = base_call(g.lat, FAM_INV, prec);
+      iv.in = V.acc;
+      iv.out = z;
+      UFG_TRY(slice(B, g, iv, 0));
+    }
   }
   return UFG_OK;
 }
@@ -334,7 +374,7 @@ ufg_status bicg_b(Batch& B, int prec, int op, const std::vector<double>& tol,
   const bool tr = op == BOP_MDAG;
   // the direction update rides on the preconditioner's first forward transform where every
   // group runs it on the TMA kernel
-  bool fuse_p = pc;
+  bool fuse_p = pc && !B.mom;
   for (auto& g : B.groups)
     fuse_p = fuse_p && slice_tma_prep_supported(g.lat->nx, prec, g.lat->use_tma[prec]);
   for (int p = 0; p < B.n; ++p) {
@@ -391,8 +431,8 @@ ufg_status bicg_b(Batch& B, int prec, int op, const std::vector<double>& tol,
     return UFG_OK;
   };
   char key[128];
-  snprintf(key, sizeof(key), "bicg|%d|%d|%d|%d|%d|%d", prec, op, check_every, B.pc_kind,
-           B.pc.order, B.pc.euler);
+  snprintf(key, sizeof(key), "bicg|%d|%d|%d|%d|%d|%d|%d", prec, op, check_every, B.pc_kind,
+           B.pc.order, B.pc.euler, B.mom ? 1 : 0);
   std::vector<int> restarts(B.n, 0);
   while (true) {
     UFG_TRY(read_scs(B));
@@ -526,8 +566,10 @@ ufg_status mixed_glue(Batch& B, int mode, double* x64, float* y32, const std::ve
   return UFG_OK;
 }
 
-// Solves A x = rhs (FP64 arenas) for every problem to per-problem relative tolerances.
-ufg_status solve_b(Batch& B, int op, const double* rhs, double* x, const std::vector<double>& tol,
+// Solves A x = rhs (FP64 arenas, in the batch's current basis) for every problem to per-problem
+// relative tolerances.
+ufg_status solve_in_basis(Batch& B, int op, const double* rhs, double* x,
+                          const std::vector<double>& tol,
                    const std::vector<char>& want, const ufg_params* p, std::vector<int>& iters,
                    std::vector<int>& outer, std::vector<int>& restarts, std::vector<int>& done) {
   const size_t bytes = (size_t)B.S * sizeof(double);
@@ -676,6 +718,51 @@ ufg_status solve_b(Batch& B, int op, const double* rhs, double* x, const std::ve
   return UFG_OK;
 }
 
+// y = F x (inverse: F^T x) per slice for every problem, FP64 arenas
+ufg_status fourier_b(Batch& B, const double* x, double* y, bool inverse) {
+  for (auto& g : B.groups) {
+    SliceCall c = base_call(g.lat, inverse ? FAM_INV : FAM_FWD, 0);
+    c.in = x;
+    c.out = y;
+    UFG_TRY(slice(B, g, c, -1));
+  }
+  return UFG_OK;
+}
+
+// Whether the batch solves in the momentum basis: with the WCE preconditioner, whose forward and
+// inverse transforms it removes, and where every group has the fused momentum-space operator in
+// the precisions the solve uses (UFG_NO_MOMENTUM=1 keeps the position basis).
+bool momentum_basis(const Batch& B, const ufg_params* p) {
+  static int env = -1;
+  if (env < 0) {
+    const char* e = std::getenv("UFG_NO_MOMENTUM");
+    env = (e && e[0] == '1') ? 0 : 1;
+  }
+  if (!env || B.pc_kind != UFG_PC_WCE) return false;
+  for (const auto& g : B.groups) {
+    if (!slice_m1w_supported(g.lat->nx, 0)) return false;
+    if (p->precision == UFG_MIXED && !slice_m1w_supported(g.lat->nx, 1)) return false;
+  }
+  return true;
+}
+
+// solve_in_basis in the momentum basis where it applies: rhs to F rhs, the solve, x = F^T x^.
+// Problems outside `want` get x = 0 there.
+ufg_status solve_b(Batch& B, int op, const double* rhs, double* x, const std::vector<double>& tol,
+                   const std::vector<char>& want, const ufg_params* p, std::vector<int>& iters,
+                   std::vector<int>& outer, std::vector<int>& restarts, std::vector<int>& done) {
+  if (!momentum_basis(B, p))
+    return solve_in_basis(B, op, rhs, x, tol, want, p, iters, outer, restarts, done);
+  UFG_TRY(fourier_b(B, rhs, B.bm64, false));
+  UFG_CUDA(cudaMemsetAsync(B.xm64, 0, (size_t)B.S * sizeof(double), B.st));
+  B.mom = true;
+  const ufg_status s = solve_in_basis(B, op, B.bm64, B.xm64, tol, want, p, iters, outer,
+                                      restarts, done);
+  B.mom = false;
+  UFG_TRY(s);
+  return fourier_b(B, B.xm64, x, true);
+}
+
 std::string signature(int n, const ufg_problem* probs) {
   std::string sig;
   char buf[96];
@@ -812,6 +899,8 @@ ufg_status setup(Batch& B, int n, const ufg_problem* probs) {
   UFG_TRY(B.alloc(&B.y64, S));
   UFG_TRY(B.alloc(&B.rc64, S));
   UFG_TRY(B.alloc(&B.cr64, S));
+  UFG_TRY(B.alloc(&B.xm64, S));
+  UFG_TRY(B.alloc(&B.bm64, S));
   return UFG_OK;
 }
 

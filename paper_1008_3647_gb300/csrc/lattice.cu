@@ -600,6 +600,41 @@ ufg_status ufg_apply_M0invT(ufg_field* f, const void* x, void* y, int prec, void
   return op_M0inv(f, prec, x, y, tmp, 1, as_stream(stream));
 }
 
+ufg_status ufg_fourier(ufg_field* f, const void* x, void* y, int prec, int inverse,
+                       void* stream) {
+  clear_error();
+  UFG_TRY(check_vec(f, x, y, prec));
+  SliceCall c = base_call(f->lat, inverse ? FAM_INV : FAM_FWD, prec);
+  c.in = x;
+  c.out = y;
+  return run(f->lat, c, as_stream(stream));
+}
+
+ufg_status ufg_apply_M_momentum(ufg_field* f, const void* x, void* y, int prec, int transpose,
+                                void* stream) {
+  clear_error();
+  UFG_TRY(check_vec(f, x, y, prec));
+  const ufg_lattice* lat = f->lat;
+  if (!slice_m1w_supported(lat->nx, prec)) {
+    set_error("momentum-space apply built for FP32 N_x = 16 and FP64 N_x = 8, 16 (got N_x = %d)",
+              lat->nx);
+    return UFG_INVALID_ARG;
+  }
+  SliceCall c = base_call(lat, FAM_INV, prec);
+  c.fam = FAM_M1W;
+  c.coef2 = base_call(lat, FAM_FWD, prec).coef;
+  c.m1w_full = 1;
+  c.in = x;
+  c.pre = fld(f, 'w', prec);
+  const void* bk = prec ? (const void*)lat->bk32 : (const void*)lat->bk64;
+  if (transpose) c.bkpre = bk;
+  else c.bkpost = bk;
+  c.shift = transpose ? +1 : -1;
+  c.a = 1.0;
+  c.out = y;
+  return run(lat, c, as_stream(stream));
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------------

@@ -197,6 +197,7 @@ std::string slice_kernel_name(const SliceCall& c, int N) {
     if (c.prep_out) s += "+prep";
   } else {
     s += c.shift > 0 ? "T" : "";
+    if (c.m1w_full) s += (c.want_dotP || c.want_self) ? "+full+dot" : "+full";
   }
   s += " N" + std::to_string(N) + (c.prec ? " f32" : " f64");
   return s;

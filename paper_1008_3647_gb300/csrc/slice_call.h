@@ -75,6 +75,11 @@ struct SliceCall {
   const void* prep_r = nullptr;
   const void* prep_v = nullptr;
   void* prep_out = nullptr;
+  // FAM_M1W with m1w_full = 1: the whole matrix M (shift -1) or M^T (shift +1) in the momentum
+  // basis, out = full_scale * M x + bU * U with the partials as the KIN family; pre is then the
+  // potential w = 1 + A sin(sigma) and a = 1
+  int m1w_full = 0;
+  double full_scale = 1.0;
 };
 
 // Launches the slice kernel for lattice extent N (explicitly instantiated per N).

@@ -527,6 +527,18 @@ struct M1wArgs {
   int scale_by_A;
   int ntau;
   int* err;
+  // FULL (the whole operator in momentum space, see slice_m1w_kernel): identity term read from
+  // the input arena, out = full_scale * M x + bU * U, partial sums and the batched scalar step
+  const R* xin;
+  const R* U;
+  const R* dotP;
+  double full_scale, bU;
+  int want_dotP, want_self;
+  double* partials;
+  int fop;
+  DevScalars* scs;
+  unsigned* counters;
+  int part_base;
 };
 
 template <int N, typename R>
@@ -563,7 +575,13 @@ __device__ __forceinline__ void swz_ypass(R* xs, const LineCoef<N, R>& cf) {
   }
 }
 
-template <int N, typename R, int DIR>
+//
+// FULL: the fermion matrix itself in the momentum basis, x = F^T x^ per slice.  With
+// B_t = e^{-tau K} w_t, w_t = 1 + A sin(sigma_t) (Sec. 1), and F e^{-tau K} = b .* F:
+//   DIR 0:  (M x^)_t   = x^_t + sgn(t) b .* F( w_{t-1} .* F^T x^_{t-1} )
+//   DIR 1:  (M^T x^)_t = x^_t + sgn(t) F( w_t .* F^T( b .* x^_{t+1} ) )
+// i.e. the same three steps with w as the site multiplier and a = 1, plus the identity term.
+template <int N, typename R, int DIR, bool FULL>
 __global__ void __launch_bounds__(TMA_NT, (m1w_min_blocks<N, R>()))
 slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
   pdl_begin();
@@ -572,6 +590,7 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
   constexpr int VOL = N * NN;
   extern __shared__ __align__(1024) unsigned char tma_smem[];
   __shared__ alignas(8) uint64_t bar;
+  __shared__ double red[FULL ? TMA_NT / 32 : 1][2];
   const int tid = threadIdx.x;
   int t_out, ntau;
   size_t off = 0;
@@ -598,11 +617,12 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
   R* const xs = reinterpret_cast<R*>(base);
   R* const ss = xs + VOL;
   R* const ks = ss + VOL;
+  const int row_in = (int)((off + (size_t)t_in * VOL) / N);
   if (tid == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     mbar_expect_tx(&bar, (uint32_t)(VOL * sizeof(R)) * (DIR == 1 ? 3u : 2u));
-    tma_load_rows(xs, &A.tm_in, (int)((off + (size_t)t_in * VOL) / N), &bar);
+    tma_load_rows(xs, &A.tm_in, row_in, &bar);
     tma_load_rows(ss, &A.tm_s, (int)((off + (size_t)t_s * VOL) / N), &bar);
     if (DIR == 1) tma_load_rows(ks, &A.tm_k, 0, &bar);
   }
@@ -640,20 +660,72 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
   __syncthreads();
   const R f2 = DIR == 0 ? sgn * R(acoef) : R(1);
   R* const gout = A.out + off + (size_t)t_out * VOL;
-  for (int q = tid; q < NN; q += TMA_NT) {
-    const int y = q / N, x = q - (q / N) * N;
-    R v[N];
+  if constexpr (!FULL) {
+    for (int q = tid; q < NN; q += TMA_NT) {
+      const int y = q / N, x = q - (q / N) * N;
+      R v[N];
 #pragma unroll
-    for (int z = 0; z < N; ++z) v[z] = xs[G::off(z * N + y, x)];
-    line_op<N, R, false, true>(v, A.cf_z, [&](int zp, R val) {
-      R o = f2 * val;
-      if constexpr (DIR == 0) o *= __ldg(A.bk + zp * NN + q);
-      gout[zp * NN + q] = o;
-    });
+      for (int z = 0; z < N; ++z) v[z] = xs[G::off(z * N + y, x)];
+      line_op<N, R, false, true>(v, A.cf_z, [&](int zp, R val) {
+        R o = f2 * val;
+        if constexpr (DIR == 0) o *= __ldg(A.bk + zp * NN + q);
+        gout[zp * NN + q] = o;
+      });
+    }
+  } else {
+    const size_t so = off + (size_t)t_out * VOL;
+    const R* __restrict__ gid = A.xin + so;
+    const R* __restrict__ gU = A.U ? A.U + so : nullptr;
+    const R* __restrict__ gdot = A.dotP ? A.dotP + so : nullptr;
+    const R fs = R(A.full_scale), bU = R(A.bU);
+    R acc_dot = R(0), acc_self = R(0);
+    for (int q = tid; q < NN; q += TMA_NT) {
+      const int y = q / N, x = q - (q / N) * N;
+      R v[N];
+#pragma unroll
+      for (int z = 0; z < N; ++z) v[z] = xs[G::off(z * N + y, x)];
+      line_op<N, R, false, true>(v, A.cf_z, [&](int zp, R val) {
+        const int g = zp * NN + q;
+        R m = f2 * val;
+        if constexpr (DIR == 0) m *= __ldg(A.bk + g);
+        R o = fs * (m + __ldg(gid + g));
+        if (gU != nullptr) o = fmadd(bU, __ldg(gU + g), o);
+        gout[g] = o;
+        if (A.want_dotP) acc_dot = fmadd(o, __ldg(gdot + g), acc_dot);
+        if (A.want_self) acc_self = fmadd(o, o, acc_self);
+      });
+    }
+    if (A.want_dotP || A.want_self) {  // one partial pair per CTA, as the slice kernels
+      double pd = (double)acc_dot, ps = (double)acc_self;
+#pragma unroll
+      for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        pd += __shfl_xor_sync(0xffffffffu, pd, o2);
+        ps += __shfl_xor_sync(0xffffffffu, ps, o2);
+      }
+      if ((tid & 31) == 0) {
+        red[tid >> 5][0] = pd;
+        red[tid >> 5][1] = ps;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double d = 0.0, q2 = 0.0;
+        for (int w = 0; w < TMA_NT / 32; ++w) {
+          d += red[w][0];
+          q2 += red[w][1];
+        }
+        A.partials[2 * blockIdx.x] = d;
+        A.partials[2 * blockIdx.x + 1] = q2;
+      }
+      if (A.fop >= 0 && A.tiles != nullptr) {
+        const int prob = A.tiles[blockIdx.x].prob;
+        last_block_update(A.fop, A.scs + prob, A.partials, A.probs[prob].st0 - A.part_base,
+                          A.probs[prob].st1 - A.part_base, A.counters + prob);
+      }
+    }
   }
 }
 
-template <int N, typename R, int DIR>
+template <int N, typename R, int DIR, bool FULL>
 inline cudaError_t m1w_launch(const SliceCall& c, cudaStream_t st) {
   constexpr int VOL = N * N * N;
   M1wArgs<N, R> a;
@@ -682,8 +754,25 @@ inline cudaError_t m1w_launch(const SliceCall& c, cudaStream_t st) {
   a.scale_by_A = c.scale_by_A;
   a.ntau = c.ntau;
   a.err = c.err;
+  if constexpr (FULL) {
+    if ((c.want_dotP && c.dotP == nullptr) || ((c.want_dotP || c.want_self) && !c.partials) ||
+        (c.fop >= 0 && (c.tiles == nullptr || c.scs == nullptr || c.counters == nullptr)))
+      return cudaErrorInvalidValue;
+    a.xin = static_cast<const R*>(c.in);
+    a.U = static_cast<const R*>(c.U);
+    a.dotP = static_cast<const R*>(c.dotP);
+    a.full_scale = c.full_scale;
+    a.bU = c.bU;
+    a.want_dotP = c.want_dotP;
+    a.want_self = c.want_self;
+    a.partials = c.partials;
+    a.fop = c.fop;
+    a.scs = c.scs;
+    a.counters = c.counters;
+    a.part_base = c.part_base;
+  }
   const size_t smem = (size_t)(DIR == 1 ? 3 : 2) * VOL * sizeof(R) + 1024;
-  auto kern = slice_m1w_kernel<N, R, DIR>;
+  auto kern = slice_m1w_kernel<N, R, DIR, FULL>;
   static int configured = 0;
   if (!configured) {
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -699,15 +788,20 @@ inline cudaError_t m1w_launch(const SliceCall& c, cudaStream_t st) {
   return launch_k(kern, dim3(units), dim3(TMA_NT), smem, st, 1, a);
 }
 
+template <int N, typename R, bool FULL>
+inline cudaError_t m1w_dir(const SliceCall& c, cudaStream_t st) {
+  return c.shift < 0 ? m1w_launch<N, R, 0, FULL>(c, st) : m1w_launch<N, R, 1, FULL>(c, st);
+}
+
 template <int N>
 inline cudaError_t slice_m1w_try(const SliceCall& c, cudaStream_t st) {
   if (!slice_m1w_supported(N, c.prec) || c.shift == 0) return cudaErrorNotSupported;
   if constexpr (N == 16) {
-    if (c.prec == 1)
-      return c.shift < 0 ? m1w_launch<16, float, 0>(c, st) : m1w_launch<16, float, 1>(c, st);
-    return c.shift < 0 ? m1w_launch<16, double, 0>(c, st) : m1w_launch<16, double, 1>(c, st);
+    if (c.prec == 1) return c.m1w_full ? m1w_dir<16, float, true>(c, st)
+                                       : m1w_dir<16, float, false>(c, st);
+    return c.m1w_full ? m1w_dir<16, double, true>(c, st) : m1w_dir<16, double, false>(c, st);
   } else if constexpr (N == 8) {
-    return c.shift < 0 ? m1w_launch<8, double, 0>(c, st) : m1w_launch<8, double, 1>(c, st);
+    return c.m1w_full ? m1w_dir<8, double, true>(c, st) : m1w_dir<8, double, false>(c, st);
   }
   return cudaErrorNotSupported;
 }

@@ -99,6 +99,8 @@ _SIGS = {
     "ufg_apply_kinetic": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "ufg_apply_M0inv": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "ufg_apply_M0invT": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    "ufg_fourier": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp]),
+    "ufg_apply_M_momentum": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp]),
     "ufg_solver_create": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
     "ufg_solver_destroy": (None, [_vp]),
     "ufg_set_preconditioner": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(PcParams)]),
@@ -285,6 +287,26 @@ def ufg_apply_M0inv(field, x, y=None):
 
 def ufg_apply_M0invT(field, x, y=None):
     return _apply("ufg_apply_M0invT", field, x, y)
+
+
+def _apply_flag(name, field, x, flag, y=None):
+    _vec(x, field.lattice.shape)
+    if y is None:
+        y = torch.empty_like(x)
+    _vec(y, field.lattice.shape, (x.dtype,))
+    prec = UFG_FP64 if x.dtype == torch.float64 else UFG_FP32
+    _check(getattr(load(), name)(field._h, _ptr(x), _ptr(y), prec, int(flag), _stream()))
+    return y
+
+
+def ufg_fourier(field, x, inverse=False, y=None):
+    """Per-slice orthogonal real Fourier transform (inverse: its transpose)."""
+    return _apply_flag("ufg_fourier", field, x, inverse, y)
+
+
+def ufg_apply_M_momentum(field, x, transpose=False, y=None):
+    """M (or M^T) in the momentum basis: F M F^T x per slice-stacked vector."""
+    return _apply_flag("ufg_apply_M_momentum", field, x, transpose, y)
 
 
 def _pc_params(kind, degree=16, eps=0.0, scale=0.0, alpha=2.0, order=2, euler=False):

@@ -91,3 +91,29 @@ def test_batch_rejects_bad_problem(ufg):
     probs[0]["nx"] = 7
     with pytest.raises(ufg.UfgError):
         ufg.ufg_solve_batch(probs, "wce", {"order": 1})
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_in_momentum_basis_matches_solo(ufg, precision):
+    # every group has the fused momentum-space operator in both precisions (N_x = 16 only), so
+    # the batch iterates on F x; the solo solves iterate in position space
+    shapes = [(16, 64, 11), (16, 48, 14)]
+    probs = _problems(shapes)
+    prec = ufg.UFG_FP64 if precision == "fp64" else ufg.UFG_MIXED
+    stats = ufg.ufg_solve_batch(probs, "wce", {"order": 2}, tol=1e-10, precision=prec)
+    for pr, st in zip(probs, stats):
+        assert st["status"] == ufg.UFG_OK, st
+        olat = O.Lattice(pr["nx"], pr["ntau"])
+        r = pr["b_h"] - O.apply_Q(olat, pr["sigma_h"], pr["x"].cpu().numpy())
+        assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(pr["b_h"])
+        lat = ufg.Lattice(pr["nx"], pr["ntau"])
+        solver = ufg.Solver(lat)
+        solver.ufg_set_preconditioner("wce", order=2)
+        field = ufg.Field(lat, pr["sigma"])
+        xs, ss = solver.ufg_solve_bicgstab_two_step(field, pr["b"], tol=1e-10, precision=prec)
+        assert ss["status"] == ufg.UFG_OK
+        if precision == "fp64" and ss["restarts"] == 0 and st["restarts"] == 0:
+            # the same iteration in an orthogonal basis: only rounding differs
+            assert abs(ss["iterations"] - st["iterations"]) <= 2, (
+                ss["iterations_step"], st["iterations_step"])
+        assert float((xs - pr["x"]).norm() / xs.norm()) < 1e-7
