@@ -515,6 +515,7 @@ struct M1wArgs {
   CUtensorMap tm_in;  // momentum-space input arena
   CUtensorMap tm_s;   // site multiplier arena
   CUtensorMap tm_k;   // per-mode factor (one slice), DIR 1
+  CUtensorMap tm_dot; // FULL with want_dotP: the dot operand arena
   LineCoef<N, R> ci_x, ci_y, ci_z;  // inverse transform, one copy per pass (see TmaArgs)
   LineCoef<N, R> cf_x, cf_y, cf_z;  // forward transform
   const R* bk;                      // per-mode factor, DIR 0 (applied to the output)
@@ -527,9 +528,8 @@ struct M1wArgs {
   int scale_by_A;
   int ntau;
   int* err;
-  // FULL (the whole operator in momentum space, see slice_m1w_kernel): identity term read from
-  // the input arena, out = full_scale * M x + bU * U, partial sums and the batched scalar step
-  const R* xin;
+  // FULL (the whole operator in momentum space, see slice_m1w_kernel): out = full_scale * M x +
+  // bU * U, partial sums and the batched scalar step
   const R* U;
   const R* dotP;
   double full_scale, bU;
@@ -581,6 +581,8 @@ __device__ __forceinline__ void swz_ypass(R* xs, const LineCoef<N, R>& cf) {
 //   DIR 0:  (M x^)_t   = x^_t + sgn(t) b .* F( w_{t-1} .* F^T x^_{t-1} )
 //   DIR 1:  (M^T x^)_t = x^_t + sgn(t) F( w_t .* F^T( b .* x^_{t+1} ) )
 // i.e. the same three steps with w as the site multiplier and a = 1, plus the identity term.
+// Once the inverse transform has consumed the multiplier (and b) boxes, they receive x^_t and
+// the dot operand's slice by TMA, overlapping the forward x and y passes.
 template <int N, typename R, int DIR, bool FULL>
 __global__ void __launch_bounds__(TMA_NT, (m1w_min_blocks<N, R>()))
 slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
@@ -618,6 +620,7 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
   R* const ss = xs + VOL;
   R* const ks = ss + VOL;
   const int row_in = (int)((off + (size_t)t_in * VOL) / N);
+  R* const ds = ks;  // FULL: the dot operand's slice (third box)
   if (tid == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -653,6 +656,15 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
     });
   }
   __syncthreads();
+  if constexpr (FULL) {  // the multiplier and b boxes are free: prefetch the epilogue operands
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const int row_out = (int)((off + (size_t)t_out * VOL) / N);
+      mbar_expect_tx(&bar, (uint32_t)(VOL * sizeof(R)) * (A.want_dotP ? 2u : 1u));
+      tma_load_rows(ss, &A.tm_in, row_out, &bar);
+      if (A.want_dotP) tma_load_rows(ds, &A.tm_dot, row_out, &bar);
+    }
+  }
   // forward transform (spectral output)
   swz_xpass<N, R, false, true, false>(xs, nullptr, A.cf_x);
   __syncthreads();
@@ -673,10 +685,17 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
       });
     }
   } else {
+    {
+      uint32_t n = 0;
+      while (!mbar_try_wait(&bar, 1u)) {
+        if (++n > TMA_WAIT_LIMIT) {
+          if (A.err != nullptr) atomicExch(A.err, 1);
+          break;
+        }
+      }
+    }
     const size_t so = off + (size_t)t_out * VOL;
-    const R* __restrict__ gid = A.xin + so;
     const R* __restrict__ gU = A.U ? A.U + so : nullptr;
-    const R* __restrict__ gdot = A.dotP ? A.dotP + so : nullptr;
     const R fs = R(A.full_scale), bU = R(A.bU);
     R acc_dot = R(0), acc_self = R(0);
     for (int q = tid; q < NN; q += TMA_NT) {
@@ -686,12 +705,13 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
       for (int z = 0; z < N; ++z) v[z] = xs[G::off(z * N + y, x)];
       line_op<N, R, false, true>(v, A.cf_z, [&](int zp, R val) {
         const int g = zp * NN + q;
+        const int os = G::off(zp * N + y, x);
         R m = f2 * val;
         if constexpr (DIR == 0) m *= __ldg(A.bk + g);
-        R o = fs * (m + __ldg(gid + g));
+        R o = fs * (m + ss[os]);
         if (gU != nullptr) o = fmadd(bU, __ldg(gU + g), o);
         gout[g] = o;
-        if (A.want_dotP) acc_dot = fmadd(o, __ldg(gdot + g), acc_dot);
+        if (A.want_dotP) acc_dot = fmadd(o, ds[os], acc_dot);
         if (A.want_self) acc_self = fmadd(o, o, acc_self);
       });
     }
@@ -758,7 +778,8 @@ inline cudaError_t m1w_launch(const SliceCall& c, cudaStream_t st) {
     if ((c.want_dotP && c.dotP == nullptr) || ((c.want_dotP || c.want_self) && !c.partials) ||
         (c.fop >= 0 && (c.tiles == nullptr || c.scs == nullptr || c.counters == nullptr)))
       return cudaErrorInvalidValue;
-    a.xin = static_cast<const R*>(c.in);
+    if (c.want_dotP && encode_rows<R>(&a.tm_dot, c.dotP, nelem, N, N * N) != cudaSuccess)
+      return cudaErrorNotSupported;
     a.U = static_cast<const R*>(c.U);
     a.dotP = static_cast<const R*>(c.dotP);
     a.full_scale = c.full_scale;
@@ -771,7 +792,8 @@ inline cudaError_t m1w_launch(const SliceCall& c, cudaStream_t st) {
     a.counters = c.counters;
     a.part_base = c.part_base;
   }
-  const size_t smem = (size_t)(DIR == 1 ? 3 : 2) * VOL * sizeof(R) + 1024;
+  const size_t smem =
+      (size_t)((DIR == 1 || (FULL && c.want_dotP)) ? 3 : 2) * VOL * sizeof(R) + 1024;
   auto kern = slice_m1w_kernel<N, R, DIR, FULL>;
   static int configured = 0;
   if (!configured) {
