@@ -77,7 +77,11 @@ typedef struct {
  *   maxit     : iteration cap of each Krylov solve.
  *   precision : UFG_FP64, or UFG_MIXED (FP32 inner solves inside an FP64 defect-correction loop).
  *   x0_given  : nonzero uses the content of x as the initial guess (else x0 = 0).
- *   inner_tol : MIXED only, relative reduction asked of each FP32 inner solve (e.g. 1e-5).
+ *   inner_tol : MIXED only, relative reduction asked of each FP32 inner solve (0: 1e-5).  A
+ *               negative value autotunes it: the first such call of a solver and method times
+ *               the whole solve for 1e-3, 1e-4, 1e-5 and 1e-6 (four extra solves, from x0 = 0,
+ *               the caller's x0 restored) and keeps the fastest that converges.  Batched solves
+ *               use reliable updates instead and ignore it.
  *   check_every : Krylov iterations between host convergence checks (CUDA-graph replay length). */
 typedef struct {
   double tol;
@@ -101,6 +105,7 @@ typedef struct {
   double mv_paper;
   double true_residual;    /* ||b - M^T M x|| / ||b|| in FP64 at exit */
   double seconds;          /* wall time of the call */
+  double inner_tol;        /* MIXED single-problem solves: the inner tolerance used (else 0) */
 } ufg_stats;
 
 /* One independent problem of a batched solve.  sigma, b, x: FP64 arrays of its own lattice size

@@ -62,6 +62,8 @@ struct ufg_solver {
   };
   std::map<std::string, GraphEntry> graphs;
   Counts counts;
+  double inner_auto[2] = {0.0, 0.0};  // autotuned inner tolerance per method (0: not yet)
+  double* x0s64 = nullptr;            // the caller's initial guess kept across tuning trials
 };
 
 bool ufg::graphs_enabled() {
@@ -939,6 +941,7 @@ void ufg_solver_destroy(ufg_solver* S) {
   dev_free(S->rc64);
   dev_free(S->xs64);
   dev_free(S->xf64);
+  dev_free(S->x0s64);
   dev_free(S->parts);
   dev_free(S->sc);
   dev_free(S->red_dev);
@@ -999,6 +1002,57 @@ ufg_status ufg_apply_preconditioner(ufg_solver* S, ufg_field* f, const void* r, 
   return pc_apply(S, f, precision, r, z, transpose != 0);
 }
 
+using SolveFn = ufg_status (*)(ufg_solver*, ufg_field*, const double*, double*,
+                               const ufg_params*, ufg_stats*, void*);
+
+// Mixed precision with inner_tol < 0: the inner tolerance is chosen once per solver and method
+// by timing the whole solve of this right-hand side (from x0 = 0) for each candidate; the
+// fastest one that converges is kept (1e-5 if none does).  The caller's initial guess is
+// restored afterwards.
+static ufg_status tune_inner(ufg_solver* S, int method, ufg_field* f, const double* b, double* x,
+                             const ufg_params* p, void* stream, SolveFn fn, double* chosen) {
+  if (S->inner_auto[method] > 0.0) {
+    *chosen = S->inner_auto[method];
+    return UFG_OK;
+  }
+  const size_t bytes = (size_t)S->lat->S * sizeof(double);
+  if (p->x0_given) {
+    if (!S->x0s64) UFG_TRY(dev_alloc(&S->x0s64, (size_t)S->lat->S));
+    UFG_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    UFG_CUDA(cudaMemcpy(S->x0s64, x, bytes, cudaMemcpyDefault));
+  }
+  double best = 1e-5, best_s = 0.0;
+  bool found = false;
+  for (double cand : {1e-3, 1e-4, 1e-5, 1e-6}) {
+    ufg_params q = *p;
+    q.inner_tol = cand;
+    q.x0_given = 0;
+    const auto t0 = std::chrono::steady_clock::now();
+    const ufg_status s = fn(S, f, b, x, &q, nullptr, stream);
+    UFG_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    const double secs =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (s == UFG_OK && (!found || secs < best_s)) {
+      best = cand;
+      best_s = secs;
+      found = true;
+    } else if (s != UFG_OK && s != UFG_NOT_CONVERGED && s != UFG_BREAKDOWN &&
+               s != UFG_NONFINITE) {
+      return s;  // a CUDA or argument error, not a property of the candidate
+    }
+  }
+  if (p->x0_given) UFG_CUDA(cudaMemcpy(x, S->x0s64, bytes, cudaMemcpyDefault));
+  clear_error();
+  S->inner_auto[method] = best;
+  *chosen = best;
+  return UFG_OK;
+}
+
+static double inner_used(const ufg_params* p) {
+  if (p->precision != UFG_MIXED) return 0.0;
+  return p->inner_tol > 0 ? p->inner_tol : 1e-5;
+}
+
 ufg_status ufg_solve_cg_normal(ufg_solver* S, ufg_field* f, const double* b, double* x,
                                const ufg_params* p, ufg_stats* stats, void* stream) {
   clear_error();
@@ -1006,6 +1060,12 @@ ufg_status ufg_solve_cg_normal(ufg_solver* S, ufg_field* f, const double* b, dou
   if (S->pc_kind == UFG_PC_WCE) {
     set_error("CG on the normal equations takes the Chebyshev or SCA preconditioner");
     return UFG_INVALID_ARG;
+  }
+  ufg_params tuned;
+  if (p->precision == UFG_MIXED && p->inner_tol < 0) {
+    tuned = *p;
+    UFG_TRY(tune_inner(S, 0, f, b, x, p, stream, ufg_solve_cg_normal, &tuned.inner_tol));
+    p = &tuned;
   }
   const auto t0 = std::chrono::steady_clock::now();
   CallGuard g(S, as_stream(stream));
@@ -1029,7 +1089,11 @@ ufg_status ufg_solve_cg_normal(ufg_solver* S, ufg_field* f, const double* b, dou
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   fill_stats(stats, S, o, rel, secs, false, st);
-  if (stats) stats->iterations_step[0] = o.iters, stats->iterations_step[1] = 0;
+  if (stats) {
+    stats->iterations_step[0] = o.iters;
+    stats->iterations_step[1] = 0;
+    stats->inner_tol = inner_used(p);
+  }
   return st;
 }
 
@@ -1040,6 +1104,12 @@ ufg_status ufg_solve_bicgstab_two_step(ufg_solver* S, ufg_field* f, const double
   if (S->pc_kind == UFG_PC_CHEB || S->pc_kind == UFG_PC_SCA) {
     set_error("two-step BiCGStab takes the weak-coupling preconditioner (or none)");
     return UFG_INVALID_ARG;
+  }
+  ufg_params tuned;
+  if (p->precision == UFG_MIXED && p->inner_tol < 0) {
+    tuned = *p;
+    UFG_TRY(tune_inner(S, 1, f, b, x, p, stream, ufg_solve_bicgstab_two_step, &tuned.inner_tol));
+    p = &tuned;
   }
   const auto t0 = std::chrono::steady_clock::now();
   CallGuard g(S, as_stream(stream));
@@ -1096,6 +1166,7 @@ ufg_status ufg_solve_bicgstab_two_step(ufg_solver* S, ufg_field* f, const double
   if (stats) {
     stats->iterations_step[0] = o1.iters;
     stats->iterations_step[1] = o2.iters;
+    stats->inner_tol = inner_used(p);
   }
   return st;
 }

@@ -111,6 +111,36 @@ def test_mixed_precision_16x256(ufg, kind, pc, kw):
     assert err < 1e-6  # both solutions within the 1e-10 residual ball of the same system
 
 
+@pytest.mark.parametrize("kind,pc,kw", [("cg", "sca", {"alpha": 2.0}), ("bicg", "wce", {"order": 2})])
+def test_mixed_inner_tolerance_autotuned(ufg, kind, pc, kw):
+    nx, ntau = 8, 32
+    sigma, b = field_and_source(nx, ntau, 4)
+    lat = ufg.Lattice(nx, ntau)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    solver = ufg.Solver(lat)
+    solver.ufg_set_preconditioner(pc, **kw)
+    fn = solver.ufg_solve_cg_normal if kind == "cg" else solver.ufg_solve_bicgstab_two_step
+    bd = torch.from_numpy(b).cuda()
+    x, st = fn(field, bd, tol=1e-10, precision=ufg.UFG_MIXED, inner_tol=-1.0)
+    assert st["status"] == ufg.UFG_OK, st
+    assert st["inner_tol"] in (1e-3, 1e-4, 1e-5, 1e-6)
+    assert _true_rel(O.Lattice(nx, ntau), sigma, b, x.cpu().numpy()) <= 1e-10
+    # the choice is kept; an initial guess given with the first tuned call of a method survives
+    # the tuning trials (warm start from the solution: the solve that takes x0 - CG, or the
+    # second BiCGStab step - needs almost no iterations)
+    x2, st2 = fn(field, bd, tol=1e-10, precision=ufg.UFG_MIXED, inner_tol=-1.0)
+    assert st2["inner_tol"] == st["inner_tol"]
+    fresh = ufg.Solver(lat)
+    fresh.ufg_set_preconditioner(pc, **kw)
+    fn2 = fresh.ufg_solve_cg_normal if kind == "cg" else fresh.ufg_solve_bicgstab_two_step
+    x3, st3 = fn2(field, bd, x.clone(), tol=1e-10, precision=ufg.UFG_MIXED, inner_tol=-1.0,
+                  x0_given=True)
+    assert st3["status"] == ufg.UFG_OK
+    assert st3["iterations_step"][1 if kind == "bicg" else 0] <= 2, st3
+    fixed = fn(field, bd, tol=1e-10, precision=ufg.UFG_MIXED, inner_tol=1e-4)[1]
+    assert fixed["inner_tol"] == 1e-4
+
+
 def test_host_buffers_match_device_buffers(ufg):
     nx, ntau = 8, 16
     sigma, b = field_and_source(nx, ntau, 9)
