@@ -299,6 +299,32 @@ def run_ufg(args, rank, world, local_rank):
     t_cheb = timed(1, lambda: cheb_box.__setitem__("st", step(ufg.UFG_MIXED, kind="cg")),
                    "step_cg_cheb16")
 
+    # the uneven batch of 96 problems (N_x in {6, 8, 10, 12}, N_tau in {40, 80, 120, 160}, problem i
+    # with seed i + 1), mixed and FP64, one timed step each
+    from paper_1008_3647_gb300.inputs import batch_shapes
+    shapes96 = batch_shapes(96)
+    probs96 = []
+    for i, (nx96, nt96, seed96) in enumerate(shapes96):
+        sg96, bb96 = field_and_source(nx96, nt96, seed96)
+        probs96.append({"nx": nx96, "ntau": nt96, "tau": 0.05, "g": 5.0,
+                        "sigma": torch.from_numpy(sg96).to(dev),
+                        "b": torch.from_numpy(bb96).to(dev),
+                        "x": torch.zeros(nt96, nx96, nx96, nx96, dtype=torch.float64, device=dev)})
+    box96 = {}
+
+    def step96(precision, key):
+        try:
+            box96[key] = ufg.ufg_solve_batch(probs96, "wce", {"order": 2}, tol=TOL,
+                                             precision=precision, check_every=8)
+        except ufg.UfgError as err:  # a problem that broke down: reported, not fatal here
+            box96[key] = [{"status": err.status, "true_residual": float("nan")}]
+
+    step96(ufg.UFG_MIXED, "mixed")
+    t96 = timed(1, lambda: step96(ufg.UFG_MIXED, "mixed"), "step_batch96")
+    step96(ufg.UFG_FP64, "fp64")
+    t96_64 = timed(1, lambda: step96(ufg.UFG_FP64, "fp64"), "step_batch96_fp64")
+    sites96 = sum(nx96 ** 3 * nt96 for nx96, nt96, _ in shapes96)
+
     solves = PER_RANK * world
     value = solves * args.steps / t_mixed
     e2e = solves * args.steps / t_e2e
@@ -359,6 +385,14 @@ def run_ufg(args, rank, world, local_rank):
                   "outer_mean": statistics.mean(s["outer_iterations"] for s in sm),
                   "true_residual_max": max(s["true_residual"] for s in sm),
                   "mv_paper_mean": statistics.mean(s["mv_paper"] for s in sm)},
+        "batch96": {"value": 96 * world / t96, "unit": "solves/s",
+                    "fp64_value": 96 * world / t96_64, "mixed_speedup": t96_64 / t96,
+                    "sites": sites96,
+                    "true_residual_max": max(st["true_residual"] for st in box96["mixed"]),
+                    "not_converged": {k: sum(st["status"] != ufg.UFG_OK for st in v)
+                                      for k, v in box96.items()},
+                    "note": "96 uneven problems per rank in one ufg_solve_batch (BiCGStab + WCE2, "
+                            "tol 1e-10), one timed step each precision"},
         "apply_fp32_32x512": roof["fp32"],
         "apply_fp64_32x512": roof["fp64"],
     }
@@ -395,9 +429,12 @@ def apply_roofline(ufg, torch, dev, stream, hbm, peak_src):
                      "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                      "frac": ach / hbm, "traffic": None, "peak_source": peak_src,
                      "us_per_launch": t * 1e6, "algorithmic_bytes": bytes_}
-    # FP64 is bound by the FP64 pipe on this part: flops of the even/odd line operators
-    H = nx // 2
-    flops_site = 3 * 2 * ((H + 1) ** 2 + (H - 1) ** 2 + 2 * (H - 1)) / nx + 3
+    # FP64 is bound by the FP64 pipe on this part: flops of the two-level even/odd line
+    # operators (blocks (Q+1)^2, Q^2, Q^2, (Q-1)^2 with Q = N/4, one multiply-add each, plus the
+    # two fold levels on input and output, ~4 N adds per line), three passes, and the epilogue
+    Q = nx // 4
+    line_flops = 2 * ((Q + 1) ** 2 + 2 * Q ** 2 + (Q - 1) ** 2) + 4 * nx
+    flops_site = 3 * line_flops / nx + 3
     f64 = out["fp64"]
     f64["flops_per_site"] = flops_site
     f64["achieved_tflops"] = flops_site * lat.ntau * nx ** 3 / (f64["us_per_launch"] * 1e-6) / 1e12
