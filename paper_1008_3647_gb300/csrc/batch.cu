@@ -605,8 +605,12 @@ ufg_status solve_in_basis(Batch& B, int op, const double* rhs, double* x,
   // RU_STALLS consecutive updates that do not halve it, or RU_MAX updates, the problem is
   // finished in FP64.
   constexpr int RU_STALLS = 3, RU_MAX = 60;
+  // A problem whose FP32 recursion needs more than RU_SPAN iterations for one RU_DELTA drop is
+  // handed to the FP64 solver too: the batch waits for its slowest problem, and a stalled FP32
+  // Krylov space can take several times the FP64 iteration count.
+  constexpr int RU_SPAN = 150;
   std::vector<char> fallback(B.n, 0), verified(B.n, 0);
-  std::vector<int> stalls(B.n, 0);
+  std::vector<int> stalls(B.n, 0), it_last(B.n, 0);
   std::vector<double> rlast(B.n, 0.0);
   std::vector<double> bn;
   UFG_TRY(norms_b(B, rhs, bn));
@@ -637,6 +641,20 @@ ufg_status solve_in_basis(Batch& B, int op, const double* rhs, double* x,
   std::vector<double> rn;
   CheckHook hook = [&](bool* changed) -> ufg_status {
     *changed = false;
+    bool stalled = false;
+    for (int i = 0; i < B.n; ++i) {
+      if (!active[i] || verified[i]) continue;
+      DevScalars& h = B.scs_h[i];
+      if (h.done == 0 && h.iters - it_last[i] > RU_SPAN) {
+        h.done = 6;  // finished in FP64 after this solve
+        stalled = true;
+      }
+    }
+    if (stalled) {
+      UFG_TRY(write_scs(B));
+      *changed = true;
+      return UFG_OK;
+    }
     std::vector<double> sc(B.n, 0.0);
     bool upd = false;
     for (int i = 0; i < B.n; ++i) {
@@ -654,8 +672,11 @@ ufg_status solve_in_basis(Batch& B, int op, const double* rhs, double* x,
     *changed = true;
     // fold the increments into x and clear them
     UFG_TRY(mixed_glue(B, 1, x, (float*)V.x, sc));
-    for (int i = 0; i < B.n; ++i)
-      if (sc[i] != 0.0) B.scs_h[i].done = RU_BUSY;
+    for (int i = 0; i < B.n; ++i) {
+      if (sc[i] == 0.0) continue;
+      B.scs_h[i].done = RU_BUSY;
+      it_last[i] = B.scs_h[i].iters;
+    }
     UFG_TRY(write_scs(B));
     UFG_TRY(vecb(B, 1, V_ZERO, RU_BUSY, V.x, nullptr, nullptr, nullptr, nullptr, nullptr,
                  nullptr));
