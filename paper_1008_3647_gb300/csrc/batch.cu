@@ -569,9 +569,9 @@ ufg_status mixed_glue(Batch& B, int mode, double* x64, float* y32, const std::ve
 // Solves A x = rhs (FP64 arenas, in the batch's current basis) for every problem to per-problem
 // relative tolerances.
 ufg_status solve_in_basis(Batch& B, int op, const double* rhs, double* x,
-                          const std::vector<double>& tol,
-                   const std::vector<char>& want, const ufg_params* p, std::vector<int>& iters,
-                   std::vector<int>& outer, std::vector<int>& restarts, std::vector<int>& done) {
+                          const std::vector<double>& tol, const std::vector<char>& want,
+                          const ufg_params* p, std::vector<int>& iters, std::vector<int>& outer,
+                          std::vector<int>& restarts, std::vector<int>& done) {
   const size_t bytes = (size_t)B.S * sizeof(double);
   const int ce = p->check_every > 0 ? p->check_every : 8;
   std::vector<char> active = want;
@@ -605,10 +605,11 @@ ufg_status solve_in_basis(Batch& B, int op, const double* rhs, double* x,
   // RU_STALLS consecutive updates that do not halve it, or RU_MAX updates, the problem is
   // finished in FP64.
   constexpr int RU_STALLS = 3, RU_MAX = 60;
-  // A problem whose FP32 recursion needs more than RU_SPAN iterations for one RU_DELTA drop is
-  // handed to the FP64 solver too: the batch waits for its slowest problem, and a stalled FP32
-  // Krylov space can take several times the FP64 iteration count.
-  constexpr int RU_SPAN = 150;
+  // A problem whose FP32 recursion needs more than RU_SPAN iterations for one RU_DELTA drop
+  // (about four times the usual) is handed to the FP64 solver too: the batch waits for its
+  // slowest problem, and a stalled FP32 Krylov space can take several times the FP64 iteration
+  // count.
+  constexpr int RU_SPAN = 60;
   std::vector<char> fallback(B.n, 0), verified(B.n, 0);
   std::vector<int> stalls(B.n, 0), it_last(B.n, 0);
   std::vector<double> rlast(B.n, 0.0);
