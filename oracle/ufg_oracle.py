@@ -10,7 +10,7 @@ literally as "K is diagonal in momentum space": a 3-D discrete Fourier transform
 as a library step), a multiplication by exp(-tau E(k)) on the momentum grid of Sec. 1, and the
 inverse transform.  The GPU path instead uses a real separable circulant contraction.
 
-Conventions (readings of the paper, all listed in the design doc):
+Conventions (readings of the paper where it leaves a choice open):
   * arrays are shaped [N_tau, N_x, N_x, N_x] = [t][z][y][x]; slice t (0-based) is the paper's
     time index j = t + 1, so B_t uses sigma_t and the corner block of Eq. (MatrixM) is
     B_{N_tau-1} mapping slice N_tau-1 onto slice 0;
