@@ -43,7 +43,7 @@ typedef enum {
   UFG_CUDA_ERROR = 6,    /* a CUDA runtime call failed */
   UFG_OOM = 7,           /* device allocation failed at handle creation */
   UFG_INTERNAL = 8,      /* internal consistency check failed */
-  UFG_UNSUPPORTED = 9    /* valid input outside what this build implements (e.g. N_x) */
+  UFG_UNSUPPORTED = 9    /* valid input outside what the library implements (e.g. N_x) */
 } ufg_status;
 
 typedef enum { UFG_FP64 = 0, UFG_FP32 = 1, UFG_MIXED = 2 } ufg_precision;

@@ -64,7 +64,7 @@ struct SliceCall {
   int shift = 0;               // -1: t_in = t_out - 1, +1: t_in = t_out + 1, 0: t_in = t_out
   int spc = 1;                 // time slices per CTA (cluster)
   int C = 1;                   // cluster size (1, 2 or 4; N = 32 only uses 2 or 4)
-  int nt = 256;                // threads per CTA (fixed at 256 in this build)
+  int nt = 256;                // threads per CTA (the kernels are written for 256)
   // batched mode: scalar op applied to each problem from the partials by its last CTA
   int fop = -1;                // ScalarOp, -1: none
   DevScalars* scs = nullptr;   // per-problem solver scalars

@@ -354,7 +354,7 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
 namespace ufg {
 
 // cuTensorMapEncodeTiled, resolved through the runtime at first use so that loading the library
-// does not require the driver library on machines without a GPU.
+// does not require the CUDA driver library (libcuda) on machines without a GPU.
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                    const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
