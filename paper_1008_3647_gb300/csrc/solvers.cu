@@ -64,6 +64,12 @@ struct ufg_solver {
   Counts counts;
   double inner_auto[2] = {0.0, 0.0};  // autotuned inner tolerance per method (0: not yet)
   double* x0s64 = nullptr;            // the caller's initial guess kept across tuning trials
+  // Momentum basis (Sec. 3): while `mom` is set, BiCGStab's vectors hold F x per slice, the
+  // operator is the fused momentum-space M and the WCE preconditioner needs no transforms.
+  // mb64 / mx64: right-hand side and solution in that basis (lattices with the fused kernel).
+  bool mom = false;
+  double* mb64 = nullptr;
+  double* mx64 = nullptr;
 };
 
 bool ufg::graphs_enabled() {
@@ -111,6 +117,44 @@ ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const v
                     int* nparts) {
   const ufg_lattice* L = f->lat;
   const int* done = &S->sc->done;
+  if (S->mom) {  // the fused momentum-space operator (BiCGStab only)
+    if (op == OPK_Q) {
+      set_error("normal-equation operator requested in the momentum basis");
+      return UFG_INTERNAL;
+    }
+    SliceCall c = base_call(L, FAM_INV, prec);
+    c.fam = FAM_M1W;
+    c.coef2 = base_call(L, FAM_FWD, prec).coef;
+    c.m1w_full = 1;
+    c.in = in;
+    c.pre = fld(f, 'w', prec);
+    const void* bk = prec ? (const void*)L->bk32 : (const void*)L->bk64;
+    if (op == OPK_M) {
+      c.bkpost = bk;
+      c.shift = -1;
+      S->counts.M++;
+    } else {
+      c.bkpre = bk;
+      c.shift = +1;
+      S->counts.Mdag++;
+    }
+    c.a = 1.0;
+    c.full_scale = a;
+    c.out = out;
+    c.U = U;
+    c.bU = bU;
+    c.dotP = dotP;
+    c.want_dotP = dotP != nullptr;
+    c.want_self = self;
+    c.partials = part;
+    c.done = done;
+    int launched = 0;
+    c.grid_out = &launched;
+    cudaError_t e = sdisp(L->nx, c, S->st);
+    if (nparts) *nparts = launched;
+    if (e != cudaSuccess) return cuda_fail(e, "momentum-space operator");
+    return UFG_OK;
+  }
   if (op == OPK_Q) {
     void* t1 = S->vs[prec].tmp;
     SliceCall c = base_call(L, FAM_KIN, prec);
@@ -277,6 +321,12 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
   VecSet& V = S->vs[prec];
   const void* bk = prec ? (const void*)L->bk32 : (const void*)L->bk64;
   const int* done = &S->sc->done;
+  // in the momentum basis r is already spectral and the series accumulates straight into z
+  void* const acc = S->mom ? z : V.acc;
+  if (S->mom && !slice_m1w_supported(L->nx, prec)) {
+    set_error("momentum-basis WCE without the fused kernel");
+    return UFG_INTERNAL;
+  }
   auto rec = [&](const void* in, double coef, int acc_mode, bool write_out) -> ufg_status {
     KTimer kt(std::string("recurrence acc") + std::to_string(acc_mode) + (write_out ? "+out" : "") +
                   (prec ? " f32" : " f64"),
@@ -285,20 +335,25 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
                         (double)L->S * (prec ? 4.0 : 8.0) *
                             (1 + (acc_mode == 1 ? 1 : acc_mode == 2 ? 2 : 0) + (write_out ? 1 : 0))));
     cudaError_t e = launch_recurrence(prec, in, write_out ? V.spec : nullptr, bk, L->V,
-                                      L->ntau, tr ? 1 : 0, 1.0, V.acc, coef, acc_mode, done,
+                                      L->ntau, tr ? 1 : 0, 1.0, acc, coef, acc_mode, done,
                                       S->st);
     if (e != cudaSuccess) return cuda_fail(e, "recurrence kernel");
     note_launches(1);
     if (tr) S->counts.M0invT++; else S->counts.M0inv++;
     return UFG_OK;
   };
-  SliceCall fw = base_call(L, FAM_FWD, prec);
-  fw.in = r;
-  fw.out = V.spec;
-  fw.done = done;
-  cudaError_t e = sdisp(L->nx, fw, S->st);
-  if (e != cudaSuccess) return cuda_fail(e, "forward transform");
-  UFG_TRY(rec(V.spec, cw[0], 1, d > 0));
+  cudaError_t e = cudaSuccess;
+  if (S->mom) {
+    UFG_TRY(rec(r, cw[0], 1, d > 0));
+  } else {
+    SliceCall fw = base_call(L, FAM_FWD, prec);
+    fw.in = r;
+    fw.out = V.spec;
+    fw.done = done;
+    e = sdisp(L->nx, fw, S->st);
+    if (e != cudaSuccess) return cuda_fail(e, "forward transform");
+    UFG_TRY(rec(V.spec, cw[0], 1, d > 0));
+  }
   const bool fused = slice_m1w_supported(L->nx, prec);
   for (int nn = 1; nn <= d; ++nn) {
     if (fused) {  // -A M1 (or M1^T) in momentum space in one kernel: spec -> wr
@@ -354,6 +409,7 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
     }
     UFG_TRY(rec(fused ? V.wr : V.spec, cw[nn], 2, nn < d));
   }
+  if (S->mom) return UFG_OK;
   SliceCall iv = base_call(L, FAM_INV, prec);
   iv.in = V.acc;
   iv.out = z;
@@ -466,9 +522,9 @@ ufg_status write_scalars(ufg_solver* S, double tol, int maxit, double div_limit 
 std::string key_of(const char* kind, ufg_solver* S, const ufg_field* f, int prec, int op,
                    int reps) {
   char buf[256];
-  snprintf(buf, sizeof(buf), "%s|%p|%d|%d|%d|%d|%d|%g|%g|%g|%d|%d", kind, (const void*)f, prec, op,
-           reps, S->pc_kind, S->pc.degree, S->pc.eps, S->pc.scale, S->pc.alpha, S->pc.order,
-           S->pc.euler);
+  snprintf(buf, sizeof(buf), "%s|%p|%d|%d|%d|%d|%d|%g|%g|%g|%d|%d|%d", kind, (const void*)f, prec,
+           op, reps, S->pc_kind, S->pc.degree, S->pc.eps, S->pc.scale, S->pc.alpha, S->pc.order,
+           S->pc.euler, S->mom ? 1 : 0);
   return buf;
 }
 
@@ -678,10 +734,10 @@ ufg_status status_of(int done) {
 }
 
 // Solves A x = rhs (A = M, M^T or Q) to relative tolerance tol, FP64 result in x64 (which holds
-// the initial guess if x0).  prec 0: FP64 Krylov; prec 2 (mixed): FP64 defect correction around
-// FP32 Krylov solves to inner_tol.
-ufg_status solve_system(ufg_solver* S, ufg_field* f, int op, const double* rhs, double* x64,
-                        bool x0, double tol, const ufg_params* p, SolveOut* out) {
+// the initial guess if x0), in the solver's current basis.  prec 0: FP64 Krylov; prec 2
+// (mixed): FP64 defect correction around FP32 Krylov solves to inner_tol.
+ufg_status solve_in_basis(ufg_solver* S, ufg_field* f, int op, const double* rhs, double* x64,
+                          bool x0, double tol, const ufg_params* p, SolveOut* out) {
   const long long n = f->lat->S;
   const int ce = p->check_every > 0 ? p->check_every : 8;
   auto krylov = [&](int prec, double t, bool guess, KrylovResult* kr, int maxit,
@@ -751,6 +807,44 @@ ufg_status solve_system(ufg_solver* S, ufg_field* f, int op, const double* rhs, 
     note_launches(1);
   }
   return UFG_OK;
+}
+
+// y = F x (inverse: F^T x) per slice, FP64
+ufg_status fourier64(ufg_solver* S, const ufg_field* f, const double* x, double* y, bool inverse) {
+  SliceCall c = base_call(f->lat, inverse ? FAM_INV : FAM_FWD, 0);
+  c.in = x;
+  c.out = y;
+  cudaError_t e = sdisp(f->lat->nx, c, S->st);
+  if (e != cudaSuccess) return cuda_fail(e, "basis change");
+  return UFG_OK;
+}
+
+// BiCGStab with the WCE preconditioner iterates in the momentum basis where the lattice has the
+// fused momentum-space operator in the precisions the solve uses (UFG_NO_MOMENTUM=1: never).
+bool momentum_basis(const ufg_solver* S, const ufg_field* f, int op, const ufg_params* p) {
+  static int env = -1;
+  if (env < 0) {
+    const char* e = std::getenv("UFG_NO_MOMENTUM");
+    env = (e && e[0] == '1') ? 0 : 1;
+  }
+  if (!env || S->pc_kind != UFG_PC_WCE || op == OPK_Q || S->mb64 == nullptr) return false;
+  const int nx = f->lat->nx;
+  return slice_m1w_supported(nx, 0) &&
+         (p->precision != UFG_MIXED || slice_m1w_supported(nx, 1));
+}
+
+// solve_in_basis in the momentum basis where it applies: rhs to F rhs (and x0 to F x0), the
+// solve, x = F^T x^.
+ufg_status solve_system(ufg_solver* S, ufg_field* f, int op, const double* rhs, double* x64,
+                        bool x0, double tol, const ufg_params* p, SolveOut* out) {
+  if (!momentum_basis(S, f, op, p)) return solve_in_basis(S, f, op, rhs, x64, x0, tol, p, out);
+  UFG_TRY(fourier64(S, f, rhs, S->mb64, false));
+  if (x0) UFG_TRY(fourier64(S, f, x64, S->mx64, false));
+  S->mom = true;
+  const ufg_status s = solve_in_basis(S, f, op, S->mb64, S->mx64, x0, tol, p, out);
+  S->mom = false;
+  UFG_TRY(s);
+  return fourier64(S, f, S->mx64, x64, true);
 }
 
 bool is_device_ptr(const void* p) {
@@ -903,6 +997,8 @@ ufg_status ufg_solver_create(const ufg_lattice* L, ufg_solver** out) {
   if ((s = dev_alloc(&S->x64, n)) || (s = dev_alloc(&S->b64, n)) || (s = dev_alloc(&S->r64, n)) ||
       (s = dev_alloc(&S->y64, n)) || (s = dev_alloc(&S->rc64, n)) ||
       (s = dev_alloc(&S->xs64, n)) || (s = dev_alloc(&S->xf64, n)) ||
+      (slice_m1w_supported(L->nx, 0) &&
+       ((s = dev_alloc(&S->mb64, n)) || (s = dev_alloc(&S->mx64, n)))) ||
       (s = dev_alloc(&S->parts, (size_t)NSLOT * 2 * MAX_PARTIAL_CTAS)) ||
       (s = dev_alloc(&S->sc, 1)) || (s = dev_alloc(&S->red_dev, 1)))
     return fail(s);
@@ -942,6 +1038,8 @@ void ufg_solver_destroy(ufg_solver* S) {
   dev_free(S->xs64);
   dev_free(S->xf64);
   dev_free(S->x0s64);
+  dev_free(S->mb64);
+  dev_free(S->mx64);
   dev_free(S->parts);
   dev_free(S->sc);
   dev_free(S->red_dev);

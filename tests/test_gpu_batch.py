@@ -47,9 +47,10 @@ def test_uneven_batch_converges_and_matches_solo(ufg, precision):
         xs, ss = solver.ufg_solve_bicgstab_two_step(field, pr["b"], tol=1e-10, precision=prec)
         assert ss["status"] == ufg.UFG_OK
         if precision == "fp64" and ss["restarts"] == 0 and st["restarts"] == 0:
-            # same algorithm, reduction trees differ only in tiling: counts agree; after a
+            # same algorithm (the solo solve iterates in the momentum basis where the lattice
+            # has the fused operator), rounding differs only: counts agree to 2; after a
             # near-breakdown restart the count depends on rounding and is not compared
-            assert abs(ss["iterations"] - st["iterations"]) <= 1, (
+            assert abs(ss["iterations"] - st["iterations"]) <= 2, (
                 ss["iterations_step"], st["iterations_step"])
         assert float((xs - pr["x"]).norm() / xs.norm()) < 1e-7
 
