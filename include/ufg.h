@@ -25,6 +25,13 @@
  *     asynchronous on it; solves and the force return after the result is complete.
  *   - No function throws or aborts; every failure returns a status and leaves a thread-local
  *     message for ufg_last_error().
+ *
+ * Environment switches (read once per process; for comparisons and diagnosis):
+ *   UFG_NO_TMA=1       every slice kernel takes the shared-memory-staged path instead of TMA;
+ *   UFG_NO_GRAPH=1     solver loops are launched directly instead of replayed CUDA graphs;
+ *   UFG_PDL=1          kernels are launched with programmatic dependent launch;
+ *   UFG_NO_MOMENTUM=1  WCE-preconditioned BiCGStab stays in the position basis (by default it
+ *                      iterates on F x where the lattice has the fused momentum-space operator).
  */
 #ifndef UFG_H
 #define UFG_H
@@ -80,7 +87,8 @@ typedef struct {
  *   inner_tol : MIXED only, relative reduction asked of each FP32 inner solve (0: 1e-5).  A
  *               negative value autotunes it: the first such call of a solver and method times
  *               the whole solve for 1e-3, 1e-4, 1e-5 and 1e-6 (four extra solves, from x0 = 0,
- *               the caller's x0 restored) and keeps the fastest that converges.  Batched solves
+ *               the caller's x0 restored; with x0_given that call allocates one FP64 vector of
+ *               the solver to keep x0) and keeps the fastest that converges.  Batched solves
  *               use reliable updates instead and ignore it.
  *   check_every : Krylov iterations between host convergence checks (CUDA-graph replay length). */
 typedef struct {
