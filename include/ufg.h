@@ -27,7 +27,9 @@
  *     message for ufg_last_error().
  *
  * Environment switches (read once per process; for comparisons and diagnosis):
- *   UFG_NO_TMA=1       every slice kernel takes the shared-memory-staged path instead of TMA;
+ *   UFG_NO_TMA=1       the position-space slice kernels (applies, transforms) take the
+ *                      shared-memory-staged path instead of TMA (the fused momentum-space
+ *                      kernels are TMA-only);
  *   UFG_NO_GRAPH=1     solver loops are launched directly instead of replayed CUDA graphs;
  *   UFG_PDL=1          kernels are launched with programmatic dependent launch;
  *   UFG_NO_MOMENTUM=1  WCE-preconditioned BiCGStab stays in the position basis (by default it
