@@ -36,7 +36,7 @@ def _action(ufg, lat, solver, sigma, phi):
     return S, X
 
 
-@pytest.mark.parametrize("nx,ntau,nsites", [(8, 32, 12)])
+@pytest.mark.parametrize("nx,ntau,nsites", [(8, 32, 64)])
 def test_force_matches_central_differences(ufg, nx, ntau, nsites):
     sigma, eta = field_and_source(nx, ntau, 41)
     lat = ufg.Lattice(nx, ntau)
