@@ -324,6 +324,37 @@ def run_ufg(args, rank, world, local_rank):
     step96(ufg.UFG_FP64, "fp64")
     t96_64 = timed(1, lambda: step96(ufg.UFG_FP64, "fp64"), "step_batch96_fp64")
     sites96 = sum(nx96 ** 3 * nt96 for nx96, nt96, _ in shapes96)
+    # the sequential baseline of that batch: the same 96 problems, one FP64 single-problem call
+    # each (solvers and fields made beforehand); bounded to two minutes of wall time
+    seq96 = {}
+    try:
+        solvers96, fields96 = {}, []
+        for pr in probs96:
+            key = (pr["nx"], pr["ntau"])
+            if key not in solvers96:
+                l96 = ufg.Lattice(pr["nx"], pr["ntau"], 0.05, 5.0)
+                s96 = ufg.Solver(l96)
+                s96.ufg_set_preconditioner("wce", order=2)
+                solvers96[key] = (l96, s96)
+            fields96.append(ufg.Field(solvers96[key][0], pr["sigma"]))
+        x96 = [torch.zeros_like(pr["b"]) for pr in probs96]
+        torch.cuda.synchronize()
+        t0w = time.perf_counter()
+        done96, bad96 = 0, 0
+        for pr, f96, xx in zip(probs96, fields96, x96):
+            _, st96 = solvers96[(pr["nx"], pr["ntau"])][1].ufg_solve_bicgstab_two_step(
+                f96, pr["b"], xx, tol=TOL, precision=ufg.UFG_FP64)
+            done96 += 1
+            bad96 += st96["status"] != ufg.UFG_OK
+            if time.perf_counter() - t0w > 120.0:
+                break
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0w
+        seq96 = {"value": done96 / t_seq, "unit": "solves/s", "solves": done96,
+                 "not_converged": bad96,
+                 "batched_mixed_over_sequential_fp64": (96 / t96) / (done96 / t_seq)}
+    except Exception as err:  # reported, never fatal to the bench line
+        seq96 = {"error": str(err)[:200]}
 
     solves = PER_RANK * world
     value = solves * args.steps / t_mixed
@@ -391,6 +422,7 @@ def run_ufg(args, rank, world, local_rank):
                     "true_residual_max": max(st["true_residual"] for st in box96["mixed"]),
                     "not_converged": {k: sum(st["status"] != ufg.UFG_OK for st in v)
                                       for k, v in box96.items()},
+                    "sequential_fp64": seq96,
                     "note": "96 uneven problems per rank in one ufg_solve_batch (BiCGStab + WCE2, "
                             "tol 1e-10), one timed step each precision"},
         "apply_fp32_32x512": roof["fp32"],
