@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -40,18 +41,6 @@ WORKLOAD = ("16^3x256 lattice (tau=0.05, g=5), 8 seeded problems per rank solved
             "ufg_solve_batch: two-step BiCGStab + WCE order 2, mixed FP32-inner/FP64-outer, "
             "tol 1e-10")
 ORACLE_COUNTS = os.path.join(ROOT, "tests", "golden", "oracle_counts_16x256.json")
-
-
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of kernel classes from
-# one ncu capture of the timed step's launches; a class is listed only while its kernel is
-# unchanged since the capture (the command is in the profile summary under profiles/).
-NCU_TRAFFIC = {
-    # profiles/slice_m1w_kernel_fp32_16x256x8.md: 67.17 MB read + 3.67 MB written
-    "slice m1w N16 f32": 70.84e6,
-    # profiles/slice_m1w_kernel_full_fp32_16x256x8.md: 67.17 + 4.53 MB and 100.77 + 12.68 MB
-    "slice m1wT N16 f32": 71.70e6,
-    "slice m1wT+full+dot N16 f32": 113.45e6,
-}
 
 
 def peaks():
@@ -116,36 +105,116 @@ class ClockSampler:
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
 
 
-def run_reference(args, rank, world):
-    """The FP64 CPU oracle on the host cores: each step times a bounded sample (one iteration of
-    the oracle's BiCGStab + WCE2 on the first system M^T y = b of a 16^3 x 256 problem) and scales
-    it to 8 full solves with the oracle's own iteration count for that problem."""
-    if rank != 0:
-        return
+def host_info():
+    """Host CPU of this box: core count and model name."""
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count() or 1, "cpu_model": model}
+
+
+def _oracle_iteration_sample(n_iter):
+    """Worker: seconds per BiCGStab + WCE2 iteration of the FP64 oracle on the first system
+    (M^T y = b) of the 16^3 x 256 seed-0 problem, over n_iter iterations."""
     import oracle as O
     from paper_1008_3647_gb300.inputs import field_and_source
+    lat = O.Lattice(NX, NTAU, 0.05, 5.0)
+    sigma, b = field_and_source(NX, NTAU, 0)
+    t0 = time.perf_counter()
+    O.bicgstab(lambda u: O.apply_Mdag(lat, sigma, u), b, 1e-30, n_iter,
+               lambda r: O.wce_apply_T(lat, sigma, r, 2))
+    return (time.perf_counter() - t0) / n_iter
+
+
+def oracle_rate(workers, n_iter):
+    """Oracle iterations per second on `workers` single-threaded processes running the sample at
+    the same time (spawned, so that no forked process inherits a CUDA context)."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(workers) as pool:
+        per_iter = pool.map(_oracle_iteration_sample, [n_iter] * workers)
+    wall = time.perf_counter() - t0
+    return workers / statistics.mean(per_iter), per_iter, wall
+
+
+def oracle_complete_c1():
+    """One complete oracle solve of the 4^3 x 16 problem (plain CG on M^T M, FP64, tol 1e-10)."""
+    import oracle as O
+    from paper_1008_3647_gb300.inputs import field_and_source
+    lat = O.Lattice(4, 16, 0.05, 5.0)
+    sigma, b = field_and_source(4, 16, 0)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        _, info = O.solve_cg_normal(lat, sigma, b, 1e-10)
+        reps += 1
+        if time.perf_counter() - t0 > 2.0:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "iterations": info["iterations"],
+            "note": "complete oracle solves (not extrapolated) of the 4^3x16 plain-CG problem"}
+
+
+def cpu_baseline_sample(n_iter=2):
+    """Bounded sample of the FP64 CPU oracle on the headline problem: n_iter iterations of its
+    BiCGStab + WCE2 per process, timed on one process and on one process per host core at once,
+    and extrapolated to whole solves with the oracle's own iteration count for that problem."""
+    iters, src = oracle_iterations()
+    info = host_info()
+    r1, t1, wall1 = oracle_rate(1, n_iter)
+    rn, tn, walln = oracle_rate(info["nproc"], n_iter)
+    sample = ("%d BiCGStab+WCE2 iterations of the FP64 oracle (numpy FFT, one thread per process) "
+              "on the 16^3x256 seed-0 problem per process; solves/s extrapolated with %d iterations "
+              "per solve (%s)" % (n_iter, iters, src))
+    return {"value": rn / iters, "unit": "solves/s", "cores": info["nproc"], "kind": "oracle",
+            "sample": sample, "extrapolated": True, "cpu_model": info["cpu_model"],
+            "nproc": info["nproc"],
+            "single_thread": {"value": r1 / iters, "unit": "solves/s", "cores": 1,
+                              "seconds_per_iteration": t1[0]},
+            "all_cores": {"value": rn / iters, "unit": "solves/s", "cores": info["nproc"],
+                          "seconds_per_iteration_mean": statistics.mean(tn),
+                          "sample_wall_s": walln},
+            "complete_solve_4x16_cg": oracle_complete_c1()}
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle on the host cores: each step times a bounded sample (one iteration of
+    the oracle's BiCGStab + WCE2 on the first system M^T y = b of the 16^3 x 256 problem, on one
+    single-threaded process per host core at once) and extrapolates it to solves/s with the
+    oracle's own iteration count for that problem."""
+    if rank != 0:
+        return
+    info = host_info()
     line = {"metric": METRIC, "unit": "solves/s", "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nx": NX, "ntau": NTAU, "solves_per_step": PER_RANK}}
-    lat = O.Lattice(NX, NTAU, 0.05, 5.0)
-    sigma, b = field_and_source(NX, NTAU, 0)
     iters, src = oracle_iterations()
-    pc = lambda r: O.wce_apply_T(lat, sigma, r, 2)  # noqa: E731
-    aop = lambda u: O.apply_Mdag(lat, sigma, u)  # noqa: E731
-    times = []
+    rates, walls = [], []
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        O.bicgstab(aop, b, 1e-30, 1, pc)
-        dt = time.perf_counter() - t0
+        r, _, wall = oracle_rate(info["nproc"], 1)
         if i >= args.warmup:
-            times.append(dt)
-    t_iter = statistics.mean(times)
-    sps = 1.0 / (t_iter * iters)
-    line.update({"value": sps, "ms_per_step": 1e3 * t_iter * iters * PER_RANK,
-                 "cpu_baseline": {"value": sps, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                  "sample": "1 BiCGStab+WCE2 iteration of the FP64 oracle per step "
-                                            "on the 16^3x256 seed-0 problem, scaled by %d "
+            rates.append(r)
+            walls.append(wall)
+    sps = statistics.mean(rates) / iters
+    line.update({"value": sps, "ms_per_step": 1e3 * statistics.mean(walls),
+                 "extrapolated": {"ms_per_step_of_full_solves": 1e3 * PER_RANK / sps,
+                                  "iterations_timed_per_process_and_step": 1,
+                                  "iterations_per_solve": iters},
+                 "cpu_baseline": {"value": sps, "unit": "solves/s", "cores": info["nproc"],
+                                  "kind": "oracle", "cpu_model": info["cpu_model"],
+                                  "extrapolated": True,
+                                  "sample": "1 BiCGStab+WCE2 iteration of the FP64 oracle per "
+                                            "process and step, one single-threaded process per "
+                                            "host core, 16^3x256 seed-0 problem; scaled by %d "
                                             "iterations per solve (%s)" % (iters, src)},
                  "e2e": {"value": sps, "unit": "solves/s", "h2d_bytes_per_step": 0,
                          "d2h_bytes_per_step": 0}})
@@ -158,22 +227,6 @@ def oracle_iterations():
             return int(json.load(f)["runs"]["bicg_wce2"]["iterations"]), "oracle count, stored"
     except Exception:
         return 80, "assumed 80 iterations (oracle count file missing)"
-
-
-def cpu_baseline_sample():
-    """Bounded oracle sample for the ufg arm's cpu_baseline (same definition as the reference)."""
-    import oracle as O
-    from paper_1008_3647_gb300.inputs import field_and_source
-    lat = O.Lattice(NX, NTAU, 0.05, 5.0)
-    sigma, b = field_and_source(NX, NTAU, 0)
-    iters, src = oracle_iterations()
-    t0 = time.perf_counter()
-    O.bicgstab(lambda u: O.apply_Mdag(lat, sigma, u), b, 1e-30, 2,
-               lambda r: O.wce_apply_T(lat, sigma, r, 2))
-    t_iter = (time.perf_counter() - t0) / 2
-    return {"value": 1.0 / (t_iter * iters), "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": "2 BiCGStab+WCE2 iterations of the FP64 oracle on the 16^3x256 seed-0 problem, "
-                      "scaled by %d iterations per solve (%s); numpy FFT, one thread" % (iters, src)}
 
 
 def seeds_for_rank(rank, per_rank=PER_RANK):
@@ -313,11 +366,8 @@ def run_ufg(args, rank, world, local_rank):
     box96 = {}
 
     def step96(precision, key):
-        try:
-            box96[key] = ufg.ufg_solve_batch(probs96, "wce", {"order": 2}, tol=TOL,
-                                             precision=precision, check_every=8)
-        except ufg.UfgError as err:  # a problem that broke down: reported, not fatal here
-            box96[key] = [{"status": err.status, "true_residual": float("nan")}]
+        box96[key] = ufg.ufg_solve_batch(probs96, "wce", {"order": 2}, tol=TOL,
+                                         precision=precision, check_every=8)
 
     step96(ufg.UFG_MIXED, "mixed")
     t96 = timed(1, lambda: step96(ufg.UFG_MIXED, "mixed"), "step_batch96")
@@ -372,7 +422,7 @@ def run_ufg(args, rank, world, local_rank):
     top = kstats[0]
     roofline = {"kernel": top["name"] + " (dominant kernel of the step)", "bound": "hbm",
                 "achieved": top["gbs"], "peak": hbm, "unit": "GB/s", "frac": top["gbs"] / hbm,
-                "traffic": NCU_TRAFFIC.get(top["name"]), "peak_source": peak_src,
+                "traffic": None, "peak_source": peak_src,
                 "us_per_launch": top["us_per_launch"],
                 "algorithmic_bytes_per_launch": top["bytes"] / max(1, top["launches"]),
                 "share_of_step": top["total_ms"] / ktotal}
@@ -380,8 +430,13 @@ def run_ufg(args, rank, world, local_rank):
                 "us_per_launch": round(k["us_per_launch"], 2), "gbs": round(k["gbs"], 1),
                 "frac_hbm": round(k["gbs"] / hbm, 3), "share": round(k["total_ms"] / ktotal, 4)}
                for k in kstats[:12]]
-    # the fused M apply alone on 32^3 x 512 (16.8M sites), FP32 and FP64
+    # the fused M and M^T applies alone on 32^3 x 512 (16.8M sites), FP32 and FP64
     roof = apply_roofline(ufg, torch, dev, stream, hbm, peak_src)
+    # config 1: plain FP64 CG on 4^3 x 16, one call per solve (latency-bound)
+    c1 = c1_solves(ufg, torch, dev)
+    # config 2 and the coupling sweep (iteration and MV counts; not timed work)
+    c2 = solve_count_tables(ufg, torch, dev) if not args.no_tables else None
+    sweep = coupling_sweep(ufg, torch, dev) if not args.no_tables else None
     if rank != 0:
         return
     sm = stats_box["mixed"]
@@ -426,7 +481,11 @@ def run_ufg(args, rank, world, local_rank):
                     "note": "96 uneven problems per rank in one ufg_solve_batch (BiCGStab + WCE2, "
                             "tol 1e-10), one timed step each precision"},
         "apply_fp32_32x512": roof["fp32"],
+        "apply_fp32_32x512_mdag": roof["fp32_mdag"],
         "apply_fp64_32x512": roof["fp64"],
+        "c1_4x16_fp64_cg": c1,
+        "c2_8x64_counts": c2,
+        "coupling_sweep": sweep,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
@@ -434,43 +493,194 @@ def run_ufg(args, rank, world, local_rank):
 
 
 def apply_roofline(ufg, torch, dev, stream, hbm, peak_src):
-    """Times the fused M apply on 32^3 x 512 (16.8M sites; x, w and y exceed L2 together) with
-    CUDA events on the launching stream; algorithmic bytes = read x + read w + write y."""
+    """Times the fused M and M^T applies on 32^3 x 512 (16.8M sites; x, w and y exceed L2
+    together) with CUDA events on the launching stream; algorithmic bytes = read x + read w +
+    write y.  FP64 is bound by the FP64 pipe on this part: its fraction is taken against the FMA
+    throughput measured here by the library (ufg_measure_fma_rate)."""
     from paper_1008_3647_gb300.inputs import field_and_source
     nx, nt = 32, 512
     lat = ufg.Lattice(nx, nt)
     sg, xx = field_and_source(nx, nt, 123)
     field = ufg.Field(lat, torch.from_numpy(sg).to(dev))
     out = {}
-    for name, dt, reps in (("fp32", torch.float32, 20), ("fp64", torch.float64, 5)):
+    for name, op, dt, reps in (("fp32", "ufg_apply_M", torch.float32, 20),
+                               ("fp32_mdag", "ufg_apply_Mdag", torch.float32, 20),
+                               ("fp64", "ufg_apply_M", torch.float64, 5)):
+        fn = getattr(ufg, op)
         x = torch.from_numpy(xx).to(dev, dt)
         y = torch.empty_like(x)
         for _ in range(3):
-            ufg.ufg_apply_M(field, x, y)
+            fn(field, x, y)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
-            ufg.ufg_apply_M(field, x, y)
+            fn(field, x, y)
         e1.record(stream)
         torch.cuda.synchronize()
+        lat.ufg_lattice_check()
         t = e0.elapsed_time(e1) / 1e3 / reps
         bytes_ = 3 * x.element_size() * x.numel()
         ach = bytes_ / t / 1e9
-        out[name] = {"kernel": "slice_kernel KIN family (fused M apply), %s, 32^3x512" % name,
+        out[name] = {"kernel": "fused %s apply (slice kernel, KIN family), %s, 32^3x512"
+                               % ("M^T" if op.endswith("Mdag") else "M", dt),
                      "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                      "frac": ach / hbm, "traffic": None, "peak_source": peak_src,
-                     "us_per_launch": t * 1e6, "algorithmic_bytes": bytes_}
-    # FP64 is bound by the FP64 pipe on this part: flops of the two-level even/odd line
-    # operators (blocks (Q+1)^2, Q^2, Q^2, (Q-1)^2 with Q = N/4, one multiply-add each, plus the
-    # two fold levels on input and output, ~4 N adds per line), three passes, and the epilogue
+                     "us_per_launch": t * 1e6, "algorithmic_bytes": bytes_,
+                     "applies_per_s": 1.0 / t}
+    # FP64: flops of the two-level even/odd line operators (blocks (Q+1)^2, Q^2, Q^2, (Q-1)^2
+    # with Q = N/4, one multiply-add each, plus the two fold levels on input and output, ~4 N adds
+    # per line), three passes, and the epilogue
     Q = nx // 4
     line_flops = 2 * ((Q + 1) ** 2 + 2 * Q ** 2 + (Q - 1) ** 2) + 4 * nx
     flops_site = 3 * line_flops / nx + 3
     f64 = out["fp64"]
-    f64["flops_per_site"] = flops_site
-    f64["achieved_tflops"] = flops_site * lat.ntau * nx ** 3 / (f64["us_per_launch"] * 1e-6) / 1e12
+    peak64 = ufg.ufg_measure_fma_rate(ufg.UFG_FP64)
+    ach64 = flops_site * lat.ntau * nx ** 3 / (f64["us_per_launch"] * 1e-6) / 1e12
+    f64["alu"] = {"bound": "alu (FP64 pipe)", "achieved": ach64, "peak": peak64,
+                  "unit": "TFLOP/s", "frac": ach64 / peak64, "flops_per_site": flops_site,
+                  "peak_source": "measured in this run (ufg_measure_fma_rate, FP64 FMA chains)"}
     return out
+
+
+def c1_solves(ufg, torch, dev):
+    """Config 1: plain FP64 CG on M^T M, 4^3 x 16, seed 0, tol 1e-10: solves/s of one
+    ufg_solve_cg_normal call each, device-resident b and x (wall clock over 50 calls)."""
+    from paper_1008_3647_gb300.inputs import field_and_source
+    lat = ufg.Lattice(4, 16)
+    sg, b = field_and_source(4, 16, 0)
+    field = ufg.Field(lat, torch.from_numpy(sg).to(dev))
+    solver = ufg.Solver(lat)
+    bd = torch.from_numpy(b).to(dev)
+    x = torch.zeros_like(bd)
+    for _ in range(3):
+        _, st = solver.ufg_solve_cg_normal(field, bd, x, tol=1e-10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n = 50
+    for _ in range(n):
+        _, st = solver.ufg_solve_cg_normal(field, bd, x, tol=1e-10)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / n
+    return {"value": 1.0 / dt, "unit": "solves/s", "iterations": st["iterations"],
+            "true_residual": st["true_residual"], "status": st["status_name"]}
+
+
+def solve_count_tables(ufg, torch, dev):
+    """Config 2 (8^3 x 64, seeds 0-9, FP64, tol 1e-10): iterations and the paper's MV count of
+    every method on the GPU, beside the oracle's stored counts for the same inputs and the
+    paper's Table 1 / Table 2 row for 8^3 x 50 (context: other lattice, tolerance and RNG)."""
+    from paper_1008_3647_gb300.inputs import field_and_source
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_counts_8x64.json")))
+    paper = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "paper_tables_1_2.txt")):
+        f = line.split()
+        if f and f[0] in ("T1", "T2") and f[1:3] == ["8", "50"]:
+            paper[f[0]] = dict(zip(("cheb8", "cheb16", "cheb32", "sca", "wce0", "wce1", "wce2"),
+                                   f[3:]))
+    methods = {
+        "cg_none": ("cg", "none", {}, None), "cg_cheb8": ("cg", "cheb", {"degree": 8}, "cheb8"),
+        "cg_cheb16": ("cg", "cheb", {"degree": 16}, "cheb16"),
+        "cg_cheb32": ("cg", "cheb", {"degree": 32}, "cheb32"),
+        "cg_wce0": ("cg", "wce", {"order": 0}, None),
+        "cg_wce2": ("cg", "wce", {"order": 2}, None),
+        "cg_wce2_euler23": ("cg", "wce", {"order": 2, "euler": "euler23"}, None),
+        "cg_scacheb8": ("cg", "sca_cheb", {"alpha": 2.0, "degree": 8}, None),
+        "cg_scacheb16": ("cg", "sca_cheb", {"alpha": 2.0, "degree": 16}, None),
+        "cg_sca1": ("cg", "sca", {"alpha": 1.0}, None),
+        "cg_sca1.5": ("cg", "sca", {"alpha": 1.5}, None),
+        "cg_sca2": ("cg", "sca", {"alpha": 2.0}, "sca"), "cg_sca3": ("cg", "sca", {"alpha": 3.0}, None),
+        "cg_sca4": ("cg", "sca", {"alpha": 4.0}, None),
+        "bicg_none": ("bicg", "none", {}, None),
+        "bicg_wce0": ("bicg", "wce", {"order": 0}, "wce0"),
+        "bicg_wce1": ("bicg", "wce", {"order": 1}, "wce1"),
+        "bicg_wce2": ("bicg", "wce", {"order": 2}, "wce2"),
+        "bicg_wce4": ("bicg", "wce", {"order": 4}, None),
+        "bicg_wce2_euler": ("bicg", "wce", {"order": 2, "euler": True}, None),
+        "bicg_wce4_euler": ("bicg", "wce", {"order": 4, "euler": True}, None),
+        "bicg_wce2_euler23": ("bicg", "wce", {"order": 2, "euler": "euler23"}, None),
+        "bicg_wce4_euler23": ("bicg", "wce", {"order": 4, "euler": "euler23"}, None),
+        "bicg_wce2_vanw": ("bicg", "wce", {"order": 2, "euler": "vanw"}, None),
+        "bicg_wce4_vanw": ("bicg", "wce", {"order": 4, "euler": "vanw"}, None),
+    }
+    nx, nt = gold["nx"], gold["ntau"]
+    lat = ufg.Lattice(nx, nt)
+    probs = [field_and_source(nx, nt, sd) for sd in range(10)]
+    fields = [ufg.Field(lat, torch.from_numpy(sg).to(dev)) for sg, _ in probs]
+    bs = [torch.from_numpy(b).to(dev) for _, b in probs]
+    out = {}
+    t0 = time.perf_counter()
+    for name, (kind, pc, kw, col) in methods.items():
+        solver = ufg.Solver(lat)
+        solver.ufg_set_preconditioner(pc, **kw)
+        fn = solver.ufg_solve_cg_normal if kind == "cg" else solver.ufg_solve_bicgstab_two_step
+        its, mvs, conv, oits = [], [], 0, []
+        for sd in range(10):
+            _, st = fn(fields[sd], bs[sd], tol=1e-10, maxit=10000)
+            its.append(st["iterations"])
+            mvs.append(st["mv_paper"])
+            conv += st["status"] == ufg.UFG_OK
+            ref = gold["runs"].get("%s/%d" % (name, sd))
+            if ref is not None:
+                oits.append(ref["iterations"])
+        row = {"gpu_iterations_mean": statistics.mean(its), "gpu_mv_mean": statistics.mean(mvs),
+               "gpu_converged": conv}
+        if len(oits) == 10:
+            row["oracle_iterations_mean"] = statistics.mean(oits)
+        if col is not None and "T1" in paper:
+            row["paper_8x50_iterations"] = paper["T1"][col]
+            row["paper_8x50_mv"] = paper["T2"][col]
+        out[name] = row
+    return {"workload": "8^3x64, tau=0.05, g=5, seeds 0-9, FP64, tol 1e-10, maxit 10000 per "
+                        "Krylov solve", "methods": out, "seconds": time.perf_counter() - t0,
+            "note": "paper columns: Tables 1/2 at 8^3x50, tol 1e-12, their RNG (context only)"}
+
+
+def coupling_sweep(ufg, torch, dev):
+    """Table 3's shape (Sec. 5): BiCGStab MV operations with WCE2 and WCE4 (plain, Euler and the
+    special van Wijngaarden transformation) on 10^3 x {50, 100, 200} for g in {2.5, 5, 7.5}, ten
+    seeded configurations each, solved as one batched FP64 call per setting to a 1e-12 residual
+    reduction (the paper's); and g = 10 against the paper's statement that those solves
+    typically fail within 15,000 MV (833 WCE2 iterations per step)."""
+    from paper_1008_3647_gb300.inputs import field_and_source
+    table3 = {(2.5, 50): (630, 600), (2.5, 100): (702, 690), (2.5, 200): (864, 780),
+              (5.0, 50): (1206, 1320), (5.0, 100): (1584, 1530), (5.0, 200): (2178, 2190),
+              (7.5, 50): (2358, 4110), (7.5, 100): (3816, 9330), (7.5, 200): (6444, 12720)}
+    nx = 10
+    t0 = time.perf_counter()
+    rows = []
+    data = {}
+    for nt in (50, 100, 200):
+        data[nt] = [field_and_source(nx, nt, 1000 + sd) for sd in range(10)]
+    for (g, nt), (p2, p4) in table3.items():
+        row = {"g": g, "lattice": "10^3x%d" % nt, "paper_mv_wce2": p2, "paper_mv_wce4": p4}
+        for order in (2, 4):
+            for accel in ("none", "euler", "euler23", "vanw"):
+                probs = [{"nx": nx, "ntau": nt, "tau": 0.05, "g": g,
+                          "sigma": torch.from_numpy(sg).to(dev), "b": torch.from_numpy(b).to(dev),
+                          "x": torch.zeros(nt, nx, nx, nx, dtype=torch.float64, device=dev)}
+                         for sg, b in data[nt]]
+                # 2,000 iterations per step: 36,000 MV or more, far beyond any entry of Table 3
+                stats = ufg.ufg_solve_batch(probs, "wce", {"order": order, "euler": accel},
+                                            tol=1e-12, precision=ufg.UFG_FP64, maxit=2000)
+                ok = [st for st in stats if st["status"] == ufg.UFG_OK]
+                key = "wce%d" % order + ("" if accel == "none" else "_" + accel)
+                row[key + "_mv_mean"] = statistics.mean(st["mv_paper"] for st in ok) if ok else None
+                row[key + "_converged"] = len(ok)
+        rows.append(row)
+    # g = 10: how many of ten configurations converge within the paper's 15,000 MV
+    probs = [{"nx": nx, "ntau": 50, "tau": 0.05, "g": 10.0, "sigma": torch.from_numpy(sg).to(dev),
+              "b": torch.from_numpy(b).to(dev),
+              "x": torch.zeros(50, nx, nx, nx, dtype=torch.float64, device=dev)}
+             for sg, b in data[50]]
+    st10 = ufg.ufg_solve_batch(probs, "wce", {"order": 2}, tol=1e-12, precision=ufg.UFG_FP64,
+                               maxit=833)
+    conv10 = sum(st["status"] == ufg.UFG_OK and st["mv_paper"] <= 15000 for st in st10)
+    return {"rows": rows, "g10_10x50_wce2_converged_within_15000_mv": conv10,
+            "seconds": time.perf_counter() - t0,
+            "note": "seeds 1000-1009 per lattice, FP64 batched two-step BiCGStab, tol 1e-12; MV "
+                    "= iterations x 2(d+1)(1+2 beta), beta = 1; paper: Table 3, averages of 10 "
+                    "configurations (context, other RNG)"}
 
 
 def main():
@@ -480,6 +690,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ufg", choices=["ufg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tables", action="store_true",
+                    help="skip the iteration-count tables (config 2, coupling sweep)")
     ap.add_argument("--only-apply", action="store_true",
                     help="time only the 32^3x512 M apply (the case ncu profiles)")
     args = ap.parse_args()

@@ -57,7 +57,15 @@ typedef enum {
 
 typedef enum { UFG_FP64 = 0, UFG_FP32 = 1, UFG_MIXED = 2 } ufg_precision;
 
-typedef enum { UFG_PC_NONE = 0, UFG_PC_CHEB = 1, UFG_PC_SCA = 2, UFG_PC_WCE = 3 } ufg_pc_kind;
+/* UFG_PC_SCA_CHEB: the strong-coupling factorisation with the Chebyshev polynomial as a secondary
+ * filter (end of Sec. 4): P = P(G/s)/s (L^T D L)^{-1} with G = (L^T D L)^{-1} Q, for CG. */
+typedef enum {
+  UFG_PC_NONE = 0,
+  UFG_PC_CHEB = 1,
+  UFG_PC_SCA = 2,
+  UFG_PC_WCE = 3,
+  UFG_PC_SCA_CHEB = 4
+} ufg_pc_kind;
 
 typedef struct ufg_lattice ufg_lattice;
 typedef struct ufg_field ufg_field;
@@ -65,12 +73,32 @@ typedef struct ufg_solver ufg_solver;
 
 /* Preconditioner parameters (fields unused by a kind are ignored).
  *   degree : Chebyshev degree d = 2n of P(z) ~ 1/z (Sec. 2, Eq. ChebInv); even, 2..64.
- *   eps    : lower edge of [eps, 1] after normalisation; <= 0 selects (2 - 2 cos(pi/N_tau)) / scale.
- *   scale  : spectrum normalisation s of M^T M (z = Q / s); <= 0 selects (2 + A)^2, a rigorous
- *            bound on ||M||^2 since ||exp(-tau K)|| = 1 and |1 + A sin sigma| <= 1 + A.
+ *   eps    : lower edge of [eps, 1] after normalisation; <= 0 selects (2 - 2 cos(pi/N_tau)) / scale
+ *            (UFG_PC_CHEB) or 1e-3 (UFG_PC_SCA_CHEB).
+ *   scale  : spectrum normalisation s of the operator the polynomial acts on (z = Q / s, or G / s
+ *            for UFG_PC_SCA_CHEB); <= 0 selects (2 + A)^2 for Q, a rigorous bound on ||M||^2 since
+ *            ||exp(-tau K)|| = 1 and |1 + A sin sigma| <= 1 + A, and for G 1.1 times the estimate
+ *            of 30 power steps from w = 1 + A sin sigma (made once per field and alpha).
  *   alpha  : strong-coupling parameter alpha of D_t (Sec. 4); must be > 0.
  *   order  : weak-coupling expansion order d (Sec. 3, Eq. WCE); 0..16.
- *   euler  : nonzero selects Euler acceleration with p = 1/2 (Sec. 3.1, Eq. Euler). */
+ *   euler  : acceleration of the order-d series over its partial sums S_{0,k} (Sec. 3.1), a
+ *            ufg_accel value: UFG_ACCEL_NONE the plain sum S_{0,d}; UFG_ACCEL_EULER the Euler
+ *            recursion S_{j+1,k} = p S_{j,k} + (1-p) S_{j,k+1} (Eq. Euler) down to S_{d,0};
+ *            UFG_ACCEL_EULER23 its entry S_{j,d-j} with j the integer nearest 2d/3 (the paper's
+ *            S_{2kmax/3,kmax/3}); UFG_ACCEL_VANW the special van Wijngaarden transformation
+ *            (lambda_k = s^k/k!, phi(t) = s exp(-s t)) truncated at order d.  Every mode only
+ *            changes the weights of the d + 1 series terms: the cost per application is that of
+ *            the plain series.
+ *   euler_p: p of the Euler recursion, in (0, 1); 0 selects 1/2, the paper's choice.
+ *   vw_s   : the free parameter s > 0 of the special van Wijngaarden transformation; 0 selects 1.
+ * All fields zero except those a kind uses is a valid set of defaults for euler_p and vw_s. */
+typedef enum {
+  UFG_ACCEL_NONE = 0,
+  UFG_ACCEL_EULER = 1,
+  UFG_ACCEL_EULER23 = 2,
+  UFG_ACCEL_VANW = 3
+} ufg_accel;
+
 typedef struct {
   int degree;
   double eps;
@@ -78,6 +106,8 @@ typedef struct {
   double alpha;
   int order;
   int euler;
+  double euler_p;
+  double vw_s;
 } ufg_pc_params;
 
 /* Solve parameters.
@@ -156,6 +186,12 @@ typedef struct {
   double bytes;        /* sum of the algorithmic bytes */
 } ufg_kernel_stat;
 ufg_status ufg_profile_enable(int on);
+/* Measured multiply-add throughput of the current GPU in precision UFG_FP64 or UFG_FP32, in
+ * TFLOP/s (2 flops per FMA): a register-resident kernel of independent FMA chains filling every
+ * SM, timed with CUDA events on stream over five launches after one warm-up.  The roofline
+ * denominator of the applies that the arithmetic pipe rather than HBM bounds (FP64 on this part).
+ * Allocates and frees a small output buffer; synchronises stream. */
+ufg_status ufg_measure_fma_rate(int precision, void* stream, double* tflops);
 /* Synchronises the device and aggregates the records by name into out[0 .. min(max, n) - 1],
  * sorted by total time (largest first); *n receives the number of distinct names.  out may be
  * NULL with max = 0 to query n. */
@@ -172,6 +208,20 @@ ufg_status ufg_lattice_create(int nx, int ntau, double tau, double g, int disper
 void ufg_lattice_destroy(ufg_lattice* lat);
 /* Coupling A of the lattice (Sec. 1). */
 double ufg_lattice_coupling(const ufg_lattice* lat);
+/* Device-side failure check for asynchronous applies.  The TMA-staged kernels wait for their
+ * shared-memory copies with a bounded number of polling rounds (under a second); a wait that runs
+ * out raises a flag of the lattice and the kernel finishes on incomplete data.  Solves, the force
+ * and batched solves read the flags themselves and return UFG_TIMEOUT; after applies, call this:
+ * it synchronises stream, reads and clears the flag of lat, and returns UFG_TIMEOUT (with a
+ * message) if any kernel launched on the lattice since the last check ran out of its wait, else
+ * UFG_OK.  The paper has no counterpart (failure reporting of this library). */
+ufg_status ufg_lattice_check(const ufg_lattice* lat, void* stream);
+/* Test hook for the failure path above: the next `launches` TMA-staged slice-kernel launches (in
+ * any lattice of the process) each run one extra bounded wait on a barrier whose expected bytes
+ * never arrive, so that wait runs out after a few hundred polling rounds and raises the flag
+ * exactly as a real timeout would.  The kernel's own copies complete as usual, nothing faults or
+ * hangs, and the results stay correct; only the reported status changes.  0 cancels. */
+void ufg_test_expire_waits(int launches);
 /* Autotuner: times the fused M apply for every compiled launch shape (CTAs per cluster C, time
  * slices per CTA) on this lattice, in FP64 and FP32, and keeps the fastest for all later applies
  * and solves built on the lattice.  Results are cached per (GPU name, N_x, N_tau, precision) in
@@ -229,16 +279,19 @@ ufg_status ufg_solver_create(const ufg_lattice* lat, ufg_solver** out);
 void ufg_solver_destroy(ufg_solver* s);
 
 /* Selects the preconditioner of the following solves.  UFG_PC_CHEB and UFG_PC_SCA precondition
- * Q = M^T M (CG); UFG_PC_WCE preconditions M and M^T separately (two-step BiCGStab). */
+ * Q = M^T M (CG); UFG_PC_WCE preconditions M and M^T separately (two-step BiCGStab) or, for CG,
+ * Q from both sides. */
 ufg_status ufg_set_preconditioner(ufg_solver* s, int kind, const ufg_pc_params* p);
 
 /* z = P r with the current preconditioner: Chebyshev P(Q/s)/s ~ Q^{-1}; SCA (L^T D L)^{-1};
- * WCE P_d ~ M^{-1} (transpose != 0: P_d^T ~ M^{-T}).  For tests and for callers composing their
- * own solvers. */
+ * WCE P_d ~ M^{-1} (transpose = 1: P_d^T ~ M^{-T}; transpose = 2: P_d P_d^T ~ Q^{-1}, the SPD form
+ * CG on the normal equations uses: M0^{-T} on the left and M0^{-1} on the right, end of Sec. 5).
+ * For tests and for callers composing their own solvers. */
 ufg_status ufg_apply_preconditioner(ufg_solver* s, ufg_field* f, const void* r, void* z,
                                     int transpose, int precision, void* stream);
 
-/* Solves M^T M x = b by preconditioned CG (Eq. 1 with the left/SPD preconditioning of Eq. 3).
+/* Solves M^T M x = b by preconditioned CG (Eq. 1 with the left/SPD preconditioning of Eq. 3):
+ * Chebyshev, SCA, or the weak-coupling series applied from both sides (P_d P_d^T).
  * b, x: FP64, device or host pointers (host buffers are staged through the workspace). */
 ufg_status ufg_solve_cg_normal(ufg_solver* s, ufg_field* f, const double* b, double* x,
                                const ufg_params* p, ufg_stats* stats, void* stream);
@@ -263,6 +316,32 @@ ufg_status ufg_hmc_force(ufg_solver* s, ufg_field* f, const double* phi, double*
 ufg_status ufg_force_from_solution(ufg_solver* s, ufg_field* f, const double* X, double* dS,
                                    double scale, void* stream);
 
+/* Statistics of one HMC trajectory. */
+typedef struct {
+  int status;          /* UFG_OK, or the status of the force solve that failed */
+  int accepted;        /* 1: the proposal was accepted (the field holds it), 0: rejected */
+  int md_steps;        /* leapfrog steps done */
+  int force_solves;    /* solves of M^T M X = phi (n_steps + 1) */
+  long long iterations;  /* Krylov iterations summed over those solves */
+  double H_old, H_new, dH;         /* MD Hamiltonian sum pi^2/2 + S_p before and after */
+  double action_old, action_new;   /* S_p = phi^T (M^T M)^{-1} phi before and after */
+  double seconds;
+} ufg_hmc_stats;
+
+/* One trajectory of the phi-algorithm of Sec. 1: pseudofermion heat bath phi = M^T[sigma] eta,
+ * molecular dynamics of d sigma/dt = pi, d pi/dt = -dS_p/dsigma under H = sum pi^2/2 + S_p with
+ * n_steps leapfrog steps of size dt (a half step in pi, then full steps, a final half step:
+ * reversible and area-preserving), and a Metropolis accept/reject of exp(-dH) against u.  The
+ * random numbers are the caller's: eta and pi0 (device FP64 [N_tau][N_x]^3, each N(0,1)) and
+ * u in [0, 1).  Every force is ufg_hmc_force with the solver's preconditioner and p.  The field
+ * holds the new sigma on acceptance and the old one otherwise; sigma_out and pi_out (nullable,
+ * device or host FP64) receive the field's sigma and the final momenta.  The first call allocates
+ * five FP64 vectors of the solver (kept until ufg_solver_destroy).  Synchronises stream. */
+ufg_status ufg_hmc_trajectory(ufg_solver* s, ufg_field* f, const double* eta, const double* pi0,
+                              double u, int n_steps, double dt, const ufg_params* p,
+                              double* sigma_out, double* pi_out, ufg_hmc_stats* stats,
+                              void* stream);
+
 /* n independent problems of mixed lattice sizes, each solved by two-step BiCGStab with the
  * preconditioner settings pc_kind (UFG_PC_NONE or UFG_PC_WCE)/pc, all problems advanced together
  * by batched kernels (one launch per phase per lattice extent for the whole batch) with the
@@ -280,8 +359,8 @@ void ufg_batch_cache_clear(void);
 
 /* y = M^T M x in FP64 without allocating any device memory.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc where they need the operator (code
- * inside a CUDA-graph capture, under a memory pool that forbids extra allocations, or in a plugin
- * that must not grow its device footprint).  sigma, x, y: device FP64 [N_tau][N_x]^3, 16-byte
+ * under a memory pool or arena that forbids extra allocations, or a plugin that must not grow the
+ * process's device footprint after start-up).  sigma, x, y: device FP64 [N_tau][N_x]^3, 16-byte
  * aligned, x and y not overlapping; the lattice (N_x, N_tau, tau, g, dispersion) is as in
  * ufg_lattice_create.  The two intermediates (1 + A sin sigma and M x) live in a file-scope static
  * device array of 2 x 2^20 doubles (16 MiB) that every GPU loading the library holds until exit,
@@ -290,7 +369,8 @@ void ufg_batch_cache_clear(void);
  * current; make that first call before any stream capture.  Every call overwrites the whole used
  * part of the array before reading it, so nothing needs clearing, but calls share the array:
  * calls that overlap on the GPU (different streams, or different host threads) race and must be
- * serialised by the caller.  Asynchronous on stream. */
+ * serialised by the caller.  It runs the shared-memory-staged slice kernels, which have no
+ * bounded device wait, so it has no failure flag to read.  Asynchronous on stream. */
 ufg_status ufg_apply_Q_noalloc(int nx, int ntau, double tau, double g, int dispersion,
                                const double* sigma, const double* x, double* y, void* stream);
 

@@ -34,9 +34,10 @@ __all__ = [
     "potentials", "apply_M", "apply_Mdag", "apply_Q", "apply_M1", "apply_M1T",
     "apply_M0inv", "apply_M0invT", "dense_from_apply", "sca_factors", "sca_apply",
     "cheb_roots", "cheb_quadratic_factors", "bit_reversed", "cheb_scale_eps",
-    "cheb_apply", "cheb_scalar", "euler_transform", "euler_weights", "wce_apply",
-    "wce_apply_T", "cg", "bicgstab", "solve_cg_normal", "solve_bicgstab_two_step",
-    "pseudofermion_action", "force_dS_dsigma", "mv_formula", "Counter",
+    "cheb_apply", "cheb_scalar", "sca_cheb_scale", "sca_cheb_apply", "euler_transform", "euler_table", "euler_23_level",
+    "special_vw_lambda_mu", "vanwijngaarden_weights", "euler_weights", "wce_apply",
+    "wce_apply_T", "make_preconditioner", "cg", "bicgstab", "solve_cg_normal", "solve_bicgstab_two_step",
+    "pseudofermion_action", "force_dS_dsigma", "leapfrog", "hmc_trajectory", "mv_formula", "Counter",
 ]
 
 
@@ -341,6 +342,39 @@ def cheb_apply(qop, v, degree: int, eps: float, scale: float, counter=None):
     return out / (z0 * scale)
 
 
+def sca_cheb_scale(lat, sigma, alpha, steps=30, safety=1.1):
+    """Spectral scale s of G = (L^T D L)^{-1} Q for the combined preconditioner: the power method
+    v <- G v / |v| from v = w = 1 + A sin(sigma) (deterministic: no random start vector), whose
+    ratio |G v| / |v| approaches lambda_max(G) from below, times a safety factor."""
+    D, L = sca_factors(lat, sigma, alpha)
+    v = potentials(lat, sigma)[0].copy()
+    vn = float(np.linalg.norm(v))
+    lam = 0.0
+    for _ in range(steps):
+        g = sca_apply(D, L, apply_Q(lat, sigma, v)) / vn
+        lam = float(np.linalg.norm(g))
+        v, vn = g, lam
+    return safety * lam
+
+
+def sca_cheb_apply(lat, sigma, r, alpha, degree, eps=None, scale=None, counter=None):
+    """The strong-coupling preconditioner with the Chebyshev polynomial as a secondary filter (end
+    of Sec. 4): z = P(G/s)/s P_S r with P_S = (L^T D L)^{-1} (Sec. 4) and G = P_S Q, P the
+    polynomial of Sec. 2 (cheb_apply with G as its operator).  Defaults: eps = 1e-3, s from
+    sca_cheb_scale."""
+    D, L = sca_factors(lat, sigma, alpha)
+    s = scale if scale else sca_cheb_scale(lat, sigma, alpha)
+    e = eps if eps else 1e-3
+
+    def gop(u):
+        if counter is not None:
+            counter.add("SCA", 1)
+        return sca_apply(D, L, apply_Q(lat, sigma, u))
+    if counter is not None:
+        counter.add("SCA", 1)
+    return cheb_apply(gop, sca_apply(D, L, r), degree, e, s, counter)
+
+
 # ----------------------------------------------------------------------------------------
 # Weak-coupling expansion (Sec. 3, Eq. WCE) and Euler acceleration (Eq. Euler)
 # ----------------------------------------------------------------------------------------
@@ -354,22 +388,90 @@ def euler_transform(partial_sums, p=0.5):
     return S[0]
 
 
-def euler_weights(d: int, euler: bool, p: float = 0.5):
-    """Weights c_n with sum_n c_n t_n = S_{d,0} for t_n the n-th series term: obtained by running
-    euler_transform on unit series (so they follow Eq. Euler, not a closed form)."""
-    if not euler:
+def euler_table(partial_sums, j: int, k: int, p=0.5):
+    """S_{j,k} of Eq. (Euler): the recursion applied j times to the partial sums S_{0,0..kmax},
+    entry k of the resulting sequence (needs j + k <= kmax)."""
+    S = list(partial_sums)
+    if not 0 <= k <= len(S) - 1 - j:
+        raise ValueError("S_{j,k} needs j + k <= kmax")
+    for _ in range(j):
+        S = [p * S[i] + (1 - p) * S[i + 1] for i in range(len(S) - 1)]
+    return S[k]
+
+
+def euler_23_level(d: int) -> int:
+    """Level j of the variant S_{2 kmax/3, kmax/3} (Sec. 3.1) for kmax = d: the paper leaves the
+    rounding open; j is the integer nearest 2d/3 and k = d - j, so the entry still uses every
+    term of the series."""
+    return (2 * d + 1) // 3
+
+
+def special_vw_lambda_mu(d: int, s: float = 1.0, p: float = 0.5):
+    """The special van Wijngaarden transformation (Sec. 3.1): lambda_k = s^k / k!, phi(t) =
+    s exp(-s t), and mu_k = int_0^inf phi(t) t^k / (1 - p + p t)^(k+1) dt for k = 0..d (the
+    integral by scipy's adaptive quadrature as a library step)."""
+    from scipy import integrate
+    lam = np.array([s ** k / math.factorial(k) for k in range(d + 1)])
+    mu = np.empty(d + 1)
+    for k in range(d + 1):
+        f = lambda t, k=k: s * math.exp(-s * t) * t ** k / (1.0 - p + p * t) ** (k + 1)  # noqa: E731
+        mu[k] = integrate.quad(f, 0.0, np.inf, epsabs=1e-16, epsrel=1e-13, limit=400)[0]
+    return lam, mu
+
+
+def vanwijngaarden_weights(d: int, lam, mu, p: float = 0.5):
+    """Weights c_j with sum_j c_j t_j = sum_{n=0}^{d} mu_n b_n, the van Wijngaarden estimate
+    truncated at order d (Sec. 3.1): the terms t_j = (-1)^j a_j are multiplied by lambda_j, Euler
+    transformed, b_n = sum_{j<=n} C(n, j) p^(n-j) (1-p)^(j+1) lambda_j t_j, and summed with the
+    weights mu_n."""
+    c = np.zeros(d + 1)
+    for j in range(d + 1):
+        acc = 0.0
+        for n in range(j, d + 1):
+            acc += math.comb(n, j) * p ** (n - j) * mu[n]
+        c[j] = lam[j] * (1.0 - p) ** (j + 1) * acc
+    return c
+
+
+ACCEL = {False: 0, True: 1, 0: 0, 1: 1, 2: 2, 3: 3, "none": 0, "euler": 1, "euler23": 2,
+         "vanw": 3}
+
+
+def euler_weights(d: int, euler=True, p: float = 0.5, s: float = 1.0):
+    """Weights c_n of the accelerated order-d sum sum_n c_n t_n, t_n the n-th term of the series.
+    euler: 0/False/"none" plain partial sum S_{0,d}; 1/True/"euler" S_{d,0}; 2/"euler23"
+    S_{j,d-j} with j = euler_23_level(d); 3/"vanw" the special van Wijngaarden transformation with
+    parameter s.  The Euler weights come from running the recursion on unit series (so they
+    follow Eq. Euler, not a closed form)."""
+    mode = ACCEL[euler]
+    if mode == 0 or d == 0 and mode != 3:
         return np.ones(d + 1)
+    if mode == 3:
+        lam, mu = special_vw_lambda_mu(d, s, p)
+        return vanwijngaarden_weights(d, lam, mu, p)
+    j = d if mode == 1 else euler_23_level(d)
     c = np.empty(d + 1)
     for n in range(d + 1):
         terms = np.zeros(d + 1)
         terms[n] = 1.0
-        c[n] = euler_transform(np.cumsum(terms), p)
+        c[n] = euler_table(np.cumsum(terms), j, d - j, p)
     return c
 
 
-def wce_apply(lat, sigma, v, d: int, euler=False, counter=None):
+def _accelerated_sum(terms, d, euler, p, s):
+    mode = ACCEL[euler]
+    if mode == 0:
+        return np.sum(terms, axis=0)
+    if mode in (1, 2):
+        j = d if mode == 1 else euler_23_level(d)
+        return euler_table(np.cumsum(np.array(terms), axis=0), j, d - j, p)
+    c = euler_weights(d, 3, p, s)
+    return sum(cn * t for cn, t in zip(c, terms))
+
+
+def wce_apply(lat, sigma, v, d: int, euler=False, counter=None, p=0.5, s=1.0):
     """P_d v = sum_{n=0}^{d} (-A X)^n M0^{-1} v with X = M0^{-1} M1 (Eq. WCE), optionally
-    Euler-accelerated over the partial sums."""
+    accelerated over the partial sums (euler: see euler_weights)."""
     terms = []
     w = apply_M0inv(lat, v)
     if counter is not None:
@@ -381,14 +483,12 @@ def wce_apply(lat, sigma, v, d: int, euler=False, counter=None):
             counter.add("M1", 1)
             counter.add("M0inv", 1)
         terms.append(w)
-    if euler and d > 0:
-        return euler_transform(np.cumsum(np.array(terms), axis=0))
-    return np.sum(terms, axis=0)
+    return _accelerated_sum(terms, d, euler, p, s)
 
 
-def wce_apply_T(lat, sigma, v, d: int, euler=False, counter=None):
+def wce_apply_T(lat, sigma, v, d: int, euler=False, counter=None, p=0.5, s=1.0):
     """P_d^T v = sum_n (-A)^n M0^{-T} (M1^T M0^{-T})^n v: the exact transpose of P_d, the
-    weak-coupling preconditioner of M^dagger."""
+    weak-coupling preconditioner of M^dagger (same acceleration as wce_apply)."""
     terms = []
     w = apply_M0invT(lat, v)
     if counter is not None:
@@ -400,9 +500,7 @@ def wce_apply_T(lat, sigma, v, d: int, euler=False, counter=None):
             counter.add("M1T", 1)
             counter.add("M0invT", 1)
         terms.append(w)
-    if euler and d > 0:
-        return euler_transform(np.cumsum(np.array(terms), axis=0))
-    return np.sum(terms, axis=0)
+    return _accelerated_sum(terms, d, euler, p, s)
 
 
 # ----------------------------------------------------------------------------------------
@@ -507,8 +605,16 @@ def bicgstab(aop, b, tol, maxit, precond=None, x0=None, restart_cos=1e-12, max_r
     return x, maxit, False
 
 
-def _make_pc(lat, sigma, pc, counter, transpose=False):
+def _make_pc(lat, sigma, pc, counter, transpose=False, normal=False):
+    """Preconditioner closure.  normal=True: for CG on M^dagger M, where the weak-coupling series
+    is used from both sides, P_d P_d^dagger ~ M^{-1} M^{-dagger} (M0^{-dagger} on the left and
+    M0^{-1} on the right, end of Sec. 5)."""
     kind = pc.get("kind", "none") if pc else "none"
+    if kind == "wce" and normal:
+        args = (pc["order"], pc.get("euler", False))
+        kw = {"p": pc.get("p", 0.5), "s": pc.get("s", 1.0)}
+        return lambda r: wce_apply(lat, sigma, wce_apply_T(lat, sigma, r, *args, counter, **kw),
+                                   *args, counter, **kw)
     if kind == "none":
         return None
     if kind == "cheb":
@@ -517,6 +623,10 @@ def _make_pc(lat, sigma, pc, counter, transpose=False):
             s = pc["scale"]
         qop = lambda u: apply_Q(lat, sigma, u)  # noqa: E731
         return lambda r: cheb_apply(qop, r, pc["degree"], eps, s, counter)
+    if kind == "sca_cheb":
+        alpha, degree = pc.get("alpha", 2.0), pc["degree"]
+        s = pc.get("scale") or sca_cheb_scale(lat, sigma, alpha)
+        return lambda r: sca_cheb_apply(lat, sigma, r, alpha, degree, pc.get("eps"), s, counter)
     if kind == "sca":
         D, L = sca_factors(lat, sigma, pc.get("alpha", 2.0))
 
@@ -526,19 +636,26 @@ def _make_pc(lat, sigma, pc, counter, transpose=False):
         return f
     if kind == "wce":
         fn = wce_apply_T if transpose else wce_apply
-        return lambda r: fn(lat, sigma, r, pc["order"], pc.get("euler", False), counter)
+        return lambda r: fn(lat, sigma, r, pc["order"], pc.get("euler", False), counter,
+                            pc.get("p", 0.5), pc.get("s", 1.0))
     raise ValueError(kind)
 
 
+def make_preconditioner(lat, sigma, pc, transpose=False, normal=False):
+    """The preconditioner the solvers use for a settings dict (see _make_pc); None for none."""
+    return _make_pc(lat, sigma, pc, Counter(), transpose, normal)
+
+
 def solve_cg_normal(lat, sigma, b, tol=1e-10, maxit=20000, pc=None):
-    """CG on M^dagger M x = b (Eq. 1) with an SPD preconditioner (Chebyshev or SCA)."""
+    """CG on M^dagger M x = b (Eq. 1) with an SPD preconditioner (Chebyshev, SCA, or the
+    weak-coupling series from both sides)."""
     counter = Counter()
 
     def qop(u):
         counter.add("M")
         counter.add("Mdag")
         return apply_Q(lat, sigma, u)
-    x, it, ok = cg(qop, b, tol, maxit, _make_pc(lat, sigma, pc, counter))
+    x, it, ok = cg(qop, b, tol, maxit, _make_pc(lat, sigma, pc, counter, normal=True))
     return x, {"iterations": it, "converged": ok, "counts": dict(counter)}
 
 
@@ -590,6 +707,36 @@ def pseudofermion_action(lat, sigma, phi, x=None, tol=1e-13):
     if x is None:
         x, _ = solve_cg_normal(lat, sigma, phi, tol=tol)
     return _dot(phi, x), x
+
+
+def leapfrog(lat, sigma, pi, phi, n_steps, dt, tol=1e-13):
+    """Molecular dynamics of the phi-algorithm (Sec. 1): H = sum pi^2/2 + S_p(sigma) with phi held
+    fixed, integrated by leapfrog (half step in pi, n_steps steps in sigma with full pi steps
+    between them, final half step).  Returns (sigma, pi, S_p at the start, S_p at the end)."""
+    sigma, pi = sigma.copy(), pi.copy()
+    S0, X = pseudofermion_action(lat, sigma, phi, tol=tol)
+    pi -= 0.5 * dt * force_dS_dsigma(lat, sigma, X)
+    S1 = S0
+    for k in range(1, n_steps + 1):
+        sigma += dt * pi
+        S1, X = pseudofermion_action(lat, sigma, phi, tol=tol)
+        pi -= (0.5 if k == n_steps else 1.0) * dt * force_dS_dsigma(lat, sigma, X)
+    return sigma, pi, S0, S1
+
+
+def hmc_trajectory(lat, sigma0, eta, pi0, u, n_steps, dt, tol=1e-13):
+    """One trajectory: pseudofermion heat bath phi = M^dagger eta (so S_p = |eta|^2), leapfrog,
+    Metropolis accept with probability min(1, exp(-dH)) against the uniform number u (Sec. 1).
+    Returns (sigma, pi, info)."""
+    phi = apply_Mdag(lat, sigma0, eta)
+    sigma, pi, S0, S1 = leapfrog(lat, sigma0, pi0, phi, n_steps, dt, tol)
+    H0 = 0.5 * _dot(pi0, pi0) + S0
+    H1 = 0.5 * _dot(pi, pi) + S1
+    dH = H1 - H0
+    accepted = dH <= 0 or u < math.exp(-dH)
+    return (sigma if accepted else sigma0.copy()), pi, {
+        "H_old": H0, "H_new": H1, "dH": dH, "accepted": accepted, "action_old": S0,
+        "action_new": S1}
 
 
 def force_dS_dsigma(lat, sigma, X):

@@ -18,7 +18,7 @@ LIB = os.path.join(LIBDIR, "libufg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SLICE_N = (4, 6, 8, 10, 12, 16, 32)
 UNITS = ["lattice.cu", "recurrence.cu", "dispatch.cu", "blas.cu", "solvers.cu", "batch.cu",
-         "noalloc.cu", "profile.cu"]
+         "noalloc.cu", "profile.cu", "series.cu"]
 
 
 def nvcc():

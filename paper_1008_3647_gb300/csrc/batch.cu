@@ -235,28 +235,17 @@ ufg_status scalb(Batch& B, int op, const double* part, int kind, const double* p
   return UFG_OK;
 }
 
-std::vector<double> weights(int d, bool euler) {
-  std::vector<double> c(d + 1, 1.0);
-  if (!euler || d == 0) return c;
-  std::vector<double> binom(d + 1, 0.0);
-  binom[0] = 1.0;
-  for (int i = 1; i <= d; ++i)
-    for (int k = i; k >= 1; --k) binom[k] += binom[k - 1];
-  for (int nn = 0; nn <= d; ++nn) {
-    double acc = 0.0;
-    for (int k = nn; k <= d; ++k) acc += binom[k];
-    c[nn] = acc / std::ldexp(1.0, d);
-  }
-  return c;
-}
-
 // z = P_d r (tr: P_d^T) for every running problem, momentum-space evaluation (see solvers.cu).
 // prep_r != nullptr: r is BiCGStab's direction p, first updated in place to
 // p = prep_r + beta (p - omega prep_v) by the forward transform (slice_tma_prep_supported).
 ufg_status wce_b(Batch& B, int prec, const void* r, void* z, bool tr,
                  const void* prep_r = nullptr, const void* prep_v = nullptr) {
   const int d = B.pc.order;
-  const std::vector<double> cw = weights(d, B.pc.euler != 0);
+  std::vector<double> cw;
+  if (!wce_series_weights(d, B.pc.euler, B.pc.euler_p, B.pc.vw_s, cw)) {
+    set_error("WCE: invalid series acceleration parameters");
+    return UFG_INVALID_ARG;
+  }
   Arena& V = B.ar[prec];
   // in the momentum basis r is already spectral and the series accumulates straight into z
   void* const acc = B.mom ? z : V.acc;
@@ -430,9 +419,9 @@ ufg_status bicg_b(Batch& B, int prec, int op, const std::vector<double>& tol,
                  OP_BI_RCHECK_RHO));
     return UFG_OK;
   };
-  char key[128];
-  snprintf(key, sizeof(key), "bicg|%d|%d|%d|%d|%d|%d|%d", prec, op, check_every, B.pc_kind,
-           B.pc.order, B.pc.euler, B.mom ? 1 : 0);
+  char key[192];
+  snprintf(key, sizeof(key), "bicg|%d|%d|%d|%d|%d|%d|%.17g|%.17g|%d", prec, op, check_every,
+           B.pc_kind, B.pc.order, B.pc.euler, B.pc.euler_p, B.pc.vw_s, B.mom ? 1 : 0);
   std::vector<int> restarts(B.n, 0);
   while (true) {
     UFG_TRY(read_scs(B));
@@ -966,10 +955,8 @@ extern "C" ufg_status ufg_solve_batch(int n, const ufg_problem* probs, int pc_ki
       return UFG_INVALID_ARG;
     }
   }
-  if (pc_kind == UFG_PC_WCE && (pc->order < 0 || pc->order > 16)) {
-    set_error("WCE order must be in 0..16");
-    return UFG_INVALID_ARG;
-  }
+  ufg_pc_params pcn = {};
+  if (pc_kind == UFG_PC_WCE) UFG_TRY(normalize_pc(pc_kind, pc, &pcn));
   const auto t0 = std::chrono::steady_clock::now();
   std::lock_guard<std::mutex> lk(g_batch_mu);
   const std::string sig = signature(n, probs);
@@ -986,7 +973,7 @@ extern "C" ufg_status ufg_solve_batch(int n, const ufg_problem* probs, int pc_ki
   }
   Batch* B = Bp;
   B->pc_kind = pc_kind;
-  if (pc) B->pc = *pc;
+  if (pc_kind == UFG_PC_WCE) B->pc = pcn;
   cudaStream_t user = as_stream(stream);
   cudaEvent_t ev;
   UFG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -1051,6 +1038,12 @@ extern "C" ufg_status ufg_solve_batch(int n, const ufg_problem* probs, int pc_ki
                              B->st));
   }
   UFG_CUDA(cudaStreamSynchronize(B->st));
+  // a bounded device wait that ran out in any group invalidates the whole batch
+  ufg_status flagged = UFG_OK;
+  for (auto& g : B->groups) {
+    const ufg_status fs = check_device_flag(g.lat, B->st);
+    if (fs != UFG_OK && flagged == UFG_OK) flagged = fs;
+  }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   for (int i = 0; i < n; ++i) {
     const int dn = (d1[i] == 1 && d2[i] == 1) ? 1 : (d1[i] != 1 ? d1[i] : d2[i]);
@@ -1060,6 +1053,7 @@ extern "C" ufg_status ufg_solve_batch(int n, const ufg_problem* probs, int pc_ki
                               : UFG_NOT_CONVERGED;
     const double rel = bn[i] > 0 ? rn[i] / bn[i] : 0.0;
     if (st == UFG_OK && rel > p->tol) st = UFG_NOT_CONVERGED;
+    if (flagged != UFG_OK) st = flagged;
     if (st != UFG_OK && worst == UFG_OK) worst = st;
     if (stats) {
       ufg_stats& s = stats[i];
@@ -1089,7 +1083,11 @@ extern "C" ufg_status ufg_solve_batch(int n, const ufg_problem* probs, int pc_ki
   cudaEventRecord(ev, B->st);
   cudaStreamWaitEvent(user, ev, 0);
   cudaEventDestroy(ev);
-  if (worst != UFG_OK) set_error("at least one problem of the batch did not converge");
+  if (flagged != UFG_OK) {
+    set_error("a bounded device wait ran out during the batched solve; its results are invalid");
+  } else if (worst != UFG_OK) {
+    set_error("at least one problem of the batch did not converge");
+  }
   return worst;
 }
 

@@ -41,6 +41,35 @@ void set_error(const char* fmt, ...) {
 }
 void clear_error() { g_err.clear(); }
 
+// Test hook: the number of coming TMA slice launches that run one wait made to run out.
+static std::atomic<int> g_expire{0};
+
+int take_expired_wait(cudaStream_t st) {
+  // never baked into a captured graph: its replays would all run the expiring wait
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return 0;
+  }
+  int n = g_expire.load(std::memory_order_relaxed);
+  while (n > 0 && !g_expire.compare_exchange_weak(n, n - 1, std::memory_order_relaxed)) {
+  }
+  return n > 0 ? 1 : 0;
+}
+
+ufg_status check_device_flag(const ufg_lattice* lat, cudaStream_t st) {
+  if (lat == nullptr || lat->dev_err == nullptr) return UFG_OK;
+  int h = 0;
+  UFG_CUDA(cudaMemcpyAsync(&h, lat->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  UFG_CUDA(cudaStreamSynchronize(st));
+  if (h == 0) return UFG_OK;
+  UFG_CUDA(cudaMemsetAsync(lat->dev_err, 0, sizeof(int), st));
+  UFG_CUDA(cudaStreamSynchronize(st));
+  set_error("a bounded device wait ran out (a TMA copy into shared memory did not complete); "
+            "the results of the kernels launched since the last check are invalid");
+  return UFG_TIMEOUT;
+}
+
 ufg_status cuda_fail(cudaError_t e, const char* what) {
   set_error("%s failed: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
   return UFG_CUDA_ERROR;
@@ -474,6 +503,17 @@ void ufg_lattice_destroy(ufg_lattice* L) {
 
 double ufg_lattice_coupling(const ufg_lattice* L) { return L ? L->A : 0.0; }
 
+ufg_status ufg_lattice_check(const ufg_lattice* L, void* stream) {
+  clear_error();
+  if (L == nullptr) {
+    set_error("null lattice");
+    return UFG_INVALID_ARG;
+  }
+  return check_device_flag(L, as_stream(stream));
+}
+
+void ufg_test_expire_waits(int launches) { g_expire.store(launches > 0 ? launches : 0); }
+
 ufg_status ufg_field_update(ufg_field* f, const double* sigma, void* stream) {
   clear_error();
   if (f == nullptr || sigma == nullptr || !aligned16(sigma)) {
@@ -487,6 +527,7 @@ ufg_status ufg_field_update(ufg_field* f, const double* sigma, void* stream) {
                              st));
   note_launches(1);
   f->sca_alpha = -1.0;
+  f->gcheb_alpha = -1.0;
   return UFG_OK;
 }
 
@@ -498,8 +539,10 @@ ufg_status ufg_field_create(const ufg_lattice* L, const double* sigma, void* str
     return UFG_INVALID_ARG;
   }
   *out = nullptr;
+  static std::atomic<unsigned long long> next_id{1};
   ufg_field* f = new ufg_field();
   f->lat = L;
+  f->id = next_id.fetch_add(1, std::memory_order_relaxed);
   const size_t S = (size_t)L->S;
   ufg_status s = UFG_OK;
   if ((s = dev_alloc(&f->sigma, S)) || (s = dev_alloc(&f->w64, S)) || (s = dev_alloc(&f->s64, S)) ||

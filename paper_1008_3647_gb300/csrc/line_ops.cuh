@@ -60,6 +60,21 @@ struct LineCoef {
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Two FP32 lines carried together (x: first line, y: second) so that every multiply-add and fold
+// of line_op is one packed FP32x2 instruction of sm_100 and later; the coefficients of
+// LineCoef<N, float2> hold each entry twice.
+__device__ __forceinline__ float2 fmadd(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)),
+        "l"(*reinterpret_cast<unsigned long long*>(&b)));
+  return *reinterpret_cast<float2*>(&d);
+}
+
 // row i of the n x n row-major block at c[off] times x
 template <int n, int off, typename R, int NC>
 __device__ __forceinline__ R block_row(const R (&c)[NC], const R* x, int i) {

@@ -1,8 +1,8 @@
 // Q = M^T M applied without any device allocation, for callers that cannot call cudaMalloc.
 //
 // Some host programs cannot allocate device memory at the point where they need the operator:
-// code running inside a CUDA-graph capture, inside a pool or arena whose owner forbids extra
-// allocations, or in a plugin that must not grow the process's device footprint after start-up.
+// code running inside a pool or arena whose owner forbids extra allocations, or a plugin that must
+// not grow the process's device footprint after start-up.
 // This entry point serves them: the caller passes sigma, x and y; the library keeps its two
 // intermediates (w = 1 + A sin sigma and the half-product M x) in a file-scope device array of fixed
 // size that every GPU loading the library holds until the process exits.  No cudaMalloc, cudaFree
@@ -107,6 +107,9 @@ ufg_status run_q(int ntau, double tau, int dispersion, double A, const double* x
   c.prec = 0;
   c.coef = &coef;
   c.ntau = ntau;
+  // the shared-memory-staged kernels: they contain no bounded device wait, so nothing can run
+  // out and there is no failure flag that would need a device allocation or a read-back here
+  c.allow_tma = 0;
   // launch shape as for a lattice of this size (4-CTA clusters for 32^3 FP64 slices)
   if (N >= 32) {
     c.C = 4;

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "line_ops.cuh"
 #include "ufg_internal.h"
 
 namespace ufg {
@@ -269,4 +270,70 @@ extern "C" ufg_status ufg_profile_read(ufg_kernel_stat* out, int max, int* n) {
     out[i].bytes = v[(size_t)i].second.bytes;
   }
   return UFG_OK;
+}
+
+// ---- arithmetic peak of this GPU (roofline denominators of the FP64 and FP32 applies) --------
+namespace ufg {
+namespace {
+
+// Each thread runs 8 independent multiply-add chains for `iters` rounds; the chains start from
+// values only the caller knows, and their sum is stored, so nothing can be folded away.
+template <typename R>
+__global__ void __launch_bounds__(256) fma_rate_kernel(R seed, int iters, R* out) {
+  R a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = seed + R(threadIdx.x * 8 + k) * R(1e-7);
+  const R m = R(0.999999), c = R(1e-9);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fmadd(a[k], m, c);
+  }
+  R s = R(0);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename R>
+ufg_status fma_rate(cudaStream_t st, double* tflops) {
+  int dev = 0, sms = 0, per_sm = 0;
+  UFG_CUDA(cudaGetDevice(&dev));
+  UFG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  UFG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_rate_kernel<R>, 256, 0));
+  const int blocks = sms * (per_sm > 0 ? per_sm : 1);
+  const int iters = sizeof(R) == 8 ? 4096 : 65536;
+  R* out = nullptr;
+  UFG_TRY(dev_alloc(&out, (size_t)blocks * 256));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fma_rate_kernel<R><<<blocks, 256, 0, st>>>(R(1), iters, out);  // warm-up
+  cudaEventRecord(e0, st);
+  const int reps = 5;
+  for (int r = 0; r < reps; ++r) fma_rate_kernel<R><<<blocks, 256, 0, st>>>(R(1), iters, out);
+  cudaEventRecord(e1, st);
+  note_launches(reps + 1);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dev_free(out);
+  if (e != cudaSuccess) return cuda_fail(e, "FMA-rate kernel");
+  const double flops = 2.0 * 8.0 * iters * 256.0 * blocks * reps;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  return UFG_OK;
+}
+
+}  // namespace
+}  // namespace ufg
+
+extern "C" ufg_status ufg_measure_fma_rate(int precision, void* stream, double* tflops) {
+  clear_error();
+  if (tflops == nullptr || (precision != UFG_FP64 && precision != UFG_FP32)) {
+    set_error("measure_fma_rate: need tflops and precision UFG_FP64 or UFG_FP32");
+    return UFG_INVALID_ARG;
+  }
+  return precision == UFG_FP64 ? fma_rate<double>(as_stream(stream), tflops)
+                               : fma_rate<float>(as_stream(stream), tflops);
 }

@@ -237,11 +237,26 @@ cudaError_t launch_sca_setup(const double* w64, long long V, int ntau, double al
   return cudaGetLastError();
 }
 
+// Epilogue of the SCA sweep: every finished z_t is stored as a z_t + bU U_t + cV W_t (U, W
+// nullable; neither may alias z, which holds the intermediate u = x / D until the backward sweep).
+template <typename R>
+struct ScaEpi {
+  R a, bU, cV;
+  const R* U;
+  const R* W;
+  __device__ __forceinline__ R operator()(R zt, size_t g) const {
+    R o = a * zt;
+    if (U != nullptr) o += bU * U[g];
+    if (W != nullptr) o += cV * W[g];
+    return o;
+  }
+};
+
 // z = (L^T D L)^{-1} y: forward solve with the lower factor (the recursion printed in Sec. 4),
 // pointwise 1/D, backward solve with the upper factor.  One thread per site, coalesced in r.
 template <typename R>
 __global__ void sca_apply_kernel(const R* __restrict__ L, const R* __restrict__ Di, const R* y,
-                                 R* z, long long V, int ntau, const int* done) {
+                                 R* z, long long V, int ntau, const int* done, ScaEpi<R> ep) {
   pdl_begin();
   if (done != nullptr && *done) return;
   const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -262,25 +277,31 @@ __global__ void sca_apply_kernel(const R* __restrict__ L, const R* __restrict__ 
   // z_0 = u_0 + L_0 z_1 - L_{N-1} z_{N-1}
   const size_t gl = (size_t)(N - 1) * V + r;
   const R zl = z[gl];
+  z[gl] = ep(zl, gl);
   R zn = zl;
   for (int t = N - 2; t >= 1; --t) {
     const size_t g = (size_t)t * V + r;
     const R zt = z[g] + L[g] * zn;
-    z[g] = zt;
+    z[g] = ep(zt, g);
     zn = zt;
   }
-  z[r] = z[r] + L[r] * zn - L[gl] * zl;
+  z[r] = ep(z[r] + L[r] * zn - L[gl] * zl, (size_t)r);
 }
 
 cudaError_t launch_sca_apply(int prec, const void* L, const void* Di, const void* y, void* z,
-                             long long V, int ntau, const int* done, cudaStream_t st) {
+                             long long V, int ntau, const int* done, cudaStream_t st, double a,
+                             const void* U, double bU, const void* W, double cV) {
   const unsigned grid = (unsigned)((V + 127) / 128);
-  if (prec == 0)
+  if (prec == 0) {
+    const ScaEpi<double> ep{a, bU, cV, (const double*)U, (const double*)W};
     sca_apply_kernel<double><<<grid, 128, 0, st>>>((const double*)L, (const double*)Di,
-                                                   (const double*)y, (double*)z, V, ntau, done);
-  else
+                                                   (const double*)y, (double*)z, V, ntau, done,
+                                                   ep);
+  } else {
+    const ScaEpi<float> ep{(float)a, (float)bU, (float)cV, (const float*)U, (const float*)W};
     sca_apply_kernel<float><<<grid, 128, 0, st>>>((const float*)L, (const float*)Di,
-                                                  (const float*)y, (float*)z, V, ntau, done);
+                                                  (const float*)y, (float*)z, V, ntau, done, ep);
+  }
   return cudaGetLastError();
 }
 

@@ -15,17 +15,19 @@ static __device__ __forceinline__ bool bad(double v) { return !isfinite(v); }
 // The four sums (pairs [i0, i1) of part, pairs [j0, j1) of part2) in one sweep: each thread adds
 // its strided share, the warps fold with shuffles and thread 0 adds the warp results in order
 // (a fixed, launch-independent order: the result is deterministic).  Valid in thread 0.
+// NT: threads of the calling CTA (SCAL_NT unless a kernel says otherwise).
+template <int NT = SCAL_NT>
 static __device__ void block_sums4(const double* part, int i0, int i1, const double* part2, int j0,
                             int j1, double (&out)[4]) {
-  __shared__ double red[SCAL_NT / 32][4];
+  __shared__ double red[NT / 32][4];
   double s[4] = {0.0, 0.0, 0.0, 0.0};
   if (part != nullptr)
-    for (int i = i0 + (int)threadIdx.x; i < i1; i += SCAL_NT) {
+    for (int i = i0 + (int)threadIdx.x; i < i1; i += NT) {
       s[0] += part[2 * i];
       s[1] += part[2 * i + 1];
     }
   if (part2 != nullptr)
-    for (int i = j0 + (int)threadIdx.x; i < j1; i += SCAL_NT) {
+    for (int i = j0 + (int)threadIdx.x; i < j1; i += NT) {
       s[2] += part2[2 * i];
       s[3] += part2[2 * i + 1];
     }
@@ -41,7 +43,7 @@ static __device__ void block_sums4(const double* part, int i0, int i1, const dou
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       double t = 0.0;
-      for (int w = 0; w < SCAL_NT / 32; ++w) t += red[w][k];
+      for (int w = 0; w < NT / 32; ++w) t += red[w][k];
       out[k] = t;
     }
   }
@@ -168,6 +170,7 @@ static __device__ __noinline__ void scalar_update(int op, DevScalars* sc, const 
 // `mine` of `part`: the CTA that completes a problem's set [i0, i1) (counted on `counter`, left at
 // 0 for the next producer) sums the set in fixed order and applies `op` to that problem's
 // scalars.  Partials reach the summing CTA through the fence before the count.
+template <int NT = SCAL_NT>
 static __device__ __forceinline__ void last_block_update(int op, DevScalars* sc, const double* part,
                                                         int i0, int i1, unsigned* counter) {
   __shared__ int is_last;
@@ -178,7 +181,7 @@ static __device__ __forceinline__ void last_block_update(int op, DevScalars* sc,
   if (!is_last) return;
   __threadfence();
   double r[4];
-  block_sums4(part, i0, i1, nullptr, 0, 0, r);
+  block_sums4<NT>(part, i0, i1, nullptr, 0, 0, r);
   if (threadIdx.x == 0) {
     scalar_update(op, sc, part, r[0], r[1], nullptr, 0.0, 0.0);
     *counter = 0u;

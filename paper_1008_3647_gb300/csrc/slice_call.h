@@ -82,6 +82,11 @@ struct SliceCall {
   double full_scale = 1.0;
 };
 
+// Test hook of ufg_test_expire_waits: 1 if this TMA launch on st runs one bounded wait that is
+// made to run out (consumes one of the requested launches), else 0; always 0 while st is being
+// captured into a graph.
+int take_expired_wait(cudaStream_t st);
+
 // Launches the slice kernel for lattice extent N (explicitly instantiated per N).
 template <int N>
 cudaError_t slice_launch(const SliceCall& c, cudaStream_t st);

@@ -3,6 +3,7 @@
 #include <cstdlib>
 
 #include "slice_kernel.cuh"
+#include "slice_pair.cuh"
 #include "slice_tma.cuh"
 
 #ifndef UFG_N

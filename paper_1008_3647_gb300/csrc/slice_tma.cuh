@@ -17,6 +17,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <cstring>
 
 #include "line_ops.cuh"
@@ -41,6 +42,7 @@ struct TmaArgs {
   LineCoef<N, R> coef_y;
   LineCoef<N, R> coef_z;
   const R* bkpost;
+  const R* pre_g;  // the load multiplier in global memory (8-CTA clusters read it directly)
   R* out;
   const R* id;
   const R* post;
@@ -64,6 +66,7 @@ struct TmaArgs {
   unsigned* counters;
   int part_base;
   int* err;  // set on an mbarrier wait that ran out (never expected)
+  int expire;  // test hook: run one wait that is made to run out (ufg_test_expire_waits)
 };
 
 template <int N, typename R>
@@ -94,9 +97,44 @@ __device__ __forceinline__ void tma_load_rows(void* dst, const CUtensorMap* tm, 
       : "memory");
 }
 
+// x-pass output: the row's N results are collected in registers and written back as 16-byte
+// chunks (chunk c at c ^ f(r)), which keeps the stores of a warp's 32 rows free of bank conflicts
+// (element-wise stores of one column index would hit 8 banks only).
+template <int N, typename R, bool IN_SPEC, bool OUT_SPEC>
+__device__ __forceinline__ void swz_store_row_impl(R* xs, int r, const R (&v)[N],
+                                                   const LineCoef<N, R>& cf) {
+  using G = SwzGeom<N, R>;
+  constexpr int CPR = G::RB / 16, EPC = 16 / (int)sizeof(R);
+  R o[N];
+  line_op<N, R, IN_SPEC, OUT_SPEC>(v, cf, [&](int i, R val) { o[i] = val; });
+#pragma unroll
+  for (int c = 0; c < CPR; ++c) {
+    R* dst = xs + G::chunk(r, c);
+    if constexpr (EPC == 4) {
+      *reinterpret_cast<float4*>(dst) =
+          make_float4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
+    } else {
+      *reinterpret_cast<double2*>(dst) = make_double2(o[2 * c], o[2 * c + 1]);
+    }
+  }
+}
+template <int N, typename R>
+__device__ __forceinline__ void swz_store_row(R* xs, int r, const R (&v)[N],
+                                              const LineCoef<N, R>& cf, bool in_spec,
+                                              bool out_spec) {
+  if (in_spec) {
+    if (out_spec) swz_store_row_impl<N, R, true, true>(xs, r, v, cf);
+    else swz_store_row_impl<N, R, true, false>(xs, r, v, cf);
+  } else {
+    if (out_spec) swz_store_row_impl<N, R, false, true>(xs, r, v, cf);
+    else swz_store_row_impl<N, R, false, false>(xs, r, v, cf);
+  }
+}
+
 constexpr int TMA_NT = 256;
 static_assert(TMA_NT == SCAL_NT, "fused scalar updates reduce over SCAL_NT threads");
 constexpr uint32_t TMA_WAIT_LIMIT = 1u << 22;  // try_wait rounds before giving up (< 1 s)
+constexpr uint32_t EXPIRE_LIMIT = 1u << 8;     // rounds of the wait ufg_test_expire_waits expires
 
 // Resident CTAs per SM the register allocation must allow.
 template <int N, typename R>
@@ -104,16 +142,28 @@ constexpr int tma_min_blocks() {
   return sizeof(R) == 4 ? (N == 16 ? 5 : 3) : (N <= 8 ? 4 : 3);
 }
 
+// Threads per CTA: 256, except for 8-CTA clusters of 32^3 slices (four z-planes per CTA, one
+// line per thread and pass), which run 128 threads and twice as many CTAs per SM.
+template <int C>
+constexpr int tma_nt() {
+  return C == 8 ? 128 : TMA_NT;
+}
+template <int N, typename R, int C>
+constexpr int tma_blocks() {
+  return C == 8 ? 6 : tma_min_blocks<N, R>();
+}
+
 // One work unit per CTA (a persistent loop would make the compiler hoist the ~500 line-operator
 // coefficients out of it into registers); several CTAs per SM overlap one another's TMA loads,
 // line passes and stores.
 template <int N, typename R, int C, int FAM, int EPI>
-__global__ void __launch_bounds__(TMA_NT, (tma_min_blocks<N, R>()))
+__global__ void __launch_bounds__(tma_nt<C>(), (tma_blocks<N, R, C>()))
 slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   pdl_begin();
   namespace cg = cooperative_groups;
   using G = SwzGeom<N, R>;
   constexpr int NP = N / C;
+  constexpr int NT = tma_nt<C>();
   constexpr int NN = N * N;
   constexpr int VOL = N * N * N;
   constexpr int ROWS = NP * N;      // rows of one box
@@ -122,9 +172,16 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   constexpr int EPC = 16 / (int)sizeof(R);
   constexpr bool IN_SPEC = (FAM == FAM_INV);
   constexpr bool OUT_SPEC = (FAM == FAM_FWD);
+  // 8-CTA clusters keep the pushed z-columns in a buffer of their own and read the load
+  // multiplier from global memory: no cluster-wide wait is then needed between the x- and
+  // y-passes (only one that every CTA of the cluster has started), and two 16 KB boxes per CTA
+  // let six CTAs share an SM
+  constexpr bool SEP = (C == 8);
+  static_assert(!SEP || (EPI & E_PREP) == 0, "the fused direction update needs the box layout");
+  static_assert(!SEP || ROWS == NT, "8-CTA clusters: one row per thread");
   extern __shared__ __align__(1024) unsigned char tma_smem[];
-  __shared__ double red[TMA_NT / 32][2];
-  __shared__ alignas(8) uint64_t bar;
+  __shared__ double red[NT / 32][2];
+  __shared__ alignas(8) uint64_t bar, bar2;
 
   const int tid = threadIdx.x;
   const int unit = blockIdx.x / C;
@@ -147,6 +204,7 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   if (done != nullptr && A.exec_if >= 0 && *done != A.exec_if) return;  // uniform per cluster
   int rank = 0;
   if constexpr (C > 1) rank = (int)cg::this_cluster().block_rank();
+  if constexpr (SEP) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
   int t_in = t_out;
   if (A.shift < 0) t_in = (t_out == 0) ? ntau - 1 : t_out - 1;
   if (A.shift > 0) t_in = (t_out == ntau - 1) ? 0 : t_out + 1;
@@ -156,30 +214,39 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   const R* const ws = reinterpret_cast<R*>(base) + BUF;
 
   // ---- TMA: this CTA's planes of x (and of the load multiplier) in one box each ----
+  const bool box_pre = A.has_pre && !SEP;
   if (tid == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     const int row = (int)((off + (size_t)t_in * VOL + (size_t)rank * NP * NN) / N);
     mbar_expect_tx(&bar, (uint32_t)(BUF * sizeof(R)) *
-                             ((A.has_pre ? 2u : 1u) + ((EPI & E_PREP) ? 2u : 0u)));
+                             ((box_pre ? 2u : 1u) + ((EPI & E_PREP) ? 2u : 0u)));
     tma_load_rows(xs, &A.tm_in, row, &bar);
     if constexpr ((EPI & E_PREP) != 0) {
       tma_load_rows(xs + BUF, &A.tm_r, row, &bar);
       tma_load_rows(xs + 2 * BUF, &A.tm_v, row, &bar);
     }
-    if (A.has_pre)
+    if (box_pre)
       tma_load_rows(const_cast<R*>(ws), &A.tm_pre, A.pre_mode ? rank * NP * N : row, &bar);
   }
-  __syncthreads();  // the mbarrier is initialised before anyone waits on it
-  {
-    uint32_t n = 0;
-    while (!mbar_try_wait(&bar, 0u)) {
-      if (++n > TMA_WAIT_LIMIT) {
-        if (A.err != nullptr) atomicExch(A.err, 1);
-        break;
+  // 8-CTA clusters: this thread's row of the multiplier, loaded while the box is in flight
+  R wrow[SEP ? N : 1];
+  if constexpr (SEP) {
+    if (A.has_pre) {
+      const R* src = A.pre_g + (size_t)rank * NP * NN + (size_t)tid * N;
+      if (!A.pre_mode) src += off + (size_t)t_in * VOL;
+#pragma unroll
+      for (int c = 0; c < CPR; ++c) {
+        R w4[EPC];
+        ld16(src + c * EPC, w4);
+#pragma unroll
+        for (int e = 0; e < EPC; ++e) wrow[c * EPC + e] = w4[e];
       }
     }
   }
+  __syncthreads();  // the mbarrier is initialised before anyone waits on it
+  mbar_wait_bounded(&bar, 0u, TMA_WAIT_LIMIT, A.err);
+  if (A.expire && tid == 0) mbar_expire_one_wait(&bar2, EXPIRE_LIMIT, A.err);
 
   R pbeta = R(0), pomega = R(0);
   R* pdst = nullptr;
@@ -190,7 +257,7 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
     pdst = A.prep_out + off + (size_t)t_in * VOL + (size_t)rank * NP * NN;
   }
   // ---- x-pass: one row per thread, read as 16-byte chunks ----
-  for (int r = tid; r < ROWS; r += TMA_NT) {
+  for (int r = tid; r < ROWS; r += NT) {
     R v[N];
 #pragma unroll
     for (int c = 0; c < CPR; ++c) {
@@ -206,11 +273,16 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
         }
         st16(pdst + r * N + c * EPC, pn);
       } else if (A.has_pre) {
+        if constexpr (SEP) {
 #pragma unroll
-        for (int e = 0; e < EPC; ++e) v[c * EPC + e] *= ws[o + e];
+          for (int e = 0; e < EPC; ++e) v[c * EPC + e] *= wrow[c * EPC + e];
+        } else {
+#pragma unroll
+          for (int e = 0; e < EPC; ++e) v[c * EPC + e] *= ws[o + e];
+        }
       }
     }
-    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_x, [&](int i, R val) { xs[G::off(r, i)] = val; });
+    swz_store_row<N, R>(xs, r, v, A.coef_x, IN_SPEC, OUT_SPEC);
   }
   // Clusters exchange by pushing: the y-pass stores each result straight into the CTA that owns
   // its z-column (rows [o RY, (o+1) RY) of every plane belong to CTA o), in that CTA's
@@ -218,7 +290,10 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   // frees every multiplier box, the second publishes the pushed columns.
   constexpr int RY = N / C;
   R* const recv = xs + BUF;  // [plane z][row y - rank RY][x], plain layout
-  if constexpr (C > 1) {
+  if constexpr (SEP) {
+    __syncthreads();  // this CTA's x-pass is complete
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");  // every CTA has started
+  } else if constexpr (C > 1) {
     cg::this_cluster().sync();
   } else {
     __syncthreads();
@@ -233,7 +308,7 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
       rdst[o] = recv;
     }
   }
-  for (int l = tid; l < NP * N; l += TMA_NT) {
+  for (int l = tid; l < NP * N; l += NT) {
     const int p = l / N, x = l - (l / N) * N;
     R v[N];
 #pragma unroll
@@ -269,7 +344,7 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   // per-thread partial sums in the working precision (FP64 arithmetic is slow on this part and
   // a thread sums at most N terms); converted to FP64 for the block reduction
   R acc_dot = R(0), acc_self = R(0);
-  for (int l = tid; l < COLS; l += TMA_NT) {
+  for (int l = tid; l < COLS; l += NT) {
     const int q = rank * COLS + l;
     const int y = q / N, x = q - (q / N) * N;
     R v[N];
@@ -334,14 +409,14 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
     __syncthreads();
     if (tid == 0) {
       double d = 0.0, q2 = 0.0;
-      for (int w = 0; w < TMA_NT / 32; ++w) {
+      for (int w = 0; w < NT / 32; ++w) {
         d += red[w][0];
         q2 += red[w][1];
       }
       A.partials[2 * blockIdx.x] = d;
       A.partials[2 * blockIdx.x + 1] = q2;
     }
-    if (A.fop >= 0 && A.tiles != nullptr) {
+    if (NT == SCAL_NT && A.fop >= 0 && A.tiles != nullptr) {
       const int prob = A.tiles[unit].prob;
       last_block_update(A.fop, A.scs + prob, A.partials, A.probs[prob].st0 - A.part_base,
                         A.probs[prob].st1 - A.part_base, A.counters + prob);
@@ -415,6 +490,7 @@ inline cudaError_t tma_launch_epi(const SliceCall& c, cudaStream_t st) {
   a.coef_y = a.coef_x;
   a.coef_z = a.coef_x;
   a.bkpost = static_cast<const R*>(c.bkpost);
+  a.pre_g = static_cast<const R*>(a.pre_mode ? c.bkpre : c.pre);
   a.out = static_cast<R*>(c.out);
   a.id = static_cast<const R*>(c.id);
   a.post = static_cast<const R*>(c.post);
@@ -437,6 +513,7 @@ inline cudaError_t tma_launch_epi(const SliceCall& c, cudaStream_t st) {
   a.shift = c.shift;
   a.units = c.tiles != nullptr ? c.ntiles : c.ntau;
   a.err = c.err;
+  a.expire = take_expired_wait(st);
   if constexpr ((EPI & E_PREP) != 0) {
     if (c.tiles == nullptr || c.scs == nullptr || c.prep_out == nullptr || a.has_pre)
       return cudaErrorInvalidValue;
@@ -453,6 +530,7 @@ inline cudaError_t tma_launch_epi(const SliceCall& c, cudaStream_t st) {
   const size_t smem = (size_t)(((EPI & E_PREP) != 0) ? 3 : ((a.has_pre || C > 1) ? 2 : 1)) * BUF *
                           sizeof(R) +
                       1024;
+  if (C == 8 && a.has_pre && a.pre_g == nullptr) return cudaErrorInvalidValue;
   auto kern = slice_tma_kernel<N, R, C, FAM, EPI>;
   static int configured = 0;
   if (!configured) {
@@ -467,7 +545,8 @@ inline cudaError_t tma_launch_epi(const SliceCall& c, cudaStream_t st) {
   }
   const int clusters = a.units;
   if (c.grid_out) *c.grid_out = clusters * C;
-  return launch_k(kern, dim3(clusters * C), dim3(TMA_NT), smem, st, C, a);
+  if (C == 8 && c.fop >= 0) return cudaErrorInvalidValue;  // the fused scalar step needs 256
+  return launch_k(kern, dim3(clusters * C), dim3(tma_nt<C>()), smem, st, C, a);
 }
 
 template <int N, typename R, int C, int FAM>
@@ -476,7 +555,7 @@ inline cudaError_t tma_launch_fam(const SliceCall& c, cudaStream_t st) {
                    ((c.U || c.V) ? E_UV : 0) | ((c.want_dotP || c.want_self) ? E_DOT : 0) |
                    (c.bkpost ? E_BK : 0) | (c.prep_out ? E_PREP : 0);
   if ((mask & E_PREP) != 0) {  // only the plain forward transform takes the direction update
-    if constexpr (FAM == FAM_FWD) {
+    if constexpr (FAM == FAM_FWD && C != 8) {
       if (mask == E_PREP) return tma_launch_epi<N, R, C, FAM, E_PREP>(c, st);
     }
     return cudaErrorInvalidValue;
@@ -528,6 +607,7 @@ struct M1wArgs {
   int scale_by_A;
   int ntau;
   int* err;
+  int expire;  // test hook, see TmaArgs
   // FULL (the whole operator in momentum space, see slice_m1w_kernel): out = full_scale * M x +
   // bU * U, partial sums and the batched scalar step
   const R* U;
@@ -559,7 +639,7 @@ __device__ __forceinline__ void swz_xpass(R* xs, const R* mul, const LineCoef<N,
 #pragma unroll
       for (int e = 0; e < EPC; ++e) v[c * EPC + e] = MUL ? xs[o + e] * mul[o + e] : xs[o + e];
     }
-    line_op<N, R, IN_SPEC, OUT_SPEC>(v, cf, [&](int i, R val) { xs[G::off(r, i)] = val; });
+    swz_store_row<N, R>(xs, r, v, cf, IN_SPEC, OUT_SPEC);
   }
 }
 
@@ -591,7 +671,7 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
   constexpr int NN = N * N;
   constexpr int VOL = N * NN;
   extern __shared__ __align__(1024) unsigned char tma_smem[];
-  __shared__ alignas(8) uint64_t bar;
+  __shared__ alignas(8) uint64_t bar, bar2;
   __shared__ double red[FULL ? TMA_NT / 32 : 1][2];
   const int tid = threadIdx.x;
   int t_out, ntau;
@@ -630,15 +710,8 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
     if (DIR == 1) tma_load_rows(ks, &A.tm_k, 0, &bar);
   }
   __syncthreads();
-  {
-    uint32_t n = 0;
-    while (!mbar_try_wait(&bar, 0u)) {
-      if (++n > TMA_WAIT_LIMIT) {
-        if (A.err != nullptr) atomicExch(A.err, 1);
-        break;
-      }
-    }
-  }
+  mbar_wait_bounded(&bar, 0u, TMA_WAIT_LIMIT, A.err);
+  if (A.expire && tid == 0) mbar_expire_one_wait(&bar2, EXPIRE_LIMIT, A.err);
   // inverse transform (spectral input); DIR 1 weights the modes by b on the way in
   swz_xpass<N, R, true, false, DIR == 1>(xs, ks, A.ci_x);
   __syncthreads();
@@ -685,15 +758,7 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
       });
     }
   } else {
-    {
-      uint32_t n = 0;
-      while (!mbar_try_wait(&bar, 1u)) {
-        if (++n > TMA_WAIT_LIMIT) {
-          if (A.err != nullptr) atomicExch(A.err, 1);
-          break;
-        }
-      }
-    }
+    mbar_wait_bounded(&bar, 1u, TMA_WAIT_LIMIT, A.err);
     const size_t so = off + (size_t)t_out * VOL;
     const R* __restrict__ gU = A.U ? A.U + so : nullptr;
     const R fs = R(A.full_scale), bU = R(A.bU);
@@ -774,6 +839,7 @@ inline cudaError_t m1w_launch(const SliceCall& c, cudaStream_t st) {
   a.scale_by_A = c.scale_by_A;
   a.ntau = c.ntau;
   a.err = c.err;
+  a.expire = take_expired_wait(st);
   if constexpr (FULL) {
     if ((c.want_dotP && c.dotP == nullptr) || ((c.want_dotP || c.want_self) && !c.partials) ||
         (c.fop >= 0 && (c.tiles == nullptr || c.scs == nullptr || c.counters == nullptr)))
@@ -828,11 +894,39 @@ inline cudaError_t slice_m1w_try(const SliceCall& c, cudaStream_t st) {
   return cudaErrorNotSupported;
 }
 
+// CTAs per cluster of the FP32 32^3 slice kernel: 8 (the default; a receive buffer of its own,
+// six CTAs per SM) or, with UFG_TMA_C32=4, 4 (the receive buffer shared with the multiplier box,
+// two cluster-wide waits, three CTAs per SM).  On the 32^3 x 512 applies: M 63.1 against 63.0 us,
+// M^T 58.0 against 69.5 us.
+inline int tma_c32() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("UFG_TMA_C32");
+    v = (e && std::atoi(e) == 4) ? 4 : 8;
+  }
+  return v;
+}
+
+// Paired-line FP32 kernel (slice_pair.cuh); cudaErrorNotSupported outside what it covers.
+template <int N>
+cudaError_t tma_pair_try(const SliceCall& c, cudaStream_t st);
+
 // TMA path for one N: cudaErrorNotSupported when the call is outside what it covers.
 template <int N>
 inline cudaError_t slice_tma_try(const SliceCall& c, cudaStream_t st) {
   if (c.bkpre != nullptr && c.pre != nullptr) return cudaErrorNotSupported;
   if (c.prec == 1) {
+    const cudaError_t e = tma_pair_try<N>(c, st);
+    if (e != cudaErrorNotSupported) return e;
+    if constexpr (N == 32) {
+      if (tma_c32() == 8 && c.fop < 0) {
+        switch (c.fam) {
+          case FAM_KIN: return tma_launch_fam<N, float, 8, FAM_KIN>(c, st);
+          case FAM_FWD: return tma_launch_fam<N, float, 8, FAM_FWD>(c, st);
+          case FAM_INV: return tma_launch_fam<N, float, 8, FAM_INV>(c, st);
+        }
+      }
+    }
     if constexpr (N == 16 || N == 32) {
       constexpr int C = N == 32 ? 4 : 1;
       switch (c.fam) {

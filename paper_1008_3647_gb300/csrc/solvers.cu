@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "blas.cuh"
+#include "launch.cuh"
 #include "ufg_internal.h"
 
 using namespace ufg;
@@ -64,6 +65,7 @@ struct ufg_solver {
   Counts counts;
   double inner_auto[2] = {0.0, 0.0};  // autotuned inner tolerance per method (0: not yet)
   double* x0s64 = nullptr;            // the caller's initial guess kept across tuning trials
+  double* hmc64 = nullptr;            // HMC trajectory: sigma_0, sigma, pi, phi, force (5 S)
   // Momentum basis (Sec. 3): while `mom` is set, BiCGStab's vectors hold F x per slice, the
   // operator is the fused momentum-space M and the WCE preconditioner needs no transforms.
   // mb64 / mx64: right-hand side and solution in that basis (lattices with the fused kernel).
@@ -294,30 +296,17 @@ ufg_status pc_cheb(ufg_solver* S, const ufg_field* f, int prec, const void* r, v
   return UFG_OK;
 }
 
-// Euler p = 1/2 weights c_n = 2^-d sum_{k=n}^{d} C(d, k): the result of applying the Euler
-// recursion S_{j+1,k} = (S_{j,k} + S_{j,k+1}) / 2 d times to the partial sums (Sec. 3.1).
-std::vector<double> wce_weights(int d, bool euler) {
-  std::vector<double> c(d + 1, 1.0);
-  if (!euler || d == 0) return c;
-  std::vector<double> binom(d + 1, 0.0);
-  binom[0] = 1.0;
-  for (int i = 1; i <= d; ++i)
-    for (int k = i; k >= 1; --k) binom[k] += binom[k - 1];
-  for (int nn = 0; nn <= d; ++nn) {
-    double acc = 0.0;
-    for (int k = nn; k <= d; ++k) acc += binom[k];
-    c[nn] = acc / std::ldexp(1.0, d);
-  }
-  return c;
-}
-
 // P_d r = sum_n c_n (-A)^n (M0^{-1} M1)^n M0^{-1} r (transpose: its exact transpose), evaluated in
 // momentum space: every M0^{-1} is the per-mode recurrence, M1 / M1^T are fused with the
 // transforms (F^T M1 w = sgn exp(-tau E) F^T(s w_shifted), M1^T F x = sgn s F(exp(-tau E) x_shifted)).
 ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, void* z, bool tr) {
   const ufg_lattice* L = f->lat;
   const int d = S->pc.order;
-  const std::vector<double> cw = wce_weights(d, S->pc.euler != 0);
+  std::vector<double> cw;
+  if (!wce_series_weights(d, S->pc.euler, S->pc.euler_p, S->pc.vw_s, cw)) {
+    set_error("WCE: invalid series acceleration parameters");
+    return UFG_INVALID_ARG;
+  }
   VecSet& V = S->vs[prec];
   const void* bk = prec ? (const void*)L->bk32 : (const void*)L->bk64;
   const int* done = &S->sc->done;
@@ -419,9 +408,95 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
   return UFG_OK;
 }
 
+// The strong-coupling factorisation with the Chebyshev polynomial as a secondary filter (end of
+// Sec. 4): z = P(G/s)/s P_S r with P_S = (L^T D L)^{-1} and G = P_S Q, the polynomial of Sec. 2 in
+// the conjugate-pair factors of pc_cheb applied to the SCA-preconditioned operator.  SPD (P_S is,
+// and P > 0 on [0, 1]).  Per factor k, with cur the running vector:
+//   u = P_S(Q cur)/s - a_k cur,   z = [P_S(Q u)/s - a_k u + b_k^2 cur] / norm_k,
+// both combinations done by the SCA sweep's epilogue; the last factor carries 1/(z0 s).
+ufg_status sca_sweep(ufg_solver* S, const ufg_field* f, int prec, const void* y, void* z, double a,
+                     const void* U, double bU, const void* W, double cV) {
+  const void* Lt = prec ? (const void*)f->L32 : (const void*)f->L64;
+  const void* Di = prec ? (const void*)f->Di32 : (const void*)f->Di64;
+  KTimer kt(std::string("sca") + (prec ? " f32" : " f64"), S->st,
+            solo_work(&S->sc->done, 0,
+                      (double)f->lat->S * (prec ? 4.0 : 8.0) *
+                          (5 + (U ? 1 : 0) + (W ? 1 : 0))));
+  cudaError_t e = launch_sca_apply(prec, Lt, Di, y, z, f->lat->V, f->lat->ntau, &S->sc->done,
+                                   S->st, a, U, bU, W, cV);
+  if (e != cudaSuccess) return cuda_fail(e, "SCA sweep");
+  note_launches(1);
+  S->counts.sca++;
+  return UFG_OK;
+}
+
+ufg_status pc_sca_cheb(ufg_solver* S, const ufg_field* f, int prec, const void* r, void* z) {
+  if (f->sca_alpha != S->pc.alpha || f->L64 == nullptr) {
+    set_error("SCA tables not prepared");
+    return UFG_INTERNAL;
+  }
+  const int d = S->pc.degree, n = d / 2;
+  const double s = S->pc.scale > 0 ? S->pc.scale : f->gcheb_scale;
+  const double eps = S->pc.eps > 0 ? S->pc.eps : 1e-3;
+  if (!(s > 0)) {
+    set_error("SCA + Chebyshev: no spectral scale (estimate not prepared)");
+    return UFG_INTERNAL;
+  }
+  const double z0 = 0.5 * (1.0 + eps);
+  std::vector<double> ak(n), bk2(n), nk(n);
+  for (int k = 0; k < n; ++k) {
+    const double th = 2.0 * 3.14159265358979323846 * (k + 1) / (2 * n + 1);
+    ak[k] = z0 * (1.0 - std::cos(th));
+    const double bb = std::sqrt(eps) * std::sin(th);
+    bk2[k] = bb * bb;
+    nk[k] = (z0 - ak[k]) * (z0 - ak[k]) + bk2[k];
+  }
+  int bits = 0;
+  while ((1 << bits) < n) ++bits;
+  if (bits == 0) bits = 1;
+  std::vector<int> order;
+  for (int i = 0; i < (1 << bits); ++i) {
+    int rv = 0;
+    for (int b = 0; b < bits; ++b)
+      if (i & (1 << b)) rv |= 1 << (bits - 1 - b);
+    if (rv < n) order.push_back(rv);
+  }
+  VecSet& V = S->vs[prec];
+  UFG_TRY(sca_sweep(S, f, prec, r, V.y, 1.0, nullptr, 0.0, nullptr, 0.0));  // cur = P_S r
+  const void* cur = V.y;
+  const int nf = (int)order.size();
+  for (int j = 0; j < nf; ++j) {
+    const int k = order[j];
+    const bool last = (j + 1 == nf);
+    const double fin = last ? 1.0 / (z0 * s) : 1.0;
+    // the output alternates between V.s and z so that the last factor lands in z
+    void* out = ((nf - 1 - j) % 2 == 0) ? z : V.s;
+    if (out == cur) out = (out == z) ? V.s : z;
+    UFG_TRY(apply_op(S, f, prec, OPK_Q, cur, V.t, 1.0, nullptr, 0.0, nullptr, false, nullptr,
+                     nullptr));
+    UFG_TRY(sca_sweep(S, f, prec, V.t, V.u, 1.0 / s, cur, -ak[k], nullptr, 0.0));
+    UFG_TRY(apply_op(S, f, prec, OPK_Q, V.u, V.t, 1.0, nullptr, 0.0, nullptr, false, nullptr,
+                     nullptr));
+    UFG_TRY(sca_sweep(S, f, prec, V.t, out, fin / (s * nk[k]), V.u, -fin * ak[k] / nk[k], cur,
+                      fin * bk2[k] / nk[k]));
+    cur = out;
+  }
+  if (cur != z) {  // (cannot happen with the alternation above; kept as a guard)
+    set_error("SCA + Chebyshev: result not in the output vector");
+    return UFG_INTERNAL;
+  }
+  return UFG_OK;
+}
+
 // Per-field preconditioner set-up that allocates or launches once (kept out of captured graphs).
+ufg_status sca_cheb_estimate(ufg_solver* S, ufg_field* f);
+
 ufg_status pc_prepare(ufg_solver* S, ufg_field* f) {
   if (S->pc_kind == UFG_PC_SCA) return ensure_sca(f, S->pc.alpha, S->st);
+  if (S->pc_kind == UFG_PC_SCA_CHEB) {
+    UFG_TRY(ensure_sca(f, S->pc.alpha, S->st));
+    if (S->pc.scale <= 0 && f->gcheb_alpha != S->pc.alpha) UFG_TRY(sca_cheb_estimate(S, f));
+  }
   return UFG_OK;
 }
 
@@ -445,9 +520,23 @@ ufg_status pc_apply(ufg_solver* S, ufg_field* f, int prec, const void* r, void* 
     }
     case UFG_PC_WCE:
       return pc_wce(S, f, prec, r, z, tr);
+    case UFG_PC_SCA_CHEB:
+      return pc_sca_cheb(S, f, prec, r, z);
   }
   set_error("no preconditioner selected");
   return UFG_INVALID_ARG;
+}
+
+// Preconditioner of Q = M^T M for CG: Chebyshev, SCA, or the weak-coupling series from both
+// sides, P_d P_d^T ~ M^{-1} M^{-T} = Q^{-1}: P_d^T to the left of M^T and P_d to the right of M,
+// the two-sided use of M0^{-1} that the end of Sec. 5 names for CG.  SPD for any order.
+ufg_status pc_apply_q(ufg_solver* S, ufg_field* f, int prec, const void* r, void* z) {
+  if (S->pc_kind == UFG_PC_WCE) {
+    void* mid = S->vs[prec].y;  // not used by CG or by the series
+    UFG_TRY(pc_wce(S, f, prec, r, mid, true));
+    return pc_wce(S, f, prec, mid, z, false);
+  }
+  return pc_apply(S, f, prec, r, z, false);
 }
 
 // ---- graph replay ---------------------------------------------------------------------------
@@ -522,9 +611,9 @@ ufg_status write_scalars(ufg_solver* S, double tol, int maxit, double div_limit 
 std::string key_of(const char* kind, ufg_solver* S, const ufg_field* f, int prec, int op,
                    int reps) {
   char buf[256];
-  snprintf(buf, sizeof(buf), "%s|%p|%d|%d|%d|%d|%d|%g|%g|%g|%d|%d|%d", kind, (const void*)f, prec,
-           op, reps, S->pc_kind, S->pc.degree, S->pc.eps, S->pc.scale, S->pc.alpha, S->pc.order,
-           S->pc.euler, S->mom ? 1 : 0);
+  snprintf(buf, sizeof(buf), "%s|%llu|%d|%d|%d|%d|%d|%g|%g|%g|%d|%d|%.17g|%.17g|%d", kind, f->id,
+           prec, op, reps, S->pc_kind, S->pc.degree, S->pc.eps, S->pc.scale, S->pc.alpha,
+           S->pc.order, S->pc.euler, S->pc.euler_p, S->pc.vw_s, S->mom ? 1 : 0);
   return buf;
 }
 
@@ -539,7 +628,7 @@ ufg_status run_cg(ufg_solver* S, ufg_field* f, int prec, double tol, int maxit, 
                   bool x0, KrylovResult* res, double div_limit = 0.0) {
   VecSet& V = S->vs[prec];
   const long long n = f->lat->S;
-  const bool pc = S->pc_kind == UFG_PC_CHEB || S->pc_kind == UFG_PC_SCA;
+  const bool pc = S->pc_kind != UFG_PC_NONE;
   UFG_TRY(write_scalars(S, tol, maxit, div_limit));
   int np = 0, npd = 0, nps = 0;
   if (x0) {
@@ -550,7 +639,7 @@ ufg_status run_cg(ufg_solver* S, ufg_field* f, int prec, double tol, int maxit, 
     VEC_NODONE(prec, V_ZERO, n, V.x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
   }
   void* z = pc ? V.z : V.r;
-  if (pc) UFG_TRY(pc_apply(S, f, prec, V.r, V.z, false));
+  if (pc) UFG_TRY(pc_apply_q(S, f, prec, V.r, V.z));
   VEC_NODONE(prec, V_DOT, n, V.r, z, V.r, V.r, nullptr, nullptr, slot(S, P_DOT), &npd);
   VEC_NODONE(prec, V_DOT, n, nullptr, nullptr, V.rhs, V.rhs, nullptr, nullptr, slot(S, P_RES), &nps);
   SCALAR(OP_CG_INIT, slot(S, P_DOT), npd, slot(S, P_RES), nps);
@@ -563,7 +652,7 @@ ufg_status run_cg(ufg_solver* S, ufg_field* f, int prec, double tol, int maxit, 
     VEC(prec, V_CG_UPDATE, n, V.x, V.p, V.r, V.q, nullptr, nullptr, slot(S, P_VEC1), &nv);
     SCALAR(OP_CG_CHECK, slot(S, P_VEC1), nv, nullptr, 0);
     if (pc) {
-      UFG_TRY(pc_apply(S, f, prec, V.r, V.z, false));
+      UFG_TRY(pc_apply_q(S, f, prec, V.r, V.z));
       VEC(prec, V_DOT, n, V.r, V.z, nullptr, nullptr, nullptr, nullptr, slot(S, P_PC), &npc);
       SCALAR(OP_CG_BETA, slot(S, P_PC), npc, nullptr, 0);
     } else {
@@ -594,6 +683,18 @@ ufg_status run_cg(ufg_solver* S, ufg_field* f, int prec, double tol, int maxit, 
     S->counts.Mdag += (long long)S->pc.degree * it_pc;
   }
   if (S->pc_kind == UFG_PC_SCA) S->counts.sca += it_pc;
+  if (S->pc_kind == UFG_PC_SCA_CHEB) {  // d Q applies and d + 1 sweeps per application
+    S->counts.M += (long long)S->pc.degree * it_pc;
+    S->counts.Mdag += (long long)S->pc.degree * it_pc;
+    S->counts.sca += (long long)(S->pc.degree + 1) * it_pc;
+  }
+  if (S->pc_kind == UFG_PC_WCE) {  // P_d^T then P_d per application
+    const long long d = S->pc.order;
+    S->counts.M0invT += (d + 1) * it_pc;
+    S->counts.M0inv += (d + 1) * it_pc;
+    S->counts.M1T += d * it_pc;
+    S->counts.M1 += d * it_pc;
+  }
   return UFG_OK;
 }
 
@@ -697,6 +798,35 @@ ufg_status norm64(ufg_solver* S, const double* v, long long n, double* out) {
   *out = std::sqrt(*S->red_host);
   return UFG_OK;
 }
+
+// Spectral scale of G = P_S Q for UFG_PC_SCA_CHEB: 30 power steps v <- G v / |v| from the potential
+// w = 1 + A sin(sigma) (FP64), lambda ~ |G v| / |v|, stored as 1.1 lambda on the field.
+ufg_status sca_cheb_estimate(ufg_solver* S, ufg_field* f) {
+  VecSet& V = S->vs[0];
+  const long long n = f->lat->S;
+  UFG_TRY(write_scalars(S, 0.0, 0));
+  UFG_CUDA(cudaMemcpyAsync(V.s, f->w64, n * sizeof(double), cudaMemcpyDeviceToDevice, S->st));
+  double vn = 0.0, lam = 0.0;
+  UFG_TRY(norm64(S, (const double*)V.s, n, &vn));
+  void* v = V.s;
+  void* g = V.y;
+  for (int it = 0; it < 30; ++it) {
+    UFG_TRY(apply_op(S, f, 0, OPK_Q, v, V.t, 1.0, nullptr, 0.0, nullptr, false, nullptr,
+                     nullptr));
+    UFG_TRY(sca_sweep(S, f, 0, V.t, g, 1.0 / vn, nullptr, 0.0, nullptr, 0.0));
+    UFG_TRY(norm64(S, (const double*)g, n, &lam));
+    vn = lam;
+    std::swap(v, g);
+  }
+  if (!(lam > 0) || !std::isfinite(lam)) {
+    set_error("SCA + Chebyshev: spectral estimate failed (%g)", lam);
+    return UFG_NONFINITE;
+  }
+  f->gcheb_scale = 1.1 * lam;
+  f->gcheb_alpha = S->pc.alpha;
+  return UFG_OK;
+}
+
 
 // r64 = rhs - A x (FP64), returns ||r64||.
 ufg_status residual64(ufg_solver* S, ufg_field* f, int op, const double* x, const double* rhs,
@@ -874,8 +1004,13 @@ double paper_mv(const ufg_solver* S, int iters, bool bicg) {
     if (S->pc_kind == UFG_PC_WCE) return iters * 2.0 * (S->pc.order + 1) * 3.0;
     return iters * 2.0;
   }
+  // CG + two-sided WCE: Q (2 MV) and P_d^T, P_d (each d M1 + (d+1) M0^{-1} of 2 beta MV): the
+  // BiCGStab count 2(d+1)(1+2 beta) again
+  if (S->pc_kind == UFG_PC_WCE) return iters * 2.0 * (S->pc.order + 1) * 3.0;
   if (S->pc_kind == UFG_PC_CHEB) return iters * 2.0 * (S->pc.degree + 1);
   if (S->pc_kind == UFG_PC_SCA) return iters * 3.0;
+  // SCA + Chebyshev: Q (2 MV), d Q applies (2d MV) and d + 1 SCA sweeps (~1 MV each, Sec. 5)
+  if (S->pc_kind == UFG_PC_SCA_CHEB) return iters * 3.0 * (S->pc.degree + 1);
   return iters * 2.0;
 }
 
@@ -896,6 +1031,14 @@ void fill_stats(ufg_stats* st, ufg_solver* S, const SolveOut& o, double rel, dou
   st->mv_paper = paper_mv(S, o.iters, bicg);
   st->true_residual = rel;
   st->seconds = secs;
+}
+
+// Bounded device waits that ran out during the call (flags of the solver's and the field's
+// lattices): UFG_TIMEOUT, else UFG_OK.  Synchronises the solver stream.
+ufg_status device_flags(ufg_solver* S, const ufg_field* f) {
+  UFG_TRY(check_device_flag(S->lat, S->st));
+  if (f->lat != S->lat) UFG_TRY(check_device_flag(f->lat, S->st));
+  return UFG_OK;
 }
 
 ufg_status check_solve_args(ufg_solver* S, ufg_field* f, const void* b, const void* x,
@@ -1038,6 +1181,7 @@ void ufg_solver_destroy(ufg_solver* S) {
   dev_free(S->xs64);
   dev_free(S->xf64);
   dev_free(S->x0s64);
+  dev_free(S->hmc64);
   dev_free(S->mb64);
   dev_free(S->mx64);
   dev_free(S->parts);
@@ -1064,25 +1208,24 @@ ufg_status ufg_set_preconditioner(ufg_solver* S, int kind, const ufg_pc_params* 
     set_error("null preconditioner parameters");
     return UFG_INVALID_ARG;
   }
-  if (kind == UFG_PC_CHEB && (p->degree < 2 || p->degree > 64 || p->degree % 2 ||
-                              p->eps >= 1.0 || !(std::isfinite(p->scale)))) {
+  if ((kind == UFG_PC_CHEB || kind == UFG_PC_SCA_CHEB) &&
+      (p->degree < 2 || p->degree > 64 || p->degree % 2 || p->eps >= 1.0 ||
+       !(std::isfinite(p->scale)))) {
     set_error("Chebyshev: need an even degree in 2..64 and eps < 1");
     return UFG_INVALID_ARG;
   }
-  if (kind == UFG_PC_SCA && !(p->alpha > 0)) {
+  if ((kind == UFG_PC_SCA || kind == UFG_PC_SCA_CHEB) && !(p->alpha > 0)) {
     set_error("SCA: alpha must be > 0");
     return UFG_INVALID_ARG;
   }
-  if (kind == UFG_PC_WCE && (p->order < 0 || p->order > 16)) {
-    set_error("WCE: order must be in 0..16");
-    return UFG_INVALID_ARG;
-  }
-  if (kind < UFG_PC_NONE || kind > UFG_PC_WCE) {
+  if (kind < UFG_PC_NONE || kind > UFG_PC_SCA_CHEB) {
     set_error("unknown preconditioner kind %d", kind);
     return UFG_INVALID_ARG;
   }
+  ufg_pc_params q;
+  UFG_TRY(normalize_pc(kind, p, &q));
   S->pc_kind = kind;
-  S->pc = *p;
+  S->pc = q;
   return UFG_OK;
 }
 
@@ -1097,6 +1240,7 @@ ufg_status ufg_apply_preconditioner(ufg_solver* S, ufg_field* f, const void* r, 
   CallGuard g(S, as_stream(stream));
   UFG_TRY(write_scalars(S, 0.0, 0));
   UFG_TRY(pc_prepare(S, f));
+  if (transpose == 2) return pc_apply_q(S, f, precision, r, z);
   return pc_apply(S, f, precision, r, z, transpose != 0);
 }
 
@@ -1155,10 +1299,6 @@ ufg_status ufg_solve_cg_normal(ufg_solver* S, ufg_field* f, const double* b, dou
                                const ufg_params* p, ufg_stats* stats, void* stream) {
   clear_error();
   UFG_TRY(check_solve_args(S, f, b, x, p));
-  if (S->pc_kind == UFG_PC_WCE) {
-    set_error("CG on the normal equations takes the Chebyshev or SCA preconditioner");
-    return UFG_INVALID_ARG;
-  }
   ufg_params tuned;
   if (p->precision == UFG_MIXED && p->inner_tol < 0) {
     tuned = *p;
@@ -1185,6 +1325,7 @@ ufg_status ufg_solve_cg_normal(ufg_solver* S, ufg_field* f, const double* b, dou
     set_error("recursive residual converged but the true residual %.3e exceeds tol", rel);
     st = UFG_NOT_CONVERGED;
   }
+  if (const ufg_status fs = device_flags(S, f); fs != UFG_OK) st = fs;
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   fill_stats(stats, S, o, rel, secs, false, st);
   if (stats) {
@@ -1199,7 +1340,7 @@ ufg_status ufg_solve_bicgstab_two_step(ufg_solver* S, ufg_field* f, const double
                                        const ufg_params* p, ufg_stats* stats, void* stream) {
   clear_error();
   UFG_TRY(check_solve_args(S, f, b, x, p));
-  if (S->pc_kind == UFG_PC_CHEB || S->pc_kind == UFG_PC_SCA) {
+  if (S->pc_kind == UFG_PC_CHEB || S->pc_kind == UFG_PC_SCA || S->pc_kind == UFG_PC_SCA_CHEB) {
     set_error("two-step BiCGStab takes the weak-coupling preconditioner (or none)");
     return UFG_INVALID_ARG;
   }
@@ -1259,6 +1400,7 @@ ufg_status ufg_solve_bicgstab_two_step(ufg_solver* S, ufg_field* f, const double
               extra);
     st = UFG_NOT_CONVERGED;
   }
+  if (const ufg_status fs = device_flags(S, f); fs != UFG_OK) st = fs;
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   fill_stats(stats, S, o, rel, secs, true, st);
   if (stats) {
@@ -1327,7 +1469,121 @@ ufg_status ufg_hmc_force(ufg_solver* S, ufg_field* f, const double* phi, double*
     UFG_CUDA(cudaStreamSynchronize(S->st));
     *S_out = *S->red_host;
   }
-  if (dS) UFG_TRY(ufg_force_from_solution(S, f, X, dS, 1.0, stream));
+  if (dS) {
+    UFG_TRY(ufg_force_from_solution(S, f, X, dS, 1.0, stream));
+    CallGuard g(S, as_stream(stream));
+    UFG_TRY(device_flags(S, f));
+  }
+  return st;
+}
+
+// ---- HMC trajectory (Sec. 1, the phi-algorithm) --------------------------------------------
+namespace {
+
+// y += a x (FP64), the molecular-dynamics updates of sigma and pi
+__global__ void hmc_axpy_kernel(double* __restrict__ y, const double* __restrict__ x, double a,
+                                long long n) {
+  ufg::pdl_begin();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+
+ufg_status hmc_axpy(ufg_solver* S, double* y, const double* x, double a) {
+  const long long n = S->lat->S;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  hmc_axpy_kernel<<<(unsigned)blocks, 256, 0, S->st>>>(y, x, a, n);
+  note_launches(1);
+  UFG_CUDA(cudaGetLastError());
+  return UFG_OK;
+}
+
+}  // namespace
+
+ufg_status ufg_hmc_trajectory(ufg_solver* S, ufg_field* f, const double* eta, const double* pi0,
+                              double u, int n_steps, double dt, const ufg_params* p,
+                              double* sigma_out, double* pi_out, ufg_hmc_stats* stats,
+                              void* stream) {
+  clear_error();
+  if (!S || !f || !eta || !pi0 || !p || n_steps < 1 || !(dt > 0) || !std::isfinite(dt) ||
+      !(u >= 0.0 && u < 1.0)) {
+    set_error("hmc_trajectory: need solver, field, eta, pi0, params, n_steps >= 1, dt > 0 and "
+              "0 <= u < 1");
+    return UFG_INVALID_ARG;
+  }
+  if (f->lat->nx != S->lat->nx || f->lat->ntau != S->lat->ntau) {
+    set_error("field and solver belong to different lattices");
+    return UFG_INVALID_ARG;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  const long long n = S->lat->S;
+  if (S->hmc64 == nullptr) UFG_TRY(dev_alloc(&S->hmc64, (size_t)(5 * n)));
+  double* sig0 = S->hmc64;
+  double* sig = sig0 + n;
+  double* pi = sig + n;
+  double* phi = pi + n;
+  double* F = phi + n;
+  ufg_hmc_stats hs;
+  std::memset(&hs, 0, sizeof(hs));
+  ufg_status st = UFG_OK;
+  {
+    CallGuard g(S, as_stream(stream));
+    UFG_CUDA(cudaMemcpyAsync(sig0, f->sigma, n * sizeof(double), cudaMemcpyDeviceToDevice, S->st));
+    UFG_CUDA(cudaMemcpyAsync(sig, f->sigma, n * sizeof(double), cudaMemcpyDeviceToDevice, S->st));
+    UFG_CUDA(cudaMemcpyAsync(pi, pi0, n * sizeof(double), cudaMemcpyDefault, S->st));
+    // heat bath of the pseudofermions: phi = M^T eta, so that S_p = |eta|^2 at the start
+    UFG_TRY(op_Mdag(f, 0, eta, phi, S->st));
+    UFG_TRY(norm64(S, pi, n, &hs.H_old));
+    hs.H_old = 0.5 * hs.H_old * hs.H_old;
+  }
+  void* sv = S->st;  // the library's calls below order themselves on the solver stream
+  ufg_stats ss;
+  auto force = [&](double* action) -> ufg_status {
+    const ufg_status fs = ufg_hmc_force(S, f, phi, F, nullptr, action, p, &ss, sv);
+    ++hs.force_solves;
+    hs.iterations += ss.iterations;
+    if (fs != UFG_OK) {
+      set_error("hmc_trajectory: force solve %d ended with status %d (%s)", hs.force_solves, fs,
+                ufg_last_error());
+      return fs;
+    }
+    return UFG_OK;
+  };
+  // leapfrog: half step in pi, n_steps full steps in sigma with full pi steps between them, and
+  // a final half step in pi (time-reversible and symplectic)
+  st = force(&hs.action_old);
+  if (st == UFG_OK) {
+    hs.H_old += hs.action_old;
+    UFG_TRY(hmc_axpy(S, pi, F, -0.5 * dt));
+    for (int k = 1; k <= n_steps && st == UFG_OK; ++k) {
+      UFG_TRY(hmc_axpy(S, sig, pi, dt));
+      UFG_TRY(ufg_field_update(f, sig, sv));
+      st = force(k == n_steps ? &hs.action_new : nullptr);
+      if (st == UFG_OK) UFG_TRY(hmc_axpy(S, pi, F, k == n_steps ? -0.5 * dt : -dt));
+      ++hs.md_steps;
+    }
+  }
+  if (st == UFG_OK) {
+    double pn = 0.0;
+    UFG_TRY(norm64(S, pi, n, &pn));
+    hs.H_new = 0.5 * pn * pn + hs.action_new;
+    hs.dH = hs.H_new - hs.H_old;
+    // Metropolis: accept with probability min(1, exp(-dH))
+    hs.accepted = std::isfinite(hs.dH) && (hs.dH <= 0.0 || u < std::exp(-hs.dH)) ? 1 : 0;
+  }
+  if (!hs.accepted) UFG_TRY(ufg_field_update(f, sig0, sv));  // back to the old configuration
+  {
+    CallGuard g(S, as_stream(stream));
+    if (sigma_out)
+      UFG_CUDA(cudaMemcpyAsync(sigma_out, f->sigma, n * sizeof(double), cudaMemcpyDefault,
+                               S->st));
+    if (pi_out) UFG_CUDA(cudaMemcpyAsync(pi_out, pi, n * sizeof(double), cudaMemcpyDefault, S->st));
+    UFG_CUDA(cudaStreamSynchronize(S->st));
+  }
+  hs.status = st;
+  hs.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = hs;
   return st;
 }
 

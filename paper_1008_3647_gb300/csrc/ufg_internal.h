@@ -81,6 +81,13 @@ double slice_bytes_per_problem(const SliceCall& c, int N);
 bool line_coef_flat(int N, const std::vector<double>& ce, const std::vector<double>& co,
                     bool in_spec, bool out_spec, std::vector<double>& flat);
 
+// Weights c_0..c_d of the weak-coupling series under the acceleration `accel` (ufg_accel) with
+// Euler parameter p and van Wijngaarden parameter s (Sec. 3.1); false on invalid arguments.
+bool wce_series_weights(int d, int accel, double p, double s, std::vector<double>& c);
+// Validated copy of preconditioner parameters with the defaults applied (euler_p 0 -> 1/2,
+// vw_s 0 -> 1); UFG_INVALID_ARG with a message otherwise.
+ufg_status normalize_pc(int kind, const ufg_pc_params* in, ufg_pc_params* out);
+
 // ---- small device buffers -----------------------------------------------------------------
 template <typename T>
 ufg_status dev_alloc(T** p, size_t n) {
@@ -117,12 +124,22 @@ cudaError_t launch_recurrence_batch(int prec, const void* in, void* out, const v
 // Strong-coupling factors (per site, sequential in t) and apply.
 cudaError_t launch_sca_setup(const double* w64, long long V, int ntau, double alpha, double* L64,
                              double* Di64, float* L32, float* Di32, cudaStream_t st);
+// z = a (L^T D L)^{-1} y + bU U + cV W (U, W nullable and not aliasing z).
 cudaError_t launch_sca_apply(int prec, const void* L, const void* Di, const void* y, void* z,
-                             long long V, int ntau, const int* done, cudaStream_t st);
+                             long long V, int ntau, const int* done, cudaStream_t st,
+                             double a = 1.0, const void* U = nullptr, double bU = 0.0,
+                             const void* W = nullptr, double cV = 0.0);
 
 }  // namespace ufg
 
 // ---- handles ------------------------------------------------------------------------------
+struct ufg_lattice;
+namespace ufg {
+// Reads (synchronising st) and clears the lattice's device flag of bounded waits; UFG_TIMEOUT with
+// a message if a wait of a kernel launched since the last check ran out.
+ufg_status check_device_flag(const ufg_lattice* lat, cudaStream_t st);
+}  // namespace ufg
+
 struct ufg_lattice {
   int nx = 0, ntau = 0, dispersion = 0;
   double tau = 0, g = 0, A = 0;
@@ -140,6 +157,9 @@ struct ufg_lattice {
 
 struct ufg_field {
   const ufg_lattice* lat = nullptr;
+  // process-unique identity: captured solver graphs are cached per field, and a field created
+  // after another was destroyed may get the same host address but different device buffers
+  unsigned long long id = 0;
   double* sigma = nullptr;
   double* w64 = nullptr;
   double* s64 = nullptr;
@@ -150,6 +170,8 @@ struct ufg_field {
   double* tmp64 = nullptr;  // apply workspace (Q intermediate, momentum-space temp)
   float* tmp32 = nullptr;
   double sca_alpha = -1.0;  // alpha the SCA tables were built for (< 0: none)
+  double gcheb_alpha = -1.0;  // alpha of the spectral estimate of (L^T D L)^{-1} Q (< 0: none)
+  double gcheb_scale = 0.0;
   double* L64 = nullptr;
   double* Di64 = nullptr;
   float* L32 = nullptr;

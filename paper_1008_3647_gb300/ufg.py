@@ -22,8 +22,9 @@ STATUS_NAMES = {0: "UFG_OK", 1: "UFG_INVALID_ARG", 2: "UFG_NOT_CONVERGED", 3: "U
                 4: "UFG_NONFINITE", 5: "UFG_TIMEOUT", 6: "UFG_CUDA_ERROR", 7: "UFG_OOM",
                 8: "UFG_INTERNAL", 9: "UFG_UNSUPPORTED"}
 UFG_FP64, UFG_FP32, UFG_MIXED = 0, 1, 2
-UFG_PC_NONE, UFG_PC_CHEB, UFG_PC_SCA, UFG_PC_WCE = 0, 1, 2, 3
-PC_KINDS = {"none": UFG_PC_NONE, "cheb": UFG_PC_CHEB, "sca": UFG_PC_SCA, "wce": UFG_PC_WCE}
+UFG_PC_NONE, UFG_PC_CHEB, UFG_PC_SCA, UFG_PC_WCE, UFG_PC_SCA_CHEB = 0, 1, 2, 3, 4
+PC_KINDS = {"none": UFG_PC_NONE, "cheb": UFG_PC_CHEB, "sca": UFG_PC_SCA, "wce": UFG_PC_WCE,
+            "sca_cheb": UFG_PC_SCA_CHEB}
 
 
 class UfgError(RuntimeError):
@@ -34,7 +35,13 @@ class UfgError(RuntimeError):
 
 class PcParams(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int), ("eps", ctypes.c_double), ("scale", ctypes.c_double),
-                ("alpha", ctypes.c_double), ("order", ctypes.c_int), ("euler", ctypes.c_int)]
+                ("alpha", ctypes.c_double), ("order", ctypes.c_int), ("euler", ctypes.c_int),
+                ("euler_p", ctypes.c_double), ("vw_s", ctypes.c_double)]
+
+
+UFG_ACCEL_NONE, UFG_ACCEL_EULER, UFG_ACCEL_EULER23, UFG_ACCEL_VANW = 0, 1, 2, 3
+ACCEL = {False: 0, True: 1, 0: 0, 1: 1, 2: 2, 3: 3, "none": 0, "euler": 1, "euler23": 2,
+         "vanw": 3}
 
 
 class Params(ctypes.Structure):
@@ -60,6 +67,19 @@ class Stats(ctypes.Structure):
         return d
 
 
+class HmcStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("accepted", ctypes.c_int), ("md_steps", ctypes.c_int),
+                ("force_solves", ctypes.c_int), ("iterations", ctypes.c_longlong),
+                ("H_old", ctypes.c_double), ("H_new", ctypes.c_double), ("dH", ctypes.c_double),
+                ("action_old", ctypes.c_double), ("action_new", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
+        return d
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 64), ("launches", ctypes.c_longlong),
                 ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
@@ -80,11 +100,14 @@ _SIGS = {
     "ufg_supported_nx": (ctypes.c_char_p, []),
     "ufg_kernel_launches": (ctypes.c_longlong, []),
     "ufg_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "ufg_measure_fma_rate": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double)]),
     "ufg_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ufg_lattice_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp)]),
     "ufg_lattice_destroy": (None, [_vp]),
     "ufg_lattice_coupling": (ctypes.c_double, [_vp]),
+    "ufg_lattice_check": (ctypes.c_int, [_vp, _vp]),
+    "ufg_test_expire_waits": (None, [ctypes.c_int]),
     "ufg_lattice_autotune": (ctypes.c_int, [_vp, _vp]),
     "ufg_lattice_launch_shape": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                 ctypes.POINTER(ctypes.c_int)]),
@@ -113,6 +136,9 @@ _SIGS = {
     "ufg_hmc_force": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(Params), ctypes.POINTER(Stats), _vp]),
     "ufg_force_from_solution": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, _vp]),
+    "ufg_hmc_trajectory": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_double, ctypes.POINTER(Params), _vp, _vp,
+                                          ctypes.POINTER(HmcStats), _vp]),
     "ufg_solve_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
                                        ctypes.POINTER(PcParams), ctypes.POINTER(Params),
                                        ctypes.POINTER(Stats), _vp]),
@@ -152,6 +178,13 @@ def ufg_profile_enable(on=True):
     """Per-kernel CUDA-event timing of the library's launches (direct launches, no graph replay)
     until disabled; enabling clears earlier records."""
     _check(load().ufg_profile_enable(1 if on else 0))
+
+
+def ufg_measure_fma_rate(precision=UFG_FP64):
+    """Measured FMA throughput of the current GPU in TFLOP/s (FP64 or FP32)."""
+    v = ctypes.c_double(0.0)
+    _check(load().ufg_measure_fma_rate(precision, _stream(), ctypes.byref(v)))
+    return v.value
 
 
 def ufg_profile_read():
@@ -213,6 +246,11 @@ class Lattice:
     def ufg_lattice_autotune(self):
         _check(load().ufg_lattice_autotune(self._h, _stream()))
         return {p: self.ufg_lattice_launch_shape(p) for p in (UFG_FP64, UFG_FP32)}
+
+    def ufg_lattice_check(self):
+        """Synchronises the current stream and raises UfgError(UFG_TIMEOUT) if a bounded device
+        wait of a kernel launched on this lattice since the last check ran out."""
+        _check(load().ufg_lattice_check(self._h, _stream()))
 
     def ufg_lattice_launch_shape(self, precision=UFG_FP32):
         c, s = ctypes.c_int(0), ctypes.c_int(0)
@@ -309,8 +347,12 @@ def ufg_apply_M_momentum(field, x, transpose=False, y=None):
     return _apply_flag("ufg_apply_M_momentum", field, x, transpose, y)
 
 
-def _pc_params(kind, degree=16, eps=0.0, scale=0.0, alpha=2.0, order=2, euler=False):
-    return PC_KINDS[kind], PcParams(degree, eps, scale, alpha, order, int(bool(euler)))
+def _pc_params(kind, degree=16, eps=0.0, scale=0.0, alpha=2.0, order=2, euler=False, p=0.5,
+               s=1.0):
+    """euler: False/True, 0..3 or "none" / "euler" / "euler23" / "vanw" (ufg_accel); p: Euler
+    parameter; s: van Wijngaarden parameter."""
+    accel = ACCEL[euler] if euler in ACCEL else int(euler)  # unknown values: the library rejects
+    return PC_KINDS[kind], PcParams(degree, eps, scale, alpha, order, accel, p, s)
 
 
 def _params(tol=1e-10, maxit=20000, precision=UFG_FP64, x0_given=False, inner_tol=1e-5,
@@ -337,11 +379,12 @@ class Solver:
         _check(load().ufg_set_preconditioner(self._h, k, ctypes.byref(p)))
 
     def ufg_apply_preconditioner(self, field, r, z=None, transpose=False):
+        """transpose: False / 0 -> P, True / 1 -> P^T, 2 -> the CG (normal-equation) form."""
         _vec(r, self.lattice.shape)
         z = torch.empty_like(r) if z is None else z
         prec = UFG_FP64 if r.dtype == torch.float64 else UFG_FP32
         _check(load().ufg_apply_preconditioner(self._h, field._h, _ptr(r), _ptr(z),
-                                               int(bool(transpose)), prec, _stream()))
+                                               int(transpose), prec, _stream()))
         return z
 
     def _solve(self, name, field, b, x, kw):
@@ -386,6 +429,23 @@ class Solver:
                                               _stream()))
         return dS
 
+    def ufg_hmc_trajectory(self, field, eta, pi0, u, n_steps, dt, **kw):
+        """One HMC trajectory (heat bath phi = M^T eta, leapfrog, Metropolis against u);
+        returns (sigma, pi, stats) with sigma the field's configuration afterwards."""
+        shape = self.lattice.shape
+        for t in (eta, pi0):
+            _vec(t, shape, (torch.float64,))
+        p = _params(**kw)
+        st = HmcStats()
+        sigma = torch.empty_like(eta)
+        pi = torch.empty_like(eta)
+        status = load().ufg_hmc_trajectory(self._h, field._h, _ptr(eta), _ptr(pi0), float(u),
+                                           int(n_steps), float(dt), ctypes.byref(p), _ptr(sigma),
+                                           _ptr(pi), ctypes.byref(st), _stream())
+        if status not in (UFG_OK, UFG_NOT_CONVERGED, UFG_BREAKDOWN, UFG_NONFINITE):
+            _check(status)
+        return sigma, pi, st.as_dict()
+
     def ufg_pseudofermion_action(self, field, phi, **kw):
         """(S, X): S = phi^T Q^{-1} phi and X = Q^{-1} phi from ufg_hmc_force without the force."""
         lib = load()
@@ -398,6 +458,12 @@ class Solver:
         if status not in (UFG_OK, UFG_NOT_CONVERGED):
             _check(status)
         return S.value, X, st.as_dict()
+
+
+def ufg_test_expire_waits(launches):
+    """Test hook: the next `launches` TMA-staged slice launches each run one bounded wait that is
+    made to run out (results stay correct; the status becomes UFG_TIMEOUT)."""
+    load().ufg_test_expire_waits(int(launches))
 
 
 def ufg_batch_cache_clear():
@@ -417,8 +483,8 @@ def ufg_solve_batch(problems, pc_kind="wce", pc=None, **kw):
     stats = (Stats * len(problems))()
     status = lib.ufg_solve_batch(len(problems), arr, k, ctypes.byref(pcp), ctypes.byref(p), stats,
                                  _stream())
-    if status not in (UFG_OK, UFG_NOT_CONVERGED):
-        _check(status)
+    if status not in (UFG_OK, UFG_NOT_CONVERGED, UFG_BREAKDOWN, UFG_NONFINITE):
+        _check(status)  # per-problem outcomes are in the returned stats
     return [s.as_dict() for s in stats]
 
 

@@ -99,6 +99,62 @@ def test_force_full_size_32cubed_x512(ufg):
     assert float(np.abs(dS.cpu().numpy() - ref).max() / np.abs(ref).max()) < 1e-12
 
 
+def test_force_full_size_central_differences(ufg):
+    # Config 5 in full: dS/dsigma on 64 seeded sites of the 32^3 x 512 lattice against central
+    # differences [S(sigma + h e_i) - S(sigma - h e_i)] / 2h of S = phi^T Q^{-1} phi.  S itself is
+    # extensive (|eta|^2 ~ 1.7e7), so the difference of two separately solved actions cancels
+    # ~10 digits; it is evaluated instead as the exact identity
+    #   S+ - S- = phi^T (Q+^{-1} - Q-^{-1}) phi = X+^T (Q- - Q+) X-,   X+- = Q+-^{-1} phi,
+    # with M+ = M- + D, D x = -sgn K(dw x_t(r) e_r) on slice t+1 (+ at the antiperiodic wrap),
+    # dw = A (sin(sigma+h) - sin(sigma-h)) = 2 A cos(sigma) sin(h):
+    #   X+^T (Q- - Q+) X- = -[(M- X+).(D X-) + (D X+).(M- X-) + (D X+).(D X-)],
+    # every term a product with the localised vector D X, so nothing cancels.
+    nx, ntau = 32, 512
+    V = nx ** 3
+    sigma, eta = field_and_source(nx, ntau, 51)
+    lat = ufg.Lattice(nx, ntau)
+    solver = ufg.Solver(lat)
+    solver.ufg_set_preconditioner("wce", order=2)
+    sig = torch.from_numpy(sigma).cuda()
+    field = ufg.Field(lat, sig)
+    phi = ufg.ufg_apply_Mdag(field, torch.from_numpy(eta).cuda())
+    kw = {"tol": 1e-12, "precision": ufg.UFG_MIXED}
+    dS, _, _, st = solver.ufg_hmc_force(field, phi, **kw)
+    assert st["status"] == ufg.UFG_OK, st
+    dS = dS.view(-1)
+    h = 1e-4  # central-difference truncation ~h^2/6 relative
+    fp, fm = ufg.Field(lat, sig), ufg.Field(lat, sig)
+    zero = torch.zeros(lat.shape, dtype=torch.float64, device="cuda")
+
+    def D(X, t, r, dw):
+        u = zero.clone()
+        u.view(ntau, V)[t, r] = dw * X.view(ntau, V)[t, r]
+        Ku = ufg.ufg_apply_kinetic(field, u).view(ntau, V)
+        out = zero.clone().view(ntau, V)
+        out[(t + 1) % ntau] = (-1.0 if t < ntau - 1 else 1.0) * Ku[t]
+        return out.view(lat.shape)
+
+    worst = 0.0
+    for i in sample_sites(lat.shape, 64, 7):
+        t, r = divmod(int(i), V)
+        sp, sm = sig.clone().view(-1), sig.clone().view(-1)
+        sp[i] += h
+        sm[i] -= h
+        fp.update(sp.view(lat.shape))
+        fm.update(sm.view(lat.shape))
+        _, Xp, s1 = solver.ufg_pseudofermion_action(fp, phi, **kw)
+        _, Xm, s2 = solver.ufg_pseudofermion_action(fm, phi, **kw)
+        assert s1["status"] == ufg.UFG_OK and s2["status"] == ufg.UFG_OK
+        dw = 2.0 * lat.A * np.cos(float(sigma.reshape(-1)[i])) * np.sin(h)
+        DXp, DXm = D(Xp, t, r, dw), D(Xm, t, r, dw)
+        MXp, MXm = ufg.ufg_apply_M(fm, Xp), ufg.ufg_apply_M(fm, Xm)
+        delta = -float((MXp * DXm).sum() + (DXp * MXm).sum() + (DXp * DXm).sum())
+        fd = delta / (2 * h)
+        err = abs(float(dS[i]) - fd) / max(abs(fd), 1e-3 * float(dS.abs().max()))
+        worst = max(worst, err)
+    assert worst < 1e-6, worst
+
+
 def test_autograd_backward_is_force(ufg):
     nx, ntau = 6, 10
     sigma, eta = field_and_source(nx, ntau, 44)

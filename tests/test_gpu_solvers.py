@@ -59,11 +59,27 @@ METHODS = {
     "bicg_wce4": ("bicg", "wce", {"order": 4}),
     "bicg_wce2_euler": ("bicg", "wce", {"order": 2, "euler": True}),
     "bicg_wce4_euler": ("bicg", "wce", {"order": 4, "euler": True}),
+    "bicg_wce2_euler23": ("bicg", "wce", {"order": 2, "euler": "euler23"}),
+    "bicg_wce4_euler23": ("bicg", "wce", {"order": 4, "euler": "euler23"}),
+    "bicg_wce2_vanw": ("bicg", "wce", {"order": 2, "euler": "vanw", "s": 1.0}),
+    "bicg_wce4_vanw": ("bicg", "wce", {"order": 4, "euler": "vanw", "s": 1.0}),
+    "cg_wce0": ("cg", "wce", {"order": 0}),
+    "cg_wce2": ("cg", "wce", {"order": 2}),
+    "cg_wce2_euler23": ("cg", "wce", {"order": 2, "euler": "euler23"}),
+    "cg_scacheb8": ("cg", "sca_cheb", {"alpha": 2.0, "degree": 8}),
+    "cg_scacheb16": ("cg", "sca_cheb", {"alpha": 2.0, "degree": 16}),
+    "cg_sca1.5": ("cg", "sca", {"alpha": 1.5}),
+    "cg_sca3": ("cg", "sca", {"alpha": 3.0}),
+    "cg_sca4": ("cg", "sca", {"alpha": 4.0}),
 }
+# the ten seeded configurations of the stored oracle counts for the cheap methods, three for the
+# slow ones (thousands of iterations)
+SLOW = {"cg_none", "bicg_none", "cg_sca1.5", "cg_sca2", "cg_sca3", "cg_sca4", "cg_wce0", "cg_wce2",
+        "cg_wce2_euler23"}
+CASES = [(m, sd) for m in METHODS for sd in (range(3) if m in SLOW else range(10))]
 
 
-@pytest.mark.parametrize("method", list(METHODS))
-@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("method,seed", CASES)
 def test_8x64_fp64_matches_oracle(ufg, method, seed):
     gold = json.load(open(GOLD))
     ref = gold["runs"]["%s/%d" % (method, seed)]
@@ -76,9 +92,9 @@ def test_8x64_fp64_matches_oracle(ufg, method, seed):
     solver.ufg_set_preconditioner(pc, **kw)
     fn = solver.ufg_solve_cg_normal if kind == "cg" else solver.ufg_solve_bicgstab_two_step
     x, st = fn(field, torch.from_numpy(b).cuda(), tol=1e-10)
-    if not ref["converged"]:
-        # unpreconditioned BiCGStab on M breaks down again and again; the oracle exhausted its
-        # restarts.  The GPU may do the same or, with different rounding, get through.
+    if not ref["converged"] or method == "bicg_none":
+        # unpreconditioned BiCGStab on M breaks down again and again; whether the restart budget
+        # runs out first depends on rounding (the oracle and the GPU may end either way)
         assert st["status"] in (ufg.UFG_OK, ufg.UFG_BREAKDOWN, ufg.UFG_NOT_CONVERGED), st
         if st["status"] != ufg.UFG_OK:
             return
@@ -207,8 +223,8 @@ def test_wrong_preconditioner_for_solver_rejected(ufg):
     sigma, b = field_and_source(4, 8, 0)
     field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
     solver = ufg.Solver(lat)
-    solver.ufg_set_preconditioner("wce", order=1)
-    with pytest.raises(ufg.UfgError):
-        solver.ufg_solve_cg_normal(field, torch.from_numpy(b).cuda())
+    solver.ufg_set_preconditioner("cheb", degree=8)
+    with pytest.raises(ufg.UfgError):  # Chebyshev and SCA precondition M^T M, not M
+        solver.ufg_solve_bicgstab_two_step(field, torch.from_numpy(b).cuda())
     with pytest.raises(ufg.UfgError):
         solver.ufg_set_preconditioner("cheb", degree=7)
