@@ -352,6 +352,21 @@ def run_ufg(args, rank, world, local_rank):
     t_cheb = timed(1, lambda: cheb_box.__setitem__("st", step(ufg.UFG_MIXED, kind="cg")),
                    "step_cg_cheb16")
 
+    # the same step with the order-2 series accelerated by Euler's S_{2k/3,k/3} (Sec. 3.1)
+    def step_euler23():
+        stats = ufg.ufg_solve_batch(probs_d, "wce", {"order": 2, "euler": "euler23"}, tol=TOL,
+                                    precision=ufg.UFG_MIXED, check_every=8)
+        if any(st["status"] != ufg.UFG_OK for st in stats):
+            raise RuntimeError("batched solve failed: %s" % stats)
+        return stats
+    step_euler23()
+    e23_box = {}
+    t_e23 = timed(max(1, min(args.steps, 3)),
+                  lambda: e23_box.__setitem__("st", step_euler23()), "step_wce2_euler23")
+    n_e23 = max(1, min(args.steps, 3))
+    # one HMC trajectory (Sec. 1) on the 16^3 x 256 lattice: heat bath, 8 leapfrog steps of 0.01,
+    # Metropolis; mixed-precision forces with WCE2 + Euler S_{2k/3,k/3}
+    hmc = hmc_trajectory_line(ufg, torch, dev)
     # the uneven batch of 96 problems (N_x in {6, 8, 10, 12}, N_tau in {40, 80, 120, 160}, problem i
     # with seed i + 1), mixed and FP64, one timed step each
     from paper_1008_3647_gb300.inputs import batch_shapes
@@ -471,6 +486,13 @@ def run_ufg(args, rank, world, local_rank):
                   "outer_mean": statistics.mean(s["outer_iterations"] for s in sm),
                   "true_residual_max": max(s["true_residual"] for s in sm),
                   "mv_paper_mean": statistics.mean(s["mv_paper"] for s in sm)},
+        "wce2_euler23_mixed": {"value": solves * n_e23 / t_e23, "unit": "solves/s",
+                               "iterations_mean": statistics.mean(s["iterations"]
+                                                                  for s in e23_box["st"]),
+                               "true_residual_max": max(s["true_residual"] for s in e23_box["st"]),
+                               "note": "the headline step with the order-2 series accelerated "
+                                       "by Euler's S_{2k/3,k/3} (Sec. 3.1)"},
+        "hmc_16x256": hmc,
         "batch96": {"value": 96 * world / t96, "unit": "solves/s",
                     "fp64_value": 96 * world / t96_64, "mixed_speedup": t96_64 / t96,
                     "sites": sites96,
@@ -541,6 +563,27 @@ def apply_roofline(ufg, torch, dev, stream, hbm, peak_src):
                   "unit": "TFLOP/s", "frac": ach64 / peak64, "flops_per_site": flops_site,
                   "peak_source": "measured in this run (ufg_measure_fma_rate, FP64 FMA chains)"}
     return out
+
+
+def hmc_trajectory_line(ufg, torch, dev):
+    """One HMC trajectory on 16^3 x 256 (tau = 0.05, g = 5): seeded sigma, eta and pi0, 8 leapfrog
+    steps of 0.01, mixed-precision forces to 1e-10 (WCE2 + Euler S_{2k/3,k/3}), wall time."""
+    from paper_1008_3647_gb300.inputs import field_and_source
+    lat = ufg.Lattice(NX, NTAU)
+    sg, eta = field_and_source(NX, NTAU, 77)
+    pi0 = np.random.default_rng(177).standard_normal(sg.shape)
+    field = ufg.Field(lat, torch.from_numpy(sg).to(dev))
+    solver = ufg.Solver(lat)
+    solver.ufg_set_preconditioner("wce", order=2, euler="euler23")
+    etad, pid = torch.from_numpy(eta).to(dev), torch.from_numpy(pi0).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, st = solver.ufg_hmc_trajectory(field, etad, pid, 0.5, 8, 0.01, tol=1e-10,
+                                         precision=ufg.UFG_MIXED)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "trajectories/s", "md_steps": st["md_steps"],
+            "force_solves": st["force_solves"], "iterations": st["iterations"], "dH": st["dH"],
+            "accepted": st["accepted"], "status": st["status_name"]}
 
 
 def c1_solves(ufg, torch, dev):

@@ -148,9 +148,14 @@ template <int C>
 constexpr int tma_nt() {
   return C == 8 ? 128 : TMA_NT;
 }
+// Resident CTAs per SM of the 8-CTA-cluster kernel (registers: 65536 / (128 x blocks)); a
+// compile-time tuning knob (-DUFG_C8_BLOCKS=n).
+#ifndef UFG_C8_BLOCKS
+#define UFG_C8_BLOCKS 6
+#endif
 template <int N, typename R, int C>
 constexpr int tma_blocks() {
-  return C == 8 ? 6 : tma_min_blocks<N, R>();
+  return C == 8 ? UFG_C8_BLOCKS : tma_min_blocks<N, R>();
 }
 
 // One work unit per CTA (a persistent loop would make the compiler hoist the ~500 line-operator

@@ -88,10 +88,12 @@ def test_mixed_precision_trajectory_16cubed(ufg):
                                          torch.from_numpy(pi0).cuda(), 0.3, 4, 0.02, tol=1e-11,
                                          precision=ufg.UFG_MIXED)
     assert st["status"] == ufg.UFG_OK and st["force_solves"] == 5
-    assert abs(st["dH"]) < 1.0 and st["accepted"] == 1
-    # the end point against the oracle's leapfrog from the same start
+    # the energy error grows with the volume (131,072 sites here); the end point, H and dH
+    # against the oracle's trajectory from the same random numbers
     olat = O.Lattice(nx, ntau)
-    phi = O.apply_Mdag(olat, sigma, eta)
-    s_ref, p_ref, _, _ = O.leapfrog(olat, sigma, pi0, phi, 4, 0.02, tol=1e-12)
+    s_ref, p_ref, info = O.hmc_trajectory(olat, sigma, eta, pi0, 0.3, 4, 0.02, tol=1e-12)
+    assert st["accepted"] == int(info["accepted"])
+    assert st["H_old"] == pytest.approx(info["H_old"], rel=1e-10)
+    assert abs(st["dH"] - info["dH"]) < 1e-4, (st["dH"], info["dH"])
     assert float(np.abs(s.cpu().numpy() - s_ref).max()) < 1e-7
     assert float(np.abs(p.cpu().numpy() - p_ref).max()) < 1e-7

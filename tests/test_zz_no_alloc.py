@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
 from paper_1008_3647_gb300.inputs import field_and_source
 
 pytestmark = pytest.mark.gpu
@@ -36,6 +37,9 @@ def test_noalloc_Q_matches_field_Q_twice(ufg, nx, ntau):
         ufg.ufg_apply_Q_noalloc(nx, ntau, 0.05, 5.0, sd, xd, y)
         torch.cuda.synchronize()
         assert _rel(y, ref) < TOL, (call, _rel(y, ref))
+        # and against the oracle's M^T M directly
+        oref = torch.from_numpy(O.apply_Q(O.Lattice(nx, ntau, 0.05, 5.0), sigma, x))
+        assert _rel(y.cpu(), oref) < TOL, (call, _rel(y.cpu(), oref))
 
 
 def test_noalloc_rejects_lattice_beyond_static_limit(ufg):
