@@ -55,7 +55,12 @@ typedef enum {
   UFG_UNSUPPORTED = 9    /* valid input outside what the library implements (e.g. N_x) */
 } ufg_status;
 
-typedef enum { UFG_FP64 = 0, UFG_FP32 = 1, UFG_MIXED = 2 } ufg_precision;
+/* UFG_FP64_EMULATED: FP64 vectors, arithmetic in double-float pairs on the FP32 pipe (about 46
+ * significant bits; GB300's FP64 pipe is ~1/76 of its FP32 rate).  Accepted by
+ * ufg_apply_M_momentum only.  Its absolute error is about 2^-46 ||M|| ||x||, so a residual
+ * b - M x of a nearly converged, ill-conditioned system (||x|| >> ||b||) is not resolved to
+ * 1e-10 of ||b||: the solvers compute their true residuals in FP64. */
+typedef enum { UFG_FP64 = 0, UFG_FP32 = 1, UFG_MIXED = 2, UFG_FP64_EMULATED = 3 } ufg_precision;
 
 /* UFG_PC_SCA_CHEB: the strong-coupling factorisation with the Chebyshev polynomial as a secondary
  * filter (end of Sec. 4): P = P(G/s)/s (L^T D L)^{-1} with G = (L^T D L)^{-1} Q, for CG. */
@@ -267,7 +272,8 @@ ufg_status ufg_apply_M0invT(ufg_field* f, const void* x, void* y, int precision,
  * ufg_apply_M_momentum: y^ = F M F^T x^ (transpose = 0) or F M^T F^T x^ (transpose = 1), one
  * fused kernel per slice (inverse transform, site multiplier, forward transform, the M0 part of
  * Sec. 3 and the identity).  Built for FP32 N_x = 16 and FP64 N_x = 8, 16; UFG_INVALID_ARG
- * elsewhere.  Same precision, alignment and overlap rules as the applies above. */
+ * elsewhere.  Same precision, alignment and overlap rules as the applies above; precision
+ * UFG_FP64_EMULATED also takes FP64 vectors (double-float arithmetic). */
 ufg_status ufg_fourier(ufg_field* f, const void* x, void* y, int precision, int inverse,
                        void* stream);
 ufg_status ufg_apply_M_momentum(ufg_field* f, const void* x, void* y, int precision,
@@ -304,7 +310,10 @@ ufg_status ufg_solve_bicgstab_two_step(ufg_solver* s, ufg_field* f, const double
                                        const ufg_params* p, ufg_stats* stats, void* stream);
 
 /* HMC force of the pseudofermion action S = phi^T (M^T M)^{-1} phi (Sec. 1): solves
- * X = Q^{-1} phi with the two-step BiCGStab (WCE preconditioner if set) and returns
+ * X = Q^{-1} phi with the two-step BiCGStab (WCE preconditioner if set; should its near-breakdown
+ * persist, CG on M^T M with the Chebyshev preconditioner of degree 16 finishes the solve from the
+ * BiCGStab iterate, and stats then describe that CG solve with the BiCGStab iterations added;
+ * the solver's own preconditioner setting is kept) and returns
  * dS/dsigma_t(r) = 2 A cos sigma_t(r) X_t(r) [exp(-tau K) Y~_{t+1}](r), Y = M X, Y~_{N_tau} = -Y_0
  * (the paper's F with the opposite sign).  phi: device FP64.  dS (nullable: solve and action
  * only), X_out (nullable): device FP64; S_out (nullable, host) receives S. */

@@ -656,6 +656,8 @@ ufg_status ufg_fourier(ufg_field* f, const void* x, void* y, int prec, int inver
 ufg_status ufg_apply_M_momentum(ufg_field* f, const void* x, void* y, int prec, int transpose,
                                 void* stream) {
   clear_error();
+  const bool emulated = (prec == UFG_FP64_EMULATED);
+  if (emulated) prec = UFG_FP64;
   UFG_TRY(check_vec(f, x, y, prec));
   const ufg_lattice* lat = f->lat;
   if (!slice_m1w_supported(lat->nx, prec)) {
@@ -675,6 +677,7 @@ ufg_status ufg_apply_M_momentum(ufg_field* f, const void* x, void* y, int prec, 
   c.shift = transpose ? +1 : -1;
   c.a = 1.0;
   c.out = y;
+  c.emulate64 = emulated ? 1 : 0;
   return run(lat, c, as_stream(stream));
 }
 

@@ -84,6 +84,47 @@ __device__ __forceinline__ R block_row(const R (&c)[NC], const R* x, int i) {
   return acc;
 }
 
+// Double-float value hi + lo (|lo| <= ulp(hi) / 2, about 46 significant bits) whose arithmetic
+// runs on the FP32 pipe: sums by Knuth's error-free TwoSum on both parts followed by two
+// renormalisations, products by the FMA-based error-free product (Dekker's splitting replaced
+// by one fused multiply-add).  GB300's FP64 pipe issues ~1/76 of its FP32 FMA rate, so an
+// operation of ~20 FP32 instructions still beats one FP64 instruction by ~4x.  Every step uses
+// the _rn intrinsics so that the compiler neither contracts nor reassociates them.
+struct dfloat {
+  float hi, lo;
+};
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dfloat df_renorm(float a, float b) {  // needs |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfloat operator+(dfloat x, dfloat y) {
+  dfloat s = df_two_sum(x.hi, y.hi);
+  const dfloat t = df_two_sum(x.lo, y.lo);
+  s = df_renorm(s.hi, __fadd_rn(s.lo, t.hi));
+  return df_renorm(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ dfloat operator-(dfloat x, dfloat y) {
+  return x + dfloat{-y.hi, -y.lo};
+}
+__device__ __forceinline__ dfloat operator*(dfloat x, dfloat y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return df_renorm(p, e);
+}
+__device__ __forceinline__ dfloat fmadd(dfloat a, dfloat b, dfloat c) { return a * b + c; }
+__host__ __device__ __forceinline__ dfloat df_from(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfloat x) { return (double)x.hi + (double)x.lo; }
+
 // Applies the reduced operator to the line v[0..N) and hands every output (index, value) to st.
 template <int N, typename R, bool IN_SPEC, bool OUT_SPEC, class Store>
 __device__ __forceinline__ void line_op(const R (&v)[N], const LineCoef<N, R>& cf, Store&& st) {

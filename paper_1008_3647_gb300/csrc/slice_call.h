@@ -80,6 +80,9 @@ struct SliceCall {
   // potential w = 1 + A sin(sigma) and a = 1
   int m1w_full = 0;
   double full_scale = 1.0;
+  // FAM_M1W FULL on FP64 vectors: double-float arithmetic on the FP32 pipe (slice_df.cuh) instead
+  // of FP64 arithmetic (the batched reliable-update residuals)
+  int emulate64 = 0;
 };
 
 // Test hook of ufg_test_expire_waits: 1 if this TMA launch on st runs one bounded wait that is

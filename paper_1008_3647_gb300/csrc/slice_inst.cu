@@ -2,6 +2,7 @@
 // supported N so the heavy unrolled kernels build in parallel).
 #include <cstdlib>
 
+#include "slice_df.cuh"
 #include "slice_kernel.cuh"
 #include "slice_pair.cuh"
 #include "slice_tma.cuh"

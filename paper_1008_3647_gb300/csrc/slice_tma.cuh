@@ -887,8 +887,12 @@ inline cudaError_t m1w_dir(const SliceCall& c, cudaStream_t st) {
 }
 
 template <int N>
+cudaError_t m1w_df_try(const SliceCall& c, cudaStream_t st);
+
+template <int N>
 inline cudaError_t slice_m1w_try(const SliceCall& c, cudaStream_t st) {
   if (!slice_m1w_supported(N, c.prec) || c.shift == 0) return cudaErrorNotSupported;
+  if (c.emulate64 && c.prec == 0) return m1w_df_try<N>(c, st);
   if constexpr (N == 16) {
     if (c.prec == 1) return c.m1w_full ? m1w_dir<16, float, true>(c, st)
                                        : m1w_dir<16, float, false>(c, st);

@@ -1454,6 +1454,28 @@ ufg_status ufg_hmc_force(ufg_solver* S, ufg_field* f, const double* phi, double*
   }
   double* X = X_out ? X_out : S->xf64;
   ufg_status st = ufg_solve_bicgstab_two_step(S, f, phi, X, p, stats, stream);
+  if (st == UFG_BREAKDOWN) {
+    // BiCGStab's near-breakdown persisted (rare, configuration-dependent): the same system
+    // M^T M X = phi is finished from the BiCGStab iterate by CG on the normal equations, which
+    // cannot break down, with the Chebyshev preconditioner of degree 16 (Sec. 2)
+    ufg_params q = *p;
+    q.x0_given = 1;
+    ufg_stats cg_stats;
+    const int iters_bicg = stats ? stats->iterations : 0;
+    const int kind = S->pc_kind;
+    const ufg_pc_params pcs = S->pc;
+    ufg_pc_params cheb = {};
+    cheb.degree = 16;
+    cheb.alpha = 2.0;
+    UFG_TRY(ufg_set_preconditioner(S, UFG_PC_CHEB, &cheb));
+    st = ufg_solve_cg_normal(S, f, phi, X, &q, stats ? &cg_stats : nullptr, stream);
+    S->pc_kind = kind;
+    S->pc = pcs;
+    if (stats) {
+      cg_stats.iterations += iters_bicg;
+      *stats = cg_stats;
+    }
+  }
   if (st != UFG_OK && st != UFG_NOT_CONVERGED) return st;
   if (S_out) {
     CallGuard g(S, as_stream(stream));

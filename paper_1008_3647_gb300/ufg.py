@@ -21,7 +21,7 @@ UFG_TIMEOUT, UFG_CUDA_ERROR, UFG_OOM, UFG_INTERNAL, UFG_UNSUPPORTED = 5, 6, 7, 8
 STATUS_NAMES = {0: "UFG_OK", 1: "UFG_INVALID_ARG", 2: "UFG_NOT_CONVERGED", 3: "UFG_BREAKDOWN",
                 4: "UFG_NONFINITE", 5: "UFG_TIMEOUT", 6: "UFG_CUDA_ERROR", 7: "UFG_OOM",
                 8: "UFG_INTERNAL", 9: "UFG_UNSUPPORTED"}
-UFG_FP64, UFG_FP32, UFG_MIXED = 0, 1, 2
+UFG_FP64, UFG_FP32, UFG_MIXED, UFG_FP64_EMULATED = 0, 1, 2, 3
 UFG_PC_NONE, UFG_PC_CHEB, UFG_PC_SCA, UFG_PC_WCE, UFG_PC_SCA_CHEB = 0, 1, 2, 3, 4
 PC_KINDS = {"none": UFG_PC_NONE, "cheb": UFG_PC_CHEB, "sca": UFG_PC_SCA, "wce": UFG_PC_WCE,
             "sca_cheb": UFG_PC_SCA_CHEB}
@@ -342,9 +342,17 @@ def ufg_fourier(field, x, inverse=False, y=None):
     return _apply_flag("ufg_fourier", field, x, inverse, y)
 
 
-def ufg_apply_M_momentum(field, x, transpose=False, y=None):
-    """M (or M^T) in the momentum basis: F M F^T x per slice-stacked vector."""
-    return _apply_flag("ufg_apply_M_momentum", field, x, transpose, y)
+def ufg_apply_M_momentum(field, x, transpose=False, y=None, emulated=False):
+    """M (or M^T) in the momentum basis: F M F^T x per slice-stacked vector.  emulated=True (FP64
+    vectors only): double-float arithmetic on the FP32 pipe."""
+    if not emulated:
+        return _apply_flag("ufg_apply_M_momentum", field, x, transpose, y)
+    _vec(x, field.lattice.shape, (torch.float64,))
+    y = torch.empty_like(x) if y is None else y
+    _vec(y, field.lattice.shape, (torch.float64,))
+    _check(load().ufg_apply_M_momentum(field._h, _ptr(x), _ptr(y), UFG_FP64_EMULATED,
+                                       int(bool(transpose)), _stream()))
+    return y
 
 
 def _pc_params(kind, degree=16, eps=0.0, scale=0.0, alpha=2.0, order=2, euler=False, p=0.5,

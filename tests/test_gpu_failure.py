@@ -111,3 +111,24 @@ def test_strong_coupling_g10_does_not_converge_within_paper_budget(ufg):
                                                maxit=833)
     assert st["status"] in (ufg.UFG_NOT_CONVERGED, ufg.UFG_BREAKDOWN, ufg.UFG_NONFINITE), st
     assert st["true_residual"] > 1e-10 or not np.isfinite(st["true_residual"])
+
+
+def test_force_finishes_a_broken_down_solve_with_cg(ufg):
+    # the same system as the breakdown test above, through the force: BiCGStab breaks down and
+    # CG on M^T M (Chebyshev 16) finishes the solve, so the force and the action are still those
+    # of Q^{-1} phi
+    nx, ntau = 8, 64
+    sigma, b = field_and_source(nx, ntau, 0)
+    lat = ufg.Lattice(nx, ntau)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    solver = ufg.Solver(lat)
+    dS, X, S, st = solver.ufg_hmc_force(field, torch.from_numpy(b).cuda(), tol=1e-10)
+    assert st["status"] == ufg.UFG_OK, st
+    olat = O.Lattice(nx, ntau)
+    Xh = X.cpu().numpy()
+    r = b - O.apply_Q(olat, sigma, Xh)
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b)
+    ref = O.force_dS_dsigma(olat, sigma, Xh)
+    # (1e-11: this unpreconditioned solution spans a wide range, so the force entries do too)
+    assert float(np.abs(dS.cpu().numpy() - ref).max() / np.abs(ref).max()) < 1e-11
+    assert S == pytest.approx(float(np.dot(b.ravel(), Xh.ravel())), rel=1e-12)

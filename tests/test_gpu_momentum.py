@@ -68,6 +68,21 @@ def test_momentum_M_matches_oracle(ufg, nx, ntau, dtype):
         assert err < TOL[dtype], (transpose, err)
 
 
+@pytest.mark.parametrize("nx,ntau", [(16, 12), (16, 5), (8, 9)])
+def test_momentum_M_emulated_fp64_matches_oracle(ufg, nx, ntau):
+    # double-float arithmetic on the FP32 pipe (about 46 bits) on FP64 vectors: against the oracle
+    # at the FP64 tolerance, and against the FP64-pipe kernel
+    sigma, x, lat, field = _field(ufg, nx, ntau, 21 + ntau)
+    olat = O.Lattice(nx, ntau, 0.05, 5.0)
+    xh = ufg.ufg_fourier(field, torch.from_numpy(x).cuda())
+    for transpose, ref_fn in ((False, O.apply_M), (True, O.apply_Mdag)):
+        ye = ufg.ufg_apply_M_momentum(field, xh, transpose=transpose, emulated=True)
+        yd = ufg.ufg_apply_M_momentum(field, xh, transpose=transpose)
+        assert float((ye - yd).abs().max() / yd.abs().max()) < 1e-12
+        y = ufg.ufg_fourier(field, ye, inverse=True)
+        assert _rel(y.cpu().numpy(), ref_fn(olat, sigma, x)) < 1e-12
+
+
 def test_momentum_M_rejects_unbuilt_extent(ufg):
     _, x, lat, field = _field(ufg, 12, 4, 3)
     with pytest.raises(ufg.UfgError):
