@@ -29,6 +29,28 @@
 
 namespace ufg {
 
+// Coefficient table of the TMA slice kernels: column-paired (line_op_k) for FP32 N = 32, where
+// the packed multiply-adds measured fastest, the plain row-major blocks otherwise.
+template <int N, typename R>
+struct TmaCoefSel {
+  using type = LineCoef<N, R>;
+};
+template <>
+struct TmaCoefSel<32, float> {
+  using type = LineCoefK<32>;
+};
+template <int N, typename R>
+using TmaCoef = typename TmaCoefSel<N, R>::type;
+
+template <int N, typename R>
+inline void tma_set_coef(LineCoef<N, R>& out, const void* in) {
+  out = *reinterpret_cast<const LineCoef<N, R>*>(in);
+}
+template <int N>
+inline void tma_set_coef(LineCoefK<N>& out, const void* in) {
+  line_coef_pairs<N>(out, *reinterpret_cast<const LineCoef<N, float>*>(in));
+}
+
 template <int N, typename R>
 struct TmaArgs {
   CUtensorMap tm_in;   // [rows][N] view of the input arena, box N x (N/C * N)
@@ -38,9 +60,9 @@ struct TmaArgs {
   // The line operator once per pass: with a single copy the compiler keeps all of its
   // coefficients in registers from the first pass to the last (118 instead of 56 registers for
   // N = 16); separate copies stay constant-bank operands of the multiply-adds.
-  LineCoef<N, R> coef_x;
-  LineCoef<N, R> coef_y;
-  LineCoef<N, R> coef_z;
+  TmaCoef<N, R> coef_x;
+  TmaCoef<N, R> coef_y;
+  TmaCoef<N, R> coef_z;
   const R* bkpost;
   const R* pre_g;  // the load multiplier in global memory (8-CTA clusters read it directly)
   R* out;
@@ -97,12 +119,38 @@ __device__ __forceinline__ void tma_load_rows(void* dst, const CUtensorMap* tm, 
       : "memory");
 }
 
+// v[i] *= w[i] for one 16-byte chunk: packed FP32x2 multiplies for FP32
+__device__ __forceinline__ void mul_chunk(float (&v)[4], const float (&w)[4]) {
+  const float2 a = __fmul2_rn(make_float2(v[0], v[1]), make_float2(w[0], w[1]));
+  const float2 b = __fmul2_rn(make_float2(v[2], v[3]), make_float2(w[2], w[3]));
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+__device__ __forceinline__ void mul_chunk(double (&v)[2], const double (&w)[2]) {
+  v[0] *= w[0];
+  v[1] *= w[1];
+}
+
+// A store into another CTA's shared memory through its 32-bit shared::cluster address (mapa).
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, int rank) {
+  uint32_t d;
+  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(smem_addr(p)), "r"(rank));
+  return d;
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v));
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v));
+}
+
 // x-pass output: the row's N results are collected in registers and written back as 16-byte
 // chunks (chunk c at c ^ f(r)), which keeps the stores of a warp's 32 rows free of bank conflicts
 // (element-wise stores of one column index would hit 8 banks only).
-template <int N, typename R, bool IN_SPEC, bool OUT_SPEC>
-__device__ __forceinline__ void swz_store_row_impl(R* xs, int r, const R (&v)[N],
-                                                   const LineCoef<N, R>& cf) {
+template <int N, typename R, bool IN_SPEC, bool OUT_SPEC, class CF>
+__device__ __forceinline__ void swz_store_row_impl(R* xs, int r, const R (&v)[N], const CF& cf) {
   using G = SwzGeom<N, R>;
   constexpr int CPR = G::RB / 16, EPC = 16 / (int)sizeof(R);
   R o[N];
@@ -118,10 +166,9 @@ __device__ __forceinline__ void swz_store_row_impl(R* xs, int r, const R (&v)[N]
     }
   }
 }
-template <int N, typename R>
-__device__ __forceinline__ void swz_store_row(R* xs, int r, const R (&v)[N],
-                                              const LineCoef<N, R>& cf, bool in_spec,
-                                              bool out_spec) {
+template <int N, typename R, class CF>
+__device__ __forceinline__ void swz_store_row(R* xs, int r, const R (&v)[N], const CF& cf,
+                                              bool in_spec, bool out_spec) {
   if (in_spec) {
     if (out_spec) swz_store_row_impl<N, R, true, true>(xs, r, v, cf);
     else swz_store_row_impl<N, R, true, false>(xs, r, v, cf);
@@ -279,8 +326,15 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
         st16(pdst + r * N + c * EPC, pn);
       } else if (A.has_pre) {
         if constexpr (SEP) {
+          R vc[EPC], wc[EPC];
 #pragma unroll
-          for (int e = 0; e < EPC; ++e) v[c * EPC + e] *= wrow[c * EPC + e];
+          for (int e = 0; e < EPC; ++e) {
+            vc[e] = v[c * EPC + e];
+            wc[e] = wrow[c * EPC + e];
+          }
+          mul_chunk(vc, wc);
+#pragma unroll
+          for (int e = 0; e < EPC; ++e) v[c * EPC + e] = vc[e];
         } else {
 #pragma unroll
           for (int e = 0; e < EPC; ++e) v[c * EPC + e] *= ws[o + e];
@@ -304,15 +358,9 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
     __syncthreads();
   }
   // ---- y-pass ----
-  R* rdst[C];
+  uint32_t rdst[C];  // shared::cluster address of every CTA's receive buffer
 #pragma unroll
-  for (int o = 0; o < C; ++o) {
-    if constexpr (C > 1) {
-      rdst[o] = cg::this_cluster().map_shared_rank(recv, o);
-    } else {
-      rdst[o] = recv;
-    }
-  }
+  for (int o = 0; o < C; ++o) rdst[o] = C > 1 ? cluster_addr(recv, o) : 0u;
   for (int l = tid; l < NP * N; l += NT) {
     const int p = l / N, x = l - (l / N) * N;
     R v[N];
@@ -321,7 +369,7 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
     if constexpr (C > 1) {
       const int zrow = (rank * NP + p) * RY;
       line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_y, [&](int i, R val) {
-        rdst[i / RY][(zrow + i % RY) * N + x] = val;
+        st_cluster(rdst[i / RY] + (uint32_t)(((zrow + i % RY) * N + x) * sizeof(R)), val);
       });
     } else {
       line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_y,
@@ -491,7 +539,7 @@ inline cudaError_t tma_launch_epi(const SliceCall& c, cudaStream_t st) {
                    : encode_rows<R>(&a.tm_pre, c.pre, nelem, N, ROWS);
     if (e != cudaSuccess) return cudaErrorNotSupported;
   }
-  a.coef_x = *reinterpret_cast<const LineCoef<N, R>*>(c.coef);
+  tma_set_coef<N>(a.coef_x, c.coef);
   a.coef_y = a.coef_x;
   a.coef_z = a.coef_x;
   a.bkpost = static_cast<const R*>(c.bkpost);
@@ -632,8 +680,8 @@ constexpr int m1w_min_blocks() {
 }
 
 // Line passes over one swizzled slice box (all N planes in this CTA).
-template <int N, typename R, bool IN_SPEC, bool OUT_SPEC, bool MUL>
-__device__ __forceinline__ void swz_xpass(R* xs, const R* mul, const LineCoef<N, R>& cf) {
+template <int N, typename R, bool IN_SPEC, bool OUT_SPEC, bool MUL, class CF>
+__device__ __forceinline__ void swz_xpass(R* xs, const R* mul, const CF& cf) {
   using G = SwzGeom<N, R>;
   constexpr int CPR = G::RB / 16, EPC = 16 / (int)sizeof(R);
   for (int r = threadIdx.x; r < N * N; r += TMA_NT) {
@@ -648,8 +696,8 @@ __device__ __forceinline__ void swz_xpass(R* xs, const R* mul, const LineCoef<N,
   }
 }
 
-template <int N, typename R, bool IN_SPEC, bool OUT_SPEC>
-__device__ __forceinline__ void swz_ypass(R* xs, const LineCoef<N, R>& cf) {
+template <int N, typename R, bool IN_SPEC, bool OUT_SPEC, class CF>
+__device__ __forceinline__ void swz_ypass(R* xs, const CF& cf) {
   using G = SwzGeom<N, R>;
   for (int l = threadIdx.x; l < N * N; l += TMA_NT) {
     const int p = l / N, x = l - (l / N) * N;
