@@ -96,6 +96,11 @@ enum EpiBits { E_ID = 1, E_POST = 2, E_POST2 = 4, E_UV = 8, E_DOT = 16, E_BK = 3
 // the kernel first forms p' = r + beta (p - omega v) (per-problem scalars), writes p' back and
 // transforms it.
 constexpr int E_PREP = 64;
+// TMA 8-CTA clusters on whole slices only (set by the launcher for the KIN family): the load
+// multiplier arrives as a box in the receive buffer (E_PRE), the identity operand as a box in
+// the x buffer once the y-pass has read it (E_IDB)
+constexpr int E_PRE = 128;
+constexpr int E_IDB = 256;
 
 // Resident CTAs per SM the register allocation must allow (256 threads each).
 template <int N, typename R>

@@ -57,6 +57,7 @@ struct TmaArgs {
   CUtensorMap tm_pre;  // same view of the per-site multiplier (when has_pre)
   CUtensorMap tm_r;    // E_PREP: r and v (boxes 1 and 2)
   CUtensorMap tm_v;
+  CUtensorMap tm_id;   // E_PRE with E_ID: 3-D view [t z][y][x] of the identity operand
   // The line operator once per pass: with a single copy the compiler keeps all of its
   // coefficients in registers from the first pass to the last (118 instead of 56 registers for
   // N = 16); separate copies stay constant-bank operands of the multiply-adds.
@@ -116,6 +117,15 @@ __device__ __forceinline__ void tma_load_rows(void* dst, const CUtensorMap* tm, 
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(row), "r"(smem_addr(bar))
+      : "memory");
+}
+// box of a 3-D view starting at (x = 0, y, plane)
+__device__ __forceinline__ void tma_load_planes(void* dst, const CUtensorMap* tm, int y, int plane,
+                                                uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(y), "r"(plane), "r"(smem_addr(bar))
       : "memory");
 }
 
@@ -200,6 +210,11 @@ constexpr int tma_nt() {
 #ifndef UFG_C8_BLOCKS
 #define UFG_C8_BLOCKS 6
 #endif
+// 8-CTA clusters: the load multiplier as a TMA box in the receive buffer (1) or as per-thread
+// global loads (0); a compile-time tuning knob
+#ifndef UFG_C8_WBOX
+#define UFG_C8_WBOX 1
+#endif
 template <int N, typename R, int C>
 constexpr int tma_blocks() {
   return C == 8 ? UFG_C8_BLOCKS : tma_min_blocks<N, R>();
@@ -224,11 +239,13 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   constexpr int EPC = 16 / (int)sizeof(R);
   constexpr bool IN_SPEC = (FAM == FAM_INV);
   constexpr bool OUT_SPEC = (FAM == FAM_FWD);
-  // 8-CTA clusters keep the pushed z-columns in a buffer of their own and read the load
-  // multiplier from global memory: no cluster-wide wait is then needed between the x- and
-  // y-passes (only one that every CTA of the cluster has started), and two 16 KB boxes per CTA
-  // let six CTAs share an SM
+  // 8-CTA clusters keep the pushed z-columns in a buffer of their own, which receives the load
+  // multiplier's box first (WBOX; otherwise each thread reads its multiplier row from global
+  // memory): each CTA announces (cluster arrive) that its buffer is free once its x-pass is
+  // done and waits for the cluster after reading its y-lines, before pushing the results; two
+  // 16 KB boxes per CTA let six CTAs share an SM
   constexpr bool SEP = (C == 8);
+  constexpr bool WBOX = SEP && (UFG_C8_WBOX != 0) && (EPI & E_PRE) != 0;
   static_assert(!SEP || (EPI & E_PREP) == 0, "the fused direction update needs the box layout");
   static_assert(!SEP || ROWS == NT, "8-CTA clusters: one row per thread");
   extern __shared__ __align__(1024) unsigned char tma_smem[];
@@ -256,7 +273,9 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   if (done != nullptr && A.exec_if >= 0 && *done != A.exec_if) return;  // uniform per cluster
   int rank = 0;
   if constexpr (C > 1) rank = (int)cg::this_cluster().block_rank();
-  if constexpr (SEP) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+  // WBOX: the receive buffer holds the multiplier first, so this CTA announces it free only
+  // after its x-pass; otherwise at once
+  if constexpr (SEP && !WBOX) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
   int t_in = t_out;
   if (A.shift < 0) t_in = (t_out == 0) ? ntau - 1 : t_out - 1;
   if (A.shift > 0) t_in = (t_out == ntau - 1) ? 0 : t_out + 1;
@@ -266,7 +285,7 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   const R* const ws = reinterpret_cast<R*>(base) + BUF;
 
   // ---- TMA: this CTA's planes of x (and of the load multiplier) in one box each ----
-  const bool box_pre = A.has_pre && !SEP;
+  const bool box_pre = A.has_pre && (!SEP || WBOX);
   if (tid == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -282,8 +301,8 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
       tma_load_rows(const_cast<R*>(ws), &A.tm_pre, A.pre_mode ? rank * NP * N : row, &bar);
   }
   // 8-CTA clusters: this thread's row of the multiplier, loaded while the box is in flight
-  R wrow[SEP ? N : 1];
-  if constexpr (SEP) {
+  R wrow[SEP && !WBOX ? N : 1];
+  if constexpr (SEP && !WBOX) {
     if (A.has_pre) {
       const R* src = A.pre_g + (size_t)rank * NP * NN + (size_t)tid * N;
       if (!A.pre_mode) src += off + (size_t)t_in * VOL;
@@ -330,7 +349,11 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
 #pragma unroll
           for (int e = 0; e < EPC; ++e) {
             vc[e] = v[c * EPC + e];
-            wc[e] = wrow[c * EPC + e];
+            if constexpr (WBOX) {
+              wc[e] = ws[o + e];
+            } else {
+              wc[e] = wrow[c * EPC + e];
+            }
           }
           mul_chunk(vc, wc);
 #pragma unroll
@@ -351,7 +374,8 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   R* const recv = xs + BUF;  // [plane z][row y - rank RY][x], plain layout
   if constexpr (SEP) {
     __syncthreads();  // this CTA's x-pass is complete
-    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");  // every CTA has started
+    if constexpr (WBOX) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+    if constexpr (!WBOX) asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
   } else if constexpr (C > 1) {
     cg::this_cluster().sync();
   } else {
@@ -361,7 +385,18 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
   uint32_t rdst[C];  // shared::cluster address of every CTA's receive buffer
 #pragma unroll
   for (int o = 0; o < C; ++o) rdst[o] = C > 1 ? cluster_addr(recv, o) : 0u;
-  for (int l = tid; l < NP * N; l += NT) {
+  if constexpr (WBOX) {  // one line per thread, read before the wait for every receive buffer
+    const int p = tid / N, x = tid - (tid / N) * N;
+    R v[N];
+#pragma unroll
+    for (int y = 0; y < N; ++y) v[y] = xs[G::off(p * N + y, x)];
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+    const int zrow = (rank * NP + p) * RY;
+    line_op<N, R, IN_SPEC, OUT_SPEC>(v, A.coef_y, [&](int i, R val) {
+      st_cluster(rdst[i / RY] + (uint32_t)(((zrow + i % RY) * N + x) * sizeof(R)), val);
+    });
+  }
+  for (int l = tid; l < (WBOX ? 0 : NP * N); l += NT) {
     const int p = l / N, x = l - (l / N) * N;
     R v[N];
 #pragma unroll
@@ -380,6 +415,17 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
     cg::this_cluster().sync();
   } else {
     __syncthreads();
+  }
+  // IDBOX (identity term): this CTA's x box is free now; its z-columns of the identity
+  // operand (planes of slice t_out, rows [rank RY, (rank+1) RY)) arrive there by TMA, laid out
+  // like the receive buffer
+  constexpr bool IDBOX = SEP && (EPI & E_IDB) != 0 && (EPI & E_ID) != 0;
+  if constexpr (IDBOX) {
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&bar, (uint32_t)(BUF * sizeof(R)));
+      tma_load_planes(xs, &A.tm_id, rank * (N / C), t_out * N, &bar);
+    }
   }
   // ---- z-pass + epilogue ----
   constexpr int COLS = NN / C;
@@ -401,10 +447,11 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
     const int q = rank * COLS + l;
     const int y = q / N, x = q - (q / N) * N;
     R v[N];
+    const int yl = y - rank * RY;
     if constexpr (C > 1) {
-      const int yl = y - rank * RY;
 #pragma unroll
       for (int z = 0; z < N; ++z) v[z] = recv[(z * RY + yl) * N + x];
+      if constexpr (IDBOX) mbar_wait_bounded(&bar, 1u, TMA_WAIT_LIMIT, A.err);
     } else {
 #pragma unroll
       for (int z = 0; z < N; ++z) v[z] = xs[G::off(z * N + y, x)];
@@ -435,7 +482,9 @@ slice_tma_kernel(const __grid_constant__ TmaArgs<N, R> A) {
         if constexpr (EPI & E_POST) b *= __ldg(rpost + g);
         if constexpr (EPI & E_POST2) b *= __ldg(rpost2 + g);
         R o;
-        if constexpr (EPI & E_ID) {
+        if constexpr (IDBOX) {
+          o = R(acoef) * fmadd(sgn, b, xs[(zp * RY + yl) * N + x]);
+        } else if constexpr (EPI & E_ID) {
           o = R(acoef) * fmadd(sgn, b, __ldg(rid + g));
         } else {
           o = sa * b;  // sign folded into the scale
@@ -521,6 +570,24 @@ inline cudaError_t encode_rows(CUtensorMap* tm, const void* base, long long nele
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// 3-D view [nelem / N^2][N][N] (planes, rows, x) with an N x box_y x N box, no swizzle
+template <typename R>
+inline cudaError_t encode_planes(CUtensorMap* tm, const void* base, long long nelem, int N,
+                                 int box_y) {
+  EncodeTiledFn encode = encode_tiled_fn();
+  if (encode == nullptr) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)(nelem / ((long long)N * N))};
+  const cuuint64_t strides[2] = {(cuuint64_t)N * sizeof(R), (cuuint64_t)N * N * sizeof(R)};
+  const cuuint32_t box[3] = {(cuuint32_t)N, (cuuint32_t)box_y, (cuuint32_t)N};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(
+      tm, sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+      const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int N, typename R, int C, int FAM, int EPI>
 inline cudaError_t tma_launch_epi(const SliceCall& c, cudaStream_t st) {
   constexpr int NP = N / C;
@@ -579,6 +646,13 @@ inline cudaError_t tma_launch_epi(const SliceCall& c, cudaStream_t st) {
   a.scs = c.scs;
   a.counters = c.counters;
   a.part_base = c.part_base;
+  if constexpr (C == 8 && (EPI & E_IDB) != 0 && (EPI & E_ID) != 0) {
+    // whole slices of one lattice (no batch tiles): planes t N .. t N + N - 1 of the 3-D view
+    if (c.tiles != nullptr || c.id == nullptr || nelem % ((long long)N * N) != 0)
+      return cudaErrorInvalidValue;
+    if (encode_planes<R>(&a.tm_id, c.id, nelem, N, N / C) != cudaSuccess)
+      return cudaErrorNotSupported;
+  }
   // clusters need the second box as the z-column receive buffer; E_PREP holds p, r and v
   const size_t smem = (size_t)(((EPI & E_PREP) != 0) ? 3 : ((a.has_pre || C > 1) ? 2 : 1)) * BUF *
                           sizeof(R) +
@@ -614,6 +688,23 @@ inline cudaError_t tma_launch_fam(const SliceCall& c, cudaStream_t st) {
     return cudaErrorInvalidValue;
   }
   if constexpr (FAM == FAM_KIN) {
+    if constexpr (C == 8) {  // operands as boxes (E_PRE, E_IDB), see slice_tma_kernel
+      if (c.tiles == nullptr) {
+        constexpr int B = E_PRE | E_IDB;
+        if (c.pre != nullptr || c.bkpre != nullptr) {
+          switch (mask) {
+            case E_ID: return tma_launch_epi<N, R, C, FAM, E_ID | B>(c, st);
+            case E_ID | E_DOT: return tma_launch_epi<N, R, C, FAM, E_ID | E_DOT | B>(c, st);
+          }
+        } else {
+          switch (mask) {
+            case E_ID | E_POST: return tma_launch_epi<N, R, C, FAM, E_ID | E_POST | E_IDB>(c, st);
+            case E_ID | E_POST | E_DOT:
+              return tma_launch_epi<N, R, C, FAM, E_ID | E_POST | E_DOT | E_IDB>(c, st);
+          }
+        }
+      }
+    }
     switch (mask) {
       case E_ID: return tma_launch_epi<N, R, C, FAM, E_ID>(c, st);
       case E_ID | E_POST: return tma_launch_epi<N, R, C, FAM, E_ID | E_POST>(c, st);
