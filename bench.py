@@ -415,7 +415,7 @@ def run_ufg(args, rank, world, local_rank):
             if key not in solvers96:
                 l96 = ufg.Lattice(pr["nx"], pr["ntau"], 0.05, 5.0)
                 s96 = ufg.Solver(l96)
-                s96.ufg_set_preconditioner("wce", order=2)
+                s96.ufg_set_preconditioner("wce", **METHOD)
                 solvers96[key] = (l96, s96)
             fields96.append(ufg.Field(solvers96[key][0], pr["sigma"]))
         x96 = [torch.zeros_like(pr["b"]) for pr in probs96]
@@ -518,8 +518,9 @@ def run_ufg(args, rank, world, local_rank):
                     "not_converged": {k: sum(st["status"] != ufg.UFG_OK for st in v)
                                       for k, v in box96.items()},
                     "sequential_fp64": seq96,
-                    "note": "96 uneven problems per rank in one ufg_solve_batch (BiCGStab + WCE2, "
-                            "tol 1e-10), one timed step each precision"},
+                    "note": "96 uneven problems per rank in one ufg_solve_batch (BiCGStab + WCE2 "
+                            "with Euler S_{2k/3,k/3}, tol 1e-10), one timed step each precision; "
+                            "the sequential baseline uses the same preconditioner"},
         "apply_fp32_32x512": roof["fp32"],
         "apply_fp32_32x512_mdag": roof["fp32_mdag"],
         "apply_fp64_32x512": roof["fp64"],

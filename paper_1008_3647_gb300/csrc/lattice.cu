@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "launch.cuh"
 #include "line_ops.cuh"
 #include "ufg_internal.h"
 
@@ -19,15 +20,20 @@ static std::atomic<long long> g_launches{0};
 
 void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-// Off by default: on the batched 16^3 solve it measured slower (107.3 vs 102.1 ms per solve),
-// the early-launched dependent CTAs only waiting on the previous grid.  UFG_PDL=1 turns it on.
+// Off for the solvers: on the batched 16^3 solve it measured slower (107.3 vs 102.1 ms per
+// solve), the early-launched dependent CTAs only waiting on the previous grid.  On for
+// standalone operator calls (back-to-back 32^3 x 512 applies: about 1.5 us less per call).
+// UFG_PDL=1 turns it on everywhere.
+static thread_local int g_pdl_scope = 0;
+PdlScope::PdlScope() { ++g_pdl_scope; }
+PdlScope::~PdlScope() { --g_pdl_scope; }
 bool pdl_enabled() {
   static int v = -1;
   if (v < 0) {
     const char* e = std::getenv("UFG_PDL");
     v = (e && e[0] == '1') ? 1 : 0;
   }
-  return v == 1;
+  return v == 1 || g_pdl_scope > 0;
 }
 long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
@@ -580,18 +586,21 @@ void ufg_field_destroy(ufg_field* f) {
 
 ufg_status ufg_apply_M(ufg_field* f, const void* x, void* y, int prec, void* stream) {
   clear_error();
+  PdlScope pdl;
   UFG_TRY(check_vec(f, x, y, prec));
   return op_M(f, prec, x, y, as_stream(stream));
 }
 
 ufg_status ufg_apply_Mdag(ufg_field* f, const void* x, void* y, int prec, void* stream) {
   clear_error();
+  PdlScope pdl;
   UFG_TRY(check_vec(f, x, y, prec));
   return op_Mdag(f, prec, x, y, as_stream(stream));
 }
 
 ufg_status ufg_apply_Q(ufg_field* f, const void* x, void* y, int prec, void* stream) {
   clear_error();
+  PdlScope pdl;
   UFG_TRY(check_vec(f, x, y, prec));
   void* tmp = prec ? (void*)f->tmp32 : (void*)f->tmp64;
   UFG_TRY(op_M(f, prec, x, tmp, as_stream(stream)));
@@ -600,6 +609,7 @@ ufg_status ufg_apply_Q(ufg_field* f, const void* x, void* y, int prec, void* str
 
 ufg_status ufg_apply_M1(ufg_field* f, const void* x, void* y, int prec, void* stream) {
   clear_error();
+  PdlScope pdl;
   UFG_TRY(check_vec(f, x, y, prec));
   SliceCall c = base_call(f->lat, FAM_KIN, prec);
   c.in = x;
@@ -611,6 +621,7 @@ ufg_status ufg_apply_M1(ufg_field* f, const void* x, void* y, int prec, void* st
 
 ufg_status ufg_apply_M1T(ufg_field* f, const void* x, void* y, int prec, void* stream) {
   clear_error();
+  PdlScope pdl;
   UFG_TRY(check_vec(f, x, y, prec));
   SliceCall c = base_call(f->lat, FAM_KIN, prec);
   c.in = x;
@@ -622,6 +633,7 @@ ufg_status ufg_apply_M1T(ufg_field* f, const void* x, void* y, int prec, void* s
 
 ufg_status ufg_apply_kinetic(ufg_field* f, const void* x, void* y, int prec, void* stream) {
   clear_error();
+  PdlScope pdl;
   UFG_TRY(check_vec(f, x, y, prec));
   SliceCall c = base_call(f->lat, FAM_KIN, prec);
   c.in = x;
@@ -631,6 +643,7 @@ ufg_status ufg_apply_kinetic(ufg_field* f, const void* x, void* y, int prec, voi
 
 ufg_status ufg_apply_M0inv(ufg_field* f, const void* x, void* y, int prec, void* stream) {
   clear_error();
+  PdlScope pdl;
   UFG_TRY(check_vec(f, x, y, prec));
   void* tmp = prec ? (void*)f->tmp32 : (void*)f->tmp64;
   return op_M0inv(f, prec, x, y, tmp, 0, as_stream(stream));
@@ -638,6 +651,7 @@ ufg_status ufg_apply_M0inv(ufg_field* f, const void* x, void* y, int prec, void*
 
 ufg_status ufg_apply_M0invT(ufg_field* f, const void* x, void* y, int prec, void* stream) {
   clear_error();
+  PdlScope pdl;
   UFG_TRY(check_vec(f, x, y, prec));
   void* tmp = prec ? (void*)f->tmp32 : (void*)f->tmp64;
   return op_M0inv(f, prec, x, y, tmp, 1, as_stream(stream));
@@ -646,6 +660,7 @@ ufg_status ufg_apply_M0invT(ufg_field* f, const void* x, void* y, int prec, void
 ufg_status ufg_fourier(ufg_field* f, const void* x, void* y, int prec, int inverse,
                        void* stream) {
   clear_error();
+  PdlScope pdl;
   UFG_TRY(check_vec(f, x, y, prec));
   SliceCall c = base_call(f->lat, inverse ? FAM_INV : FAM_FWD, prec);
   c.in = x;
@@ -656,6 +671,7 @@ ufg_status ufg_fourier(ufg_field* f, const void* x, void* y, int prec, int inver
 ufg_status ufg_apply_M_momentum(ufg_field* f, const void* x, void* y, int prec, int transpose,
                                 void* stream) {
   clear_error();
+  PdlScope pdl;
   const bool emulated = (prec == UFG_FP64_EMULATED);
   if (emulated) prec = UFG_FP64;
   UFG_TRY(check_vec(f, x, y, prec));

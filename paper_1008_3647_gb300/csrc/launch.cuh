@@ -10,8 +10,16 @@
 
 namespace ufg {
 
-// PDL only with UFG_PDL=1 (measured slower on the batched solve).
+// PDL for the launches of standalone operator calls (a PdlScope alive on the calling thread),
+// and for every launch with UFG_PDL=1; the solvers' launches go without (measured slower on the
+// batched solve).
 bool pdl_enabled();
+struct PdlScope {
+  PdlScope();
+  ~PdlScope();
+  PdlScope(const PdlScope&) = delete;
+  PdlScope& operator=(const PdlScope&) = delete;
+};
 
 __device__ __forceinline__ void pdl_begin() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
