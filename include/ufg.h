@@ -31,7 +31,10 @@
  *                      shared-memory-staged path instead of TMA (the fused momentum-space
  *                      kernels are TMA-only);
  *   UFG_NO_GRAPH=1     solver loops are launched directly instead of replayed CUDA graphs;
- *   UFG_PDL=1          kernels are launched with programmatic dependent launch;
+ *   UFG_PDL=1          every kernel is launched with programmatic dependent launch (by
+ *                      default only the launches of the standalone operator calls below);
+ *   UFG_NO_FUSED_Q=1   Q = M^T M as two launches (M, then M^T) everywhere (by default one
+ *                      kernel per output slice on 16^3 lattices with N_tau <= twice the SMs);
  *   UFG_NO_MOMENTUM=1  WCE-preconditioned BiCGStab stays in the position basis (by default it
  *                      iterates on F x where the lattice has the fused momentum-space operator).
  */
@@ -254,7 +257,9 @@ void ufg_field_destroy(ufg_field* f);
  * [1 - exp(-i omega - tau E(k))]^{-1} in frequency-momentum space, omega = (2n+1) pi / N_tau).
  * precision UFG_FP64: x, y are double*; UFG_FP32: float*.  x and y must not overlap.  Q and
  * M0^{-1}/M0^{-T} use library workspace of the field, so calls on one field must not overlap in
- * time on different streams. */
+ * time on different streams.  Q on a 16^3 lattice with 3 <= N_tau <= twice the GPU's SM count
+ * runs as one kernel per output slice (x at t-1, t, t+1 in shared memory, three kinetic
+ * stages, no intermediate vector); elsewhere as M followed by M^T. */
 ufg_status ufg_apply_M(ufg_field* f, const void* x, void* y, int precision, void* stream);
 ufg_status ufg_apply_Mdag(ufg_field* f, const void* x, void* y, int precision, void* stream);
 ufg_status ufg_apply_Q(ufg_field* f, const void* x, void* y, int precision, void* stream);

@@ -1,4 +1,6 @@
 // Runtime dispatch from the lattice extent N_x to the compiled slice-kernel instantiation.
+#include <cstdlib>
+
 #include "slice_call.h"
 
 namespace ufg {
@@ -12,6 +14,30 @@ bool slice_supported_n(int N) {
 
 bool slice_m1w_supported(int N, int prec) {
   return prec == 1 ? N == 16 : (N == 8 || N == 16);
+}
+
+bool slice_q_supported(int N, int prec, int ntau) {
+  static int env = -1;
+  if (env < 0) {
+    const char* e = std::getenv("UFG_NO_FUSED_Q");
+    const char* t = std::getenv("UFG_NO_TMA");
+    env = ((e && e[0] == '1') || (t && t[0] == '1')) ? 0 : 1;
+  }
+  if (!env || N != 16 || ntau < 3) return false;
+  // one CTA per output slice with three kinetic stages: ahead of the two launches of M and M^T
+  // while their slices fill at most about two CTAs per SM (16^3 x 256: 10.6 against 13.4 us in
+  // FP32, 183 against 191 us in FP64); behind them on longer lattices (16^3 x 1024 FP32: 23.0
+  // against 19.1 us) and on 8^3 slices (FP64 8^3 x 64: 17.3 against 14.7 us)
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+      v = 152;
+    sms = v;
+  }
+  (void)prec;
+  return ntau <= 2 * sms;
 }
 
 bool slice_tma_prep_supported(int N, int prec, int allow_tma) {

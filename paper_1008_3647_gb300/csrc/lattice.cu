@@ -602,6 +602,14 @@ ufg_status ufg_apply_Q(ufg_field* f, const void* x, void* y, int prec, void* str
   clear_error();
   PdlScope pdl;
   UFG_TRY(check_vec(f, x, y, prec));
+  if (slice_q_supported(f->lat->nx, prec, f->lat->ntau)) {  // Q in one kernel
+    SliceCall c = base_call(f->lat, FAM_KIN, prec);
+    c.fam = FAM_Q;
+    c.in = x;
+    c.pre = fld(f, 'w', prec);
+    c.out = y;
+    return run(f->lat, c, as_stream(stream));
+  }
   void* tmp = prec ? (void*)f->tmp32 : (void*)f->tmp64;
   UFG_TRY(op_M(f, prec, x, tmp, as_stream(stream)));
   return op_Mdag(f, prec, tmp, y, as_stream(stream));

@@ -183,10 +183,13 @@ void profile_graph_destroyed(cudaGraphExec_t ex) {
 }
 
 std::string slice_kernel_name(const SliceCall& c, int N) {
-  static const char* fam[] = {"kin", "fwd", "inv", "m1w"};
+  static const char* fam[] = {"kin", "fwd", "inv", "m1w", "Q"};
   std::string s = "slice ";
-  s += (c.fam >= 0 && c.fam <= 3) ? fam[c.fam] : "?";
-  if (c.fam != FAM_M1W) {
+  s += (c.fam >= 0 && c.fam <= 4) ? fam[c.fam] : "?";
+  if (c.fam == FAM_Q) {
+    if (c.U || c.V) s += "+uv";
+    if (c.want_dotP || c.want_self) s += "+dot";
+  } else if (c.fam != FAM_M1W) {
     if (c.pre) s += "+pre";
     if (c.bkpre) s += "+bkpre";
     if (c.bkpost) s += "+bkpost";

@@ -7,7 +7,10 @@ namespace ufg {
 // FAM_M1W: the weak-coupling term -A M1 (Sec. 3) in momentum space, -A S^{+-1} F^T (s * F x), for
 // one slice in one kernel
 // (inverse transform, site multiplier, forward transform); coef = inverse, coef2 = forward family.
-enum SliceFamily { FAM_KIN = 0, FAM_FWD = 1, FAM_INV = 2, FAM_M1W = 3 };
+// FAM_Q: the normal operator Q = M^T M (Eq. 1) in one kernel per output slice (slice_q.cuh):
+// in = x, pre = the potential w, coef = the kinetic family, out = a Q x + bU U + cV V with the
+// partials of the other families; whole slices of one lattice with N_tau >= 3.
+enum SliceFamily { FAM_KIN = 0, FAM_FWD = 1, FAM_INV = 2, FAM_M1W = 3, FAM_Q = 4 };
 
 // Batched mode: one problem of a batch as the kernels see it (device table).
 struct BatchProb {
@@ -81,7 +84,7 @@ struct SliceCall {
   int m1w_full = 0;
   double full_scale = 1.0;
   // FAM_M1W FULL on FP64 vectors: double-float arithmetic on the FP32 pipe (slice_df.cuh) instead
-  // of FP64 arithmetic (the batched reliable-update residuals)
+  // of FP64 arithmetic (ufg_apply_M_momentum with UFG_FP64_EMULATED)
   int emulate64 = 0;
 };
 
@@ -106,5 +109,8 @@ bool slice_supported_n(int N);
 // Whether the fused FAM_M1W kernel exists for (N, precision): one CTA per slice with the slice
 // in 64- or 128-byte TMA rows (FP32 N = 16, FP64 N = 8 and 16).
 bool slice_m1w_supported(int N, int prec);
+// Whether the fused FAM_Q kernel runs for (N, precision, N_tau): N = 16 (FP32 and FP64),
+// 3 <= N_tau <= twice the SM count, TMA enabled and UFG_NO_FUSED_Q unset.
+bool slice_q_supported(int N, int prec, int ntau);
 
 }  // namespace ufg

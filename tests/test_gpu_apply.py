@@ -136,3 +136,17 @@ def test_autotuned_launch_shape_keeps_parity(ufg, nx, ntau):
         for fn, ref_fn in [("ufg_apply_M", O.apply_M), ("ufg_apply_Mdag", O.apply_Mdag)]:
             y = getattr(ufg, fn)(field, xd).double().cpu().numpy()
             assert _rel(y, ref_fn(olat, sigma, xd.double().cpu().numpy())) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("ntau", [3, 4, 17])
+def test_fused_Q_16cubed_short_lattices(ufg, ntau, dtype):
+    """Q on 16^3 runs as one kernel per output slice (x at t-1, t, t+1): the shortest lattice
+    where the three slices differ, N_tau = 4 and an odd N_tau, against the oracle's M^T M."""
+    nx = 16
+    sigma, x = field_and_source(nx, ntau, 40 + ntau)
+    lat = ufg.Lattice(nx, ntau)
+    field = ufg.Field(lat, torch.from_numpy(sigma).cuda())
+    y = ufg.ufg_apply_Q(field, torch.from_numpy(x).cuda().to(dtype))
+    ref = O.apply_Q(O.Lattice(nx, ntau), sigma, x)
+    assert _rel(y.double().cpu().numpy(), ref) < TOL[dtype]

@@ -1,7 +1,8 @@
 """Paths selected by environment switches, each in a fresh process (the switches are read once):
 UFG_NO_MOMENTUM=1 keeps batched WCE solves in the position basis, where the BiCGStab direction
 update rides on the TMA forward transform; UFG_PDL=1 launches every kernel with programmatic
-dependent launch.  The solutions must still reach the 1e-10 residual recomputed by the oracle."""
+dependent launch; UFG_NO_FUSED_Q=1 applies Q = M^T M as two launches.  The solutions must still
+reach the 1e-10 residual recomputed by the oracle."""
 import os
 import subprocess
 import sys
@@ -41,5 +42,36 @@ def test_batched_solve_under_switch(env):
     e.update(env)
     e["PYTHONPATH"] = ROOT + os.pathsep + e.get("PYTHONPATH", "")
     r = subprocess.run([sys.executable, "-c", SCRIPT], cwd=ROOT, env=e, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0 and "env path ok" in r.stdout, (r.stdout[-2000:], r.stderr[-2000:])
+
+
+SCRIPT_CG = r"""
+import numpy as np, torch
+import oracle as O
+from paper_1008_3647_gb300 import ufg
+from paper_1008_3647_gb300.inputs import field_and_source
+nx, nt = 16, 48
+sg, b = field_and_source(nx, nt, 21)
+lat = ufg.Lattice(nx, nt)
+field = ufg.Field(lat, torch.from_numpy(sg).cuda())
+solver = ufg.Solver(lat)
+solver.ufg_set_preconditioner("cheb", degree=16)
+for prec in (ufg.UFG_MIXED, ufg.UFG_FP64):
+    x, st = solver.ufg_solve_cg_normal(field, torch.from_numpy(b).cuda(), tol=1e-10,
+                                       precision=prec)
+    assert st["status"] == ufg.UFG_OK, st
+    r = b - O.apply_Q(O.Lattice(nx, nt), sg, x.cpu().numpy())
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b)
+print("env path ok")
+"""
+
+
+@pytest.mark.parametrize("env", [{}, {"UFG_NO_FUSED_Q": "1"}])
+def test_cg_chebyshev_with_and_without_fused_q(env):
+    e = dict(os.environ)
+    e.update(env)
+    e["PYTHONPATH"] = ROOT + os.pathsep + e.get("PYTHONPATH", "")
+    r = subprocess.run([sys.executable, "-c", SCRIPT_CG], cwd=ROOT, env=e, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0 and "env path ok" in r.stdout, (r.stdout[-2000:], r.stderr[-2000:])
