@@ -524,6 +524,8 @@ def run_ufg(args, rank, world, local_rank):
         "apply_fp32_32x512": roof["fp32"],
         "apply_fp32_32x512_mdag": roof["fp32_mdag"],
         "apply_fp64_32x512": roof["fp64"],
+        "apply_q_fp32_32x512": roof["fp32_q"],
+        "apply_q_fp32_16x256": roof["fp32_q_16x256"],
         "c1_4x16_fp64_cg": c1,
         "c2_8x64_counts": c2,
         "coupling_sweep": sweep,
@@ -581,6 +583,39 @@ def apply_roofline(ufg, torch, dev, stream, hbm, peak_src):
     f64["alu"] = {"bound": "alu (FP64 pipe)", "achieved": ach64, "peak": peak64,
                   "unit": "TFLOP/s", "frac": ach64 / peak64, "flops_per_site": flops_site,
                   "peak_source": "measured in this run (ufg_measure_fma_rate, FP64 FMA chains)"}
+    # Q = M^T M: on 32^3 x 512 as M then M^T (24 B/site: x, w, y written and read, q), on
+    # 16^3 x 256 as one kernel per output slice (12 B/site: x, w, q; its 48 MB stay in L2, so
+    # its rate is not an HBM fraction)
+    for name, (qnx, qnt), reps in (("fp32_q", (32, 512), 20), ("fp32_q_16x256", (16, 256), 50)):
+        ql = ufg.Lattice(qnx, qnt)
+        qs, qx = field_and_source(qnx, qnt, 124)
+        qf = ufg.Field(ql, torch.from_numpy(qs).to(dev))
+        x = torch.from_numpy(qx).to(dev, torch.float32)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            ufg.ufg_apply_Q(qf, x, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ufg.ufg_apply_Q(qf, x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ql.ufg_lattice_check()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        if qnx == 32:
+            bytes_ = 6 * x.element_size() * x.numel()
+            out[name] = {"kernel": "Q = M^T M, torch.float32, 32^3x512, two slice launches",
+                         "bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm,
+                         "unit": "GB/s", "frac": bytes_ / t / 1e9 / hbm, "traffic": None,
+                         "peak_source": peak_src, "us_per_launch": t * 1e6 / 2,
+                         "us_per_apply": t * 1e6, "algorithmic_bytes": bytes_,
+                         "applies_per_s": 1.0 / t}
+        else:
+            out[name] = {"kernel": "Q = M^T M, torch.float32, 16^3x256, one kernel per slice "
+                                   "(inputs L2-resident)",
+                         "us_per_apply": t * 1e6, "applies_per_s": 1.0 / t,
+                         "algorithmic_bytes": 3 * x.element_size() * x.numel()}
     return out
 
 
