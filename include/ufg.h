@@ -60,9 +60,11 @@ typedef enum {
 
 /* UFG_FP64_EMULATED: FP64 vectors, arithmetic in double-float pairs on the FP32 pipe (about 46
  * significant bits; GB300's FP64 pipe is ~1/76 of its FP32 rate).  Accepted by
- * ufg_apply_M_momentum only.  Its absolute error is about 2^-46 ||M|| ||x||, so a residual
- * b - M x of a nearly converged, ill-conditioned system (||x|| >> ||b||) is not resolved to
- * 1e-10 of ||b||: the solvers compute their true residuals in FP64. */
+ * ufg_apply_M_momentum.  Its absolute error is about 2^-46 ||M|| ||x||, so a residual b - M x of
+ * a nearly converged, ill-conditioned system (||x|| >> ||b||) is not resolved to 1e-10 of
+ * ||b|| this way.  The batched mixed-precision solve uses it only for incremental residual
+ * updates r -= M d after a first FP64 residual, where the error scales with the increment d;
+ * every final residual is FP64. */
 typedef enum { UFG_FP64 = 0, UFG_FP32 = 1, UFG_MIXED = 2, UFG_FP64_EMULATED = 3 } ufg_precision;
 
 /* UFG_PC_SCA_CHEB: the strong-coupling factorisation with the Chebyshev polynomial as a secondary

@@ -79,7 +79,8 @@ struct Batch {
   bool mom = false;
   double *xm64 = nullptr, *bm64 = nullptr;  // the right-hand side and solution in that basis
   double *rc64 = nullptr, *cr64 = nullptr;  // correction round: residual copy and correction
-  double* scale = nullptr;        // per-problem scale factors (mixed precision glue)
+  double* d64 = nullptr;  // mixed solves: the FP64 increment of an incremental reliable update
+  double* scale = nullptr;        // per-problem scale factors (mixed precision glue), 2 n
   double* scale_h = nullptr;      // pinned
   double* parts = nullptr;
   size_t part_stride = 0;
@@ -157,13 +158,15 @@ ufg_status slice(Batch& B, Group& g, SliceCall c, int exec_if) {
 
 // out = a * (A in) + bU * U with partials (out.dotP, out.out), all groups; fop >= 0 applies that
 // scalar op to each problem from the partials in the same launch
+// emulate64 (FP64, momentum basis): double-float arithmetic on the FP32 pipe (slice_df.cuh)
 ufg_status apply_b(Batch& B, int prec, int op, const void* in, void* out, double a, const void* U,
                    double bU, const void* dotP, bool self, double* part, int exec_if,
-                   int fop = -1) {
+                   int fop = -1, bool emulate64 = false) {
   if (B.mom) {  // the fused momentum-space operator, one kernel per group
     for (auto& g : B.groups) {
       SliceCall c = base_call(g.lat, FAM_INV, prec);
       c.fam = FAM_M1W;
+      c.emulate64 = (emulate64 && prec == 0) ? 1 : 0;
       c.coef2 = base_call(g.lat, FAM_FWD, prec).coef;
       c.m1w_full = 1;
       c.in = in;
@@ -511,15 +514,32 @@ ufg_status norms_b(Batch& B, const double* v, std::vector<double>& out) {
   return UFG_OK;
 }
 
+// mode 0: y32 = s x64; mode 1: x64 += s y32; mode 2 (the fold of a reliable update, n
+// problems): with s = scale[p], x64 += s y32, or with s = scale[n + p], d64 = s y32 and
+// x64 += d64; y32 = 0 either way.  Problems with zero scales are skipped.
 __global__ void mixed_batch_kernel(const int4* tiles, const double* scale, double* x64, float* y32,
-                                   int mode) {
+                                   int mode, double* d64, int n) {
   pdl_begin();
   const int4 tl = tiles[blockIdx.x];
   const double sc = scale[tl.x];
-  if (sc == 0.0) return;  // problem not selected
+  const double sd = mode == 2 ? scale[n + tl.x] : 0.0;
+  if (sc == 0.0 && sd == 0.0) return;  // problem not selected
   for (long long i = (long long)tl.y + threadIdx.x; i < (long long)tl.y + tl.z; i += blockDim.x) {
-    if (mode == 0) y32[i] = (float)(sc * x64[i]);
-    else x64[i] += sc * (double)y32[i];
+    if (mode == 0) {
+      y32[i] = (float)(sc * x64[i]);
+    } else if (mode == 1) {
+      x64[i] += sc * (double)y32[i];
+    } else {
+      const double v = (double)y32[i];
+      if (sd != 0.0) {
+        const double d = sd * v;
+        d64[i] = d;
+        x64[i] += d;
+      } else {
+        x64[i] += sc * v;
+      }
+      y32[i] = 0.0f;
+    }
   }
 }
 
@@ -545,13 +565,22 @@ ufg_status axpy_b(Batch& B, double* x, const double* y, const std::vector<double
   return UFG_OK;
 }
 
-ufg_status mixed_glue(Batch& B, int mode, double* x64, float* y32, const std::vector<double>& sc) {
+// mode 2 takes the second scale set sd (see mixed_batch_kernel) and writes d64
+ufg_status mixed_glue(Batch& B, int mode, double* x64, float* y32, const std::vector<double>& sc,
+                      const std::vector<double>* sd = nullptr, double* d64 = nullptr) {
+  if (mode == 2 && (sd == nullptr || d64 == nullptr)) {
+    set_error("mixed glue: the fold needs the increment buffer");
+    return UFG_INTERNAL;
+  }
   std::memcpy(B.scale_h, sc.data(), B.n * sizeof(double));
-  UFG_CUDA(cudaMemcpyAsync(B.scale, B.scale_h, B.n * sizeof(double), cudaMemcpyHostToDevice, B.st));
+  if (mode == 2) std::memcpy(B.scale_h + B.n, sd->data(), B.n * sizeof(double));
+  const size_t nb = (mode == 2 ? 2 : 1) * (size_t)B.n * sizeof(double);
+  UFG_CUDA(cudaMemcpyAsync(B.scale, B.scale_h, nb, cudaMemcpyHostToDevice, B.st));
   note_launches(1);
-  KTimer kt("batch mixed glue", B.st, batch_work(B, nullptr, -1, mode ? 20.0 : 12.0));
+  KTimer kt("batch mixed glue", B.st,
+            batch_work(B, nullptr, -1, mode == 0 ? 12.0 : mode == 1 ? 20.0 : 32.0));
   UFG_CUDA(launch_k(mixed_batch_kernel, dim3(B.nvtiles), dim3(256), 0, B.st, 1,
-                    (const int4*)B.vtiles, (const double*)B.scale, x64, y32, mode));
+                    (const int4*)B.vtiles, (const double*)B.scale, x64, y32, mode, d64, B.n));
   return UFG_OK;
 }
 
@@ -599,6 +628,14 @@ ufg_status solve_in_basis(Batch& B, int op, const double* rhs, double* x,
   // slowest problem, and a stalled FP32 Krylov space can take several times the FP64 iteration
   // count.
   constexpr int RU_SPAN = 60;
+  // Incremental reliable updates (momentum basis): after a problem's first update r holds its
+  // FP64 true residual, and a later update x += d (d = ||rhs|| x32) needs only
+  // r -= A d, computed by the double-float operator (slice_df.cuh) on the FP32 pipe.  Its error,
+  // about 2^-46 ||A|| ||d||, scales with the increment (||d|| ~ ||A^-1|| ||r||), not with x,
+  // so it stays far below the residual it corrects; the first update of each solve and the
+  // final residual of every problem are FP64.
+  constexpr int RU_INC = 8;  // solver flag of the problems inside an incremental update
+  std::vector<char> have_r(B.n, 0);
   std::vector<char> fallback(B.n, 0), verified(B.n, 0);
   std::vector<int> stalls(B.n, 0), it_last(B.n, 0);
   std::vector<double> rlast(B.n, 0.0);
@@ -660,18 +697,25 @@ ufg_status solve_in_basis(Batch& B, int op, const double* rhs, double* x,
     }
     if (!upd) return UFG_OK;
     *changed = true;
-    // fold the increments into x and clear them
-    UFG_TRY(mixed_glue(B, 1, x, (float*)V.x, sc));
+    // fold the increments into x and clear them (incremental updates keep d = ||rhs|| x32)
+    std::vector<double> sc_full(B.n, 0.0), sc_inc(B.n, 0.0);
+    bool any_full = false, any_inc = false;
     for (int i = 0; i < B.n; ++i) {
       if (sc[i] == 0.0) continue;
-      B.scs_h[i].done = RU_BUSY;
+      const bool inc = B.mom && have_r[i];
+      (inc ? sc_inc : sc_full)[i] = sc[i];
+      (inc ? any_inc : any_full) = true;
+      B.scs_h[i].done = inc ? RU_INC : RU_BUSY;
       it_last[i] = B.scs_h[i].iters;
     }
+    UFG_TRY(mixed_glue(B, 2, x, (float*)V.x, sc_full, &sc_inc, B.d64));
     UFG_TRY(write_scs(B));
-    UFG_TRY(vecb(B, 1, V_ZERO, RU_BUSY, V.x, nullptr, nullptr, nullptr, nullptr, nullptr,
-                 nullptr));
-    // true residual in FP64
-    UFG_TRY(apply_b(B, 0, op, x, B.r64, -1.0, rhs, 1.0, nullptr, false, nullptr, RU_BUSY));
+    // true residual: r = rhs - A x in FP64, or r -= A d in double-float arithmetic
+    if (any_full)
+      UFG_TRY(apply_b(B, 0, op, x, B.r64, -1.0, rhs, 1.0, nullptr, false, nullptr, RU_BUSY));
+    if (any_inc)
+      UFG_TRY(apply_b(B, 0, op, B.d64, B.r64, -1.0, B.r64, 1.0, nullptr, false, nullptr, RU_INC,
+                      -1, true));
     UFG_TRY(norms_b(B, B.r64, rn));  // reads the scalars back
     std::vector<double> inv2(B.n, 0.0);
     bool cont = false;
@@ -693,6 +737,8 @@ ufg_status solve_in_basis(Batch& B, int op, const double* rhs, double* x,
         rmax[i] = rn[i] / bn[i];
         outer[i] += 1;
         cont = true;
+        have_r[i] = 1;
+        B.scs_h[i].done = RU_BUSY;  // the continuation below runs on RU_BUSY
       }
     }
     UFG_TRY(write_scs(B));
@@ -832,11 +878,11 @@ ufg_status setup(Batch& B, int n, const ufg_problem* probs) {
   UFG_TRY(B.alloc(&B.counters, (size_t)n));
   UFG_CUDA(cudaMemset(B.counters, 0, n * sizeof(unsigned)));
   if (cudaMallocHost(&B.scs_h, n * sizeof(DevScalars)) != cudaSuccess ||
-      cudaMallocHost(&B.scale_h, n * sizeof(double)) != cudaSuccess) {
+      cudaMallocHost(&B.scale_h, 2 * n * sizeof(double)) != cudaSuccess) {
     set_error("pinned allocation failed");
     return UFG_OOM;
   }
-  UFG_TRY(B.alloc(&B.scale, (size_t)n));
+  UFG_TRY(B.alloc(&B.scale, 2 * (size_t)n));
   // slice tiles per group (C CTAs per tile), recurrence tiles
   int cta = 0;
   for (auto& g : B.groups) {
@@ -912,6 +958,7 @@ ufg_status setup(Batch& B, int n, const ufg_problem* probs) {
   UFG_TRY(B.alloc(&B.cr64, S));
   UFG_TRY(B.alloc(&B.xm64, S));
   UFG_TRY(B.alloc(&B.bm64, S));
+  UFG_TRY(B.alloc(&B.d64, S));
   return UFG_OK;
 }
 

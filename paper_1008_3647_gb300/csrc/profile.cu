@@ -203,7 +203,7 @@ std::string slice_kernel_name(const SliceCall& c, int N) {
     s += c.shift > 0 ? "T" : "";
     if (c.m1w_full) s += (c.want_dotP || c.want_self) ? "+full+dot" : "+full";
   }
-  s += " N" + std::to_string(N) + (c.prec ? " f32" : " f64");
+  s += " N" + std::to_string(N) + (c.prec ? " f32" : (c.emulate64 ? " f64 as double-float" : " f64"));
   return s;
 }
 

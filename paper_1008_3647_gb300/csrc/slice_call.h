@@ -84,7 +84,8 @@ struct SliceCall {
   int m1w_full = 0;
   double full_scale = 1.0;
   // FAM_M1W FULL on FP64 vectors: double-float arithmetic on the FP32 pipe (slice_df.cuh) instead
-  // of FP64 arithmetic (ufg_apply_M_momentum with UFG_FP64_EMULATED)
+  // of FP64 arithmetic (ufg_apply_M_momentum with UFG_FP64_EMULATED; the batched incremental
+  // reliable updates)
   int emulate64 = 0;
 };
 

@@ -8,9 +8,11 @@
 // intermediate slices stay in the same 8-byte shared-memory slots (as float pairs), and the
 // result is written back as FP64.  Same operator, same layout and launch shape as the FP64
 // kernel: (M x^)_t = x^_t + sgn b .* F(w_{t-1} .* F^T x^_{t-1}) (DIR 0) and its transpose (DIR 1).
-// Measured at 16^3 x 256: 70 us against 105 us for the FP64 kernel.  The solvers do not use it
-// for residuals: b - M x of a nearly converged system cancels to 1e-10 of ||b|| while the error
-// here is about 2^-46 ||M|| ||x||, and the batched reliable updates needed more iterations with it.
+// Measured at 16^3 x 256: 70 us against 105 us for the FP64 kernel.  Its error is about
+// 2^-46 ||M|| ||x||: too large for a full residual b - M x of a nearly converged system (which
+// cancels to 1e-10 of ||b||; the batched solve needed more iterations that way), small enough
+// for the incremental reliable updates r -= M d of the batched mixed solve, whose error scales
+// with the increment d.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
