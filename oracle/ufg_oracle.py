@@ -11,7 +11,8 @@ as a library step), a multiplication by exp(-tau E(k)) on the momentum grid of S
 inverse transform.  The GPU path instead uses a real separable circulant contraction.
 
 Conventions (readings of the paper where it leaves a choice open):
-  * arrays are shaped [N_tau, N_x, N_x, N_x] = [t][z][y][x]; slice t (0-based) is the paper's
+  * arrays are shaped [N_tau, N_x, N_x, N_x] = [t][z][y][x] (lower-dimensional lattices, which
+    the methods carry over to (Sec. 6): [N_tau, N_x, N_x] or [N_tau, N_x]); slice t (0-based) is the paper's
     time index j = t + 1, so B_t uses sigma_t and the corner block of Eq. (MatrixM) is
     B_{N_tau-1} mapping slice N_tau-1 onto slice 0;
   * hbar = m = lattice spacing = 1, so E(k) = |k|^2 / 2 (dispersion 0).  dispersion 1 is the
@@ -63,45 +64,54 @@ def momentum_1d(nx: int) -> np.ndarray:
     return 2.0 * np.pi * n / nx
 
 
-def energy_grid(nx: int, dispersion: int = 0) -> np.ndarray:
-    """E(k) on the 3-D momentum grid [kz][ky][kx] (numpy FFT order).
+def energy_grid(nx: int, dispersion: int = 0, dim: int = 3) -> np.ndarray:
+    """E(k) on the dim-dimensional momentum grid ([kz][ky][kx] for dim 3, numpy FFT order).
 
     dispersion 0: E = hbar^2 k^2 / 2m with hbar = m = 1 (Sec. 1).
     dispersion 1: E = sum_i (1 - cos k_i), a Hubbard-type lattice dispersion (Sec. 6).
     """
+    if dim not in (1, 2, 3):
+        raise ValueError("dim must be 1, 2 or 3")
     k = momentum_1d(nx)
-    kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+    ks = np.meshgrid(*([k] * dim), indexing="ij")
     if dispersion == 0:
-        return 0.5 * (kx ** 2 + ky ** 2 + kz ** 2)
+        return sum(0.5 * ki ** 2 for ki in ks)
     if dispersion == 1:
-        return (1.0 - np.cos(kx)) + (1.0 - np.cos(ky)) + (1.0 - np.cos(kz))
+        return sum(1.0 - np.cos(ki) for ki in ks)
     raise ValueError("unknown dispersion")
 
 
 @dataclass
 class Lattice:
-    """N_x^3 x N_tau lattice with imaginary time step tau and coupling g (Sec. 1, Sec. 5)."""
+    """N_x^dim x N_tau lattice with imaginary time step tau and coupling g (Sec. 1, Sec. 5;
+    dim = 3 is the paper's problem, 1 and 2 the lower dimensions of Sec. 6)."""
     nx: int
     ntau: int
     tau: float = 0.05
     g: float = 5.0
     dispersion: int = 0
+    dim: int = 3
     A: float = field(init=False)
     E: np.ndarray = field(init=False, repr=False)
 
     def __post_init__(self):
-        if self.nx < 2 or self.nx % 2 or self.ntau < 2 or self.tau <= 0 or self.g < 0:
+        if (self.nx < 2 or self.nx % 2 or self.ntau < 2 or self.tau <= 0 or self.g < 0
+                or self.dim not in (1, 2, 3)):
             raise ValueError("invalid lattice")
         self.A = coupling_A(self.tau, self.g)
-        self.E = energy_grid(self.nx, self.dispersion)
+        self.E = energy_grid(self.nx, self.dispersion, self.dim)
 
     @property
     def shape(self):
-        return (self.ntau, self.nx, self.nx, self.nx)
+        return (self.ntau,) + (self.nx,) * self.dim
 
     @property
     def volume(self):
-        return self.nx ** 3
+        return self.nx ** self.dim
+
+    @property
+    def space_axes(self):
+        return tuple(range(-self.dim, 0))
 
     @property
     def beta(self):
@@ -110,9 +120,9 @@ class Lattice:
 
 def kinetic(lat: Lattice, u: np.ndarray) -> np.ndarray:
     """exp(-tau K) u on every time slice: K is diagonal in momentum space with entries E(k)."""
-    uh = np.fft.fftn(u, axes=(-3, -2, -1))
+    uh = np.fft.fftn(u, axes=lat.space_axes)
     uh *= np.exp(-lat.tau * lat.E)
-    return np.fft.ifftn(uh, axes=(-3, -2, -1)).real
+    return np.fft.ifftn(uh, axes=lat.space_axes).real
 
 
 def potentials(lat: Lattice, sigma: np.ndarray):
@@ -188,24 +198,28 @@ def apply_M0inv(lat, y):
 
     With the transform x_t = sum_omega e^{i omega t} x~_omega the normalisation constant is 1.
     """
-    ph = _antiperiodic_phases(lat.ntau)[:, None, None, None]
-    yh = np.fft.fftn(y * ph, axes=(0, 1, 2, 3))
+    tshape = (lat.ntau,) + (1,) * lat.dim
+    ph = _antiperiodic_phases(lat.ntau).reshape(tshape)
+    axes = tuple(range(lat.dim + 1))
+    yh = np.fft.fftn(y * ph, axes=axes)
     m = np.arange(lat.ntau)
-    omega = (2 * m + 1) * np.pi / lat.ntau
-    denom = 1.0 - np.exp(-1j * omega[:, None, None, None] - lat.tau * lat.E[None])
+    omega = ((2 * m + 1) * np.pi / lat.ntau).reshape(tshape)
+    denom = 1.0 - np.exp(-1j * omega - lat.tau * lat.E[None])
     xh = yh / denom
-    return (np.fft.ifftn(xh, axes=(0, 1, 2, 3)) / ph).real
+    return (np.fft.ifftn(xh, axes=axes) / ph).real
 
 
 def apply_M0invT(lat, y):
     """(M0^T)^{-1} y: the transposed diagonal [1 - exp(+i omega - tau E(k))]^{-1}."""
-    ph = _antiperiodic_phases(lat.ntau)[:, None, None, None]
-    yh = np.fft.fftn(y * ph, axes=(0, 1, 2, 3))
+    tshape = (lat.ntau,) + (1,) * lat.dim
+    ph = _antiperiodic_phases(lat.ntau).reshape(tshape)
+    axes = tuple(range(lat.dim + 1))
+    yh = np.fft.fftn(y * ph, axes=axes)
     m = np.arange(lat.ntau)
-    omega = (2 * m + 1) * np.pi / lat.ntau
-    denom = 1.0 - np.exp(+1j * omega[:, None, None, None] - lat.tau * lat.E[None])
+    omega = ((2 * m + 1) * np.pi / lat.ntau).reshape(tshape)
+    denom = 1.0 - np.exp(+1j * omega - lat.tau * lat.E[None])
     xh = yh / denom
-    return (np.fft.ifftn(xh, axes=(0, 1, 2, 3)) / ph).real
+    return (np.fft.ifftn(xh, axes=axes) / ph).real
 
 
 def dense_from_apply(op, shape):

@@ -4,17 +4,18 @@ This module draws random numbers only; it holds none of the method's arithmetic.
 the auxiliary field sigma is i.i.d. uniform on [-pi, pi] (the random configurations of the
 paper's Sec. 5), right-hand sides and pseudofermion sources are i.i.d. N(0, 1).  One numpy
 PCG64 generator per seed draws, in this order: sigma with shape [N_tau, N_x, N_x, N_x]
-(C order), then the vector of the same shape.
+(C order; [N_tau, N_x, N_x] or [N_tau, N_x] on lower-dimensional lattices), then the vector of
+the same shape.
 """
 from __future__ import annotations
 
 import numpy as np
 
 
-def field_and_source(nx: int, ntau: int, seed: int):
-    """(sigma, b): sigma ~ U[-pi, pi], b ~ N(0, 1), both float64 [N_tau][N_x][N_x][N_x]."""
+def field_and_source(nx: int, ntau: int, seed: int, dim: int = 3):
+    """(sigma, b): sigma ~ U[-pi, pi], b ~ N(0, 1), both float64 [N_tau][N_x]^dim."""
     rng = np.random.default_rng(seed)
-    shape = (ntau, nx, nx, nx)
+    shape = (ntau,) + (nx,) * dim
     sigma = rng.uniform(-np.pi, np.pi, size=shape)
     b = rng.standard_normal(shape)
     return sigma, b
