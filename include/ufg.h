@@ -215,6 +215,16 @@ ufg_status ufg_profile_read(ufg_kernel_stat* out, int max, int* n);
  * current device. */
 ufg_status ufg_lattice_create(int nx, int ntau, double tau, double g, int dispersion,
                               ufg_lattice** out);
+/* The same on a lattice of `dim` spatial dimensions, N_x^dim x N_tau with dim in {1, 2, 3}: the
+ * method carries over to lower dimensions with only the kinetic factor changed (Sec. 6; there
+ * exp(-tau K) = T on a 1-D slice and T (x) T on a 2-D slice).  Vectors are [N_tau][N_x]^dim,
+ * x fastest.  dim = 3 is ufg_lattice_create.  On dim 1 and 2 every apply, the solvers, the
+ * preconditioners, the force and the trajectories run on generic shared-memory slice kernels;
+ * the 3-D-only paths (TMA-staged and fused momentum-space kernels, the one-kernel Q, the
+ * momentum basis, ufg_apply_M_momentum, ufg_lattice_autotune and batched solves) are not used
+ * or return UFG_UNSUPPORTED. */
+ufg_status ufg_lattice_create_dim(int dim, int nx, int ntau, double tau, double g,
+                                  int dispersion, ufg_lattice** out);
 void ufg_lattice_destroy(ufg_lattice* lat);
 /* Coupling A of the lattice (Sec. 1). */
 double ufg_lattice_coupling(const ufg_lattice* lat);

@@ -16,14 +16,14 @@ bool slice_m1w_supported(int N, int prec) {
   return prec == 1 ? N == 16 : (N == 8 || N == 16);
 }
 
-bool slice_q_supported(int N, int prec, int ntau) {
+bool slice_q_supported(int N, int prec, int ntau, int dim) {
   static int env = -1;
   if (env < 0) {
     const char* e = std::getenv("UFG_NO_FUSED_Q");
     const char* t = std::getenv("UFG_NO_TMA");
     env = ((e && e[0] == '1') || (t && t[0] == '1')) ? 0 : 1;
   }
-  if (!env || N != 16 || ntau < 3) return false;
+  if (!env || dim != 3 || N != 16 || ntau < 3) return false;
   // one CTA per output slice with three kinetic stages: ahead of the two launches of M and M^T
   // while their slices fill at most about two CTAs per SM (16^3 x 256: 10.6 against 13.4 us in
   // FP32, 183 against 191 us in FP64); behind them on longer lattices (16^3 x 1024 FP32: 23.0

@@ -299,16 +299,17 @@ static ufg_status build_tables(ufg_lattice* L) {
     pack<double>(flat, L->coef[sp.fam][0]);
     pack<float>(flat, L->coef[sp.fam][1]);
   }
-  // per-mode table in spectral layout [sz][sy][sx]
+  // per-mode table in spectral layout [sz][sy][sx] (dim 3; [sy][sx], [sx] below): the product
+  // of the 1-D eigenvalues of the mode's slots
   std::vector<double> bk((size_t)L->V);
   std::vector<float> bkf((size_t)L->V);
-  for (int z = 0; z < N; ++z)
-    for (int y = 0; y < N; ++y)
-      for (int x = 0; x < N; ++x) {
-        const size_t i = ((size_t)z * N + y) * N + x;
-        bk[i] = L->lam[z] * L->lam[y] * L->lam[x];
-        bkf[i] = (float)bk[i];
-      }
+  for (long long i = 0; i < L->V; ++i) {
+    double b = 1.0;
+    long long r = i;
+    for (int d = 0; d < L->dim; ++d, r /= N) b *= L->lam[(size_t)(r % N)];
+    bk[(size_t)i] = b;
+    bkf[(size_t)i] = (float)b;
+  }
   UFG_TRY(dev_alloc(&L->bk64, (size_t)L->V));
   UFG_TRY(dev_alloc(&L->bk32, (size_t)L->V));
   UFG_TRY(dev_alloc(&L->dev_err, 1));
@@ -342,6 +343,7 @@ SliceCall base_call(const ufg_lattice* lat, int fam, int prec) {
   c.prec = prec;
   c.coef = lat->coef[fam][prec].data();
   c.ntau = lat->ntau;
+  c.dim = lat->dim;
   c.spc = lat->spc[prec];
   c.C = lat->C[prec];
   c.err = lat->dev_err;
@@ -462,12 +464,21 @@ long long ufg_kernel_launches(void) { return launches_so_far(); }
 
 ufg_status ufg_lattice_create(int nx, int ntau, double tau, double g, int dispersion,
                               ufg_lattice** out) {
+  return ufg_lattice_create_dim(3, nx, ntau, tau, g, dispersion, out);
+}
+
+ufg_status ufg_lattice_create_dim(int dim, int nx, int ntau, double tau, double g,
+                                  int dispersion, ufg_lattice** out) {
   clear_error();
   if (out == nullptr) {
     set_error("out is null");
     return UFG_INVALID_ARG;
   }
   *out = nullptr;
+  if (dim < 1 || dim > 3) {
+    set_error("invalid lattice: dim must be 1, 2 or 3 (got %d)", dim);
+    return UFG_INVALID_ARG;
+  }
   if (nx < 2 || nx % 2 != 0 || ntau < 3 || ntau > 1024 || !(tau > 0) || !(g >= 0) ||
       (dispersion != 0 && dispersion != 1) || !std::isfinite(tau) || !std::isfinite(g)) {
     set_error("invalid lattice: need even N_x >= 2, 3 <= N_tau <= 1024, tau > 0, g >= 0, "
@@ -486,8 +497,10 @@ ufg_status ufg_lattice_create(int nx, int ntau, double tau, double g, int disper
   L->g = g;
   L->dispersion = dispersion;
   L->A = std::sqrt(2.0) * std::sqrt(std::expm1(tau * g));
-  L->V = (long long)nx * nx * nx;
+  L->dim = dim;
+  L->V = (long long)nx * (dim >= 2 ? nx : 1) * (dim >= 3 ? nx : 1);
   L->S = L->V * ntau;
+  if (dim < 3) L->use_tma[0] = L->use_tma[1] = 0;
   cudaGetDevice(&L->device);
   ufg_status s = build_tables(L);
   if (s != UFG_OK) {
@@ -602,7 +615,7 @@ ufg_status ufg_apply_Q(ufg_field* f, const void* x, void* y, int prec, void* str
   clear_error();
   PdlScope pdl;
   UFG_TRY(check_vec(f, x, y, prec));
-  if (slice_q_supported(f->lat->nx, prec, f->lat->ntau)) {  // Q in one kernel
+  if (slice_q_supported(f->lat->nx, prec, f->lat->ntau, f->lat->dim)) {  // Q in one kernel
     SliceCall c = base_call(f->lat, FAM_KIN, prec);
     c.fam = FAM_Q;
     c.in = x;
@@ -684,7 +697,7 @@ ufg_status ufg_apply_M_momentum(ufg_field* f, const void* x, void* y, int prec, 
   if (emulated) prec = UFG_FP64;
   UFG_TRY(check_vec(f, x, y, prec));
   const ufg_lattice* lat = f->lat;
-  if (!slice_m1w_supported(lat->nx, prec)) {
+  if (lat->dim != 3 || !slice_m1w_supported(lat->nx, prec)) {
     set_error("momentum-space apply built for FP32 N_x = 16 and FP64 N_x = 8, 16 (got N_x = %d)",
               lat->nx);
     return UFG_INVALID_ARG;
@@ -776,6 +789,10 @@ extern "C" ufg_status ufg_lattice_autotune(ufg_lattice* L, void* stream) {
   if (!L) {
     set_error("null lattice");
     return UFG_INVALID_ARG;
+  }
+  if (L->dim != 3) {
+    set_error("autotune: the launch shapes it chooses exist for 3-D lattices only");
+    return UFG_UNSUPPORTED;
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   load_tune_file();

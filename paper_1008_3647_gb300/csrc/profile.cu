@@ -1,6 +1,7 @@
 // Per-kernel device timing of instrumented runs: CUDA-event pairs around each launch, with the
 // launch's algorithmic bytes, aggregated by kernel class on request (ufg_profile_*).
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstring>
 #include <map>
@@ -223,7 +224,7 @@ double slice_bytes_per_site(const SliceCall& c) {
 
 double slice_bytes_per_problem(const SliceCall& c, int N) {
   const int mode_tables = (c.bkpre ? 1 : 0) + (c.bkpost ? 1 : 0);
-  return (c.prec ? 4.0 : 8.0) * mode_tables * (double)N * N * N;
+  return (c.prec ? 4.0 : 8.0) * mode_tables * std::pow((double)N, c.dim);
 }
 
 }  // namespace ufg

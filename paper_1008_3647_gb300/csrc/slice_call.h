@@ -64,6 +64,7 @@ struct SliceCall {
   int allow_tma = 1;           // 0 forces the non-TMA kernel
   int* grid_out = nullptr;     // receives the number of CTAs launched (= partial pairs written)
   int ntau = 0;
+  int dim = 3;                 // lattice dimension: 3, or 1 / 2 (slice_lowd.cuh)
   int shift = 0;               // -1: t_in = t_out - 1, +1: t_in = t_out + 1, 0: t_in = t_out
   int spc = 1;                 // time slices per CTA (cluster)
   int C = 1;                   // cluster size (1, 2 or 4; N = 32 only uses 2 or 4)
@@ -112,6 +113,6 @@ bool slice_supported_n(int N);
 bool slice_m1w_supported(int N, int prec);
 // Whether the fused FAM_Q kernel runs for (N, precision, N_tau): N = 16 (FP32 and FP64),
 // 3 <= N_tau <= twice the SM count, TMA enabled and UFG_NO_FUSED_Q unset.
-bool slice_q_supported(int N, int prec, int ntau);
+bool slice_q_supported(int N, int prec, int ntau, int dim = 3);
 
 }  // namespace ufg

@@ -5,6 +5,7 @@
 #include "slice_df.cuh"
 #include "slice_kernel.cuh"
 #include "slice_pair.cuh"
+#include "slice_lowd.cuh"
 #include "slice_q.cuh"
 #include "slice_tma.cuh"
 
@@ -26,6 +27,7 @@ static bool tma_enabled() {
 // The TMA-pipelined kernel where it applies, the shared-memory-staged kernel otherwise.
 template <>
 cudaError_t slice_launch<UFG_N>(const SliceCall& c, cudaStream_t st) {
+  if (c.dim != 3) return slice_lowd_try<UFG_N>(c, st);       // 1-D and 2-D lattices
   if (c.fam == FAM_M1W) return slice_m1w_try<UFG_N>(c, st);  // callers check support first
   if (c.fam == FAM_Q) return slice_q_try<UFG_N>(c, st);      // callers check support first
   if (c.allow_tma && tma_enabled()) {

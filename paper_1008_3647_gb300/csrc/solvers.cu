@@ -99,7 +99,7 @@ cudaError_t sdisp(int nx, const SliceCall& c, cudaStream_t st) {
   note_launches(1);
   KTimer kt(slice_kernel_name(c, nx), st,
             solo_work(c.done, c.exec_if,
-                      slice_bytes_per_site(c) * c.ntau * nx * nx * nx +
+                      slice_bytes_per_site(c) * c.ntau * std::pow((double)nx, c.dim) +
                           slice_bytes_per_problem(c, nx)));
   return slice_dispatch(nx, c, st);
 }
@@ -157,7 +157,7 @@ ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const v
     if (e != cudaSuccess) return cuda_fail(e, "momentum-space operator");
     return UFG_OK;
   }
-  if (op == OPK_Q && slice_q_supported(L->nx, prec, L->ntau)) {  // Q in one kernel
+  if (op == OPK_Q && slice_q_supported(L->nx, prec, L->ntau, L->dim)) {  // Q in one kernel
     SliceCall c = base_call(L, FAM_KIN, prec);
     c.fam = FAM_Q;
     c.in = in;
@@ -288,7 +288,7 @@ ufg_status pc_cheb(ufg_solver* S, const ufg_field* f, int prec, const void* r, v
     UFG_TRY(apply_op(S, f, prec, OPK_Q, cur, V.u, 1.0 / s, cur, -ak[k], nullptr, false, nullptr,
                      nullptr));
     // z = [Q u / s - a_k u + b_k^2 cur] / norm_k (* 1/(z0 s) for the last factor)
-    if (slice_q_supported(L->nx, prec, L->ntau)) {  // Q in one kernel
+    if (slice_q_supported(L->nx, prec, L->ntau, L->dim)) {  // Q in one kernel
       SliceCall c = base_call(L, FAM_KIN, prec);
       c.fam = FAM_Q;
       c.in = V.u;
@@ -385,7 +385,7 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
     if (e != cudaSuccess) return cuda_fail(e, "forward transform");
     UFG_TRY(rec(V.spec, cw[0], 1, d > 0));
   }
-  const bool fused = slice_m1w_supported(L->nx, prec);
+  const bool fused = L->dim == 3 && slice_m1w_supported(L->nx, prec);
   for (int nn = 1; nn <= d; ++nn) {
     if (fused) {  // -A M1 (or M1^T) in momentum space in one kernel: spec -> wr
       SliceCall m = base_call(L, FAM_INV, prec);
@@ -1195,7 +1195,7 @@ ufg_status ufg_solver_create(const ufg_lattice* L, ufg_solver** out) {
   if ((s = dev_alloc(&S->x64, n)) || (s = dev_alloc(&S->b64, n)) || (s = dev_alloc(&S->r64, n)) ||
       (s = dev_alloc(&S->y64, n)) || (s = dev_alloc(&S->rc64, n)) ||
       (s = dev_alloc(&S->xs64, n)) || (s = dev_alloc(&S->xf64, n)) ||
-      (slice_m1w_supported(L->nx, 0) &&
+      (L->dim == 3 && slice_m1w_supported(L->nx, 0) &&
        ((s = dev_alloc(&S->mb64, n)) || (s = dev_alloc(&S->mx64, n)))) ||
       (s = dev_alloc(&S->parts, (size_t)NSLOT * 2 * MAX_PARTIAL_CTAS)) ||
       (s = dev_alloc(&S->sc, 1)) || (s = dev_alloc(&S->red_dev, 1)))

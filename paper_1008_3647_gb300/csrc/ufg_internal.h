@@ -142,6 +142,7 @@ ufg_status check_device_flag(const ufg_lattice* lat, cudaStream_t st);
 
 struct ufg_lattice {
   int nx = 0, ntau = 0, dispersion = 0;
+  int dim = 3;  // spatial dimension (1 and 2: slice_lowd.cuh; the fused 3-D kernels are off)
   double tau = 0, g = 0, A = 0;
   long long V = 0, S = 0;
   std::vector<double> lam;                 // exp(-tau E1) per 1-D spectral slot

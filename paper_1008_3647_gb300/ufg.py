@@ -104,6 +104,8 @@ _SIGS = {
     "ufg_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ufg_lattice_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "ufg_lattice_create_dim": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp)]),
     "ufg_lattice_destroy": (None, [_vp]),
     "ufg_lattice_coupling": (ctypes.c_double, [_vp]),
     "ufg_lattice_check": (ctypes.c_int, [_vp, _vp]),
@@ -229,19 +231,24 @@ def _vec(t, shape, dtypes=(torch.float64, torch.float32), host_ok=False):
 
 
 class Lattice:
-    """ufg_lattice: N_x^3 x N_tau lattice, time step tau, coupling g (A = sqrt(2(e^{tau g}-1)))."""
+    """ufg_lattice: N_x^dim x N_tau lattice (dim 3 by default; 1 and 2: the lower dimensions),
+    time step tau, coupling g (A = sqrt(2(e^{tau g}-1)))."""
 
-    def __init__(self, nx, ntau, tau=0.05, g=5.0, dispersion=0):
+    def __init__(self, nx, ntau, tau=0.05, g=5.0, dispersion=0, dim=3):
         lib = load()
         h = _vp()
-        _check(lib.ufg_lattice_create(nx, ntau, tau, g, dispersion, ctypes.byref(h)))
+        if dim == 3:
+            _check(lib.ufg_lattice_create(nx, ntau, tau, g, dispersion, ctypes.byref(h)))
+        else:
+            _check(lib.ufg_lattice_create_dim(dim, nx, ntau, tau, g, dispersion, ctypes.byref(h)))
         self._h = h
         self.nx, self.ntau, self.tau, self.g, self.dispersion = nx, ntau, tau, g, dispersion
+        self.dim = dim
         self.A = lib.ufg_lattice_coupling(h)
 
     @property
     def shape(self):
-        return (self.ntau, self.nx, self.nx, self.nx)
+        return (self.ntau,) + (self.nx,) * self.dim
 
     def ufg_lattice_autotune(self):
         _check(load().ufg_lattice_autotune(self._h, _stream()))
