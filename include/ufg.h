@@ -156,6 +156,8 @@ typedef struct {
   double true_residual;    /* ||b - M^T M x|| / ||b|| in FP64 at exit */
   double seconds;          /* wall time of the call */
   double inner_tol;        /* MIXED single-problem solves: the inner tolerance used (else 0) */
+  int tile_slices;         /* batched solves: time slices per slice-kernel tile of the problem's
+                              (N_x, tau) group, chosen by timing at the batch's set-up (else 0) */
 } ufg_stats;
 
 /* One independent problem of a batched solve.  sigma, b, x: FP64 arrays of its own lattice size

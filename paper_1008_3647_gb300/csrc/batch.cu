@@ -42,6 +42,7 @@ struct Group {
   int2* rtiles = nullptr;               // device recurrence tiles
   int nrtiles = 0;
   int max_ntau = 0;
+  int spc = 1;                          // time slices per slice tile (tune_tiles)
 };
 
 struct Arena {  // one precision's vectors, packed over all problems
@@ -836,6 +837,124 @@ std::string signature(int n, const ufg_problem* probs) {
 std::mutex g_batch_mu;
 std::vector<std::pair<std::string, std::unique_ptr<Batch>>> g_batch_cache;
 
+// Slice tiles of every group (C CTAs per tile, g.spc time slices each), the problems' CTA
+// ranges and the recurrence tiles; re-uploads the problem table when it exists already.
+ufg_status build_slice_tiles(Batch& B, const ufg_problem* probs) {
+  // slice tiles per group (C CTAs per tile), recurrence tiles
+  int cta = 0;
+  for (auto& g : B.groups) {
+    std::vector<BatchTile> tl;
+    std::vector<int2> rt;
+    const int C = g.lat->C[0];  // same cluster size for both precisions below N_x = 32
+    if (g.lat->C[1] != C) g.lat->C[1] = C;
+    g.lat->spc[0] = g.lat->spc[1] = g.spc;
+    g.cta_base = cta;
+    for (int i : g.probs) {
+      BatchProb& bp = B.probs_h[i];
+      const int nt = probs[i].ntau;
+      bp.off = B.off[i];
+      bp.ntau = nt;
+      bp.V = probs[i].nx * probs[i].nx * probs[i].nx;
+      bp.A = std::sqrt(2.0) * std::sqrt(std::expm1(probs[i].tau * probs[i].g));
+      bp.st0 = cta + (int)tl.size() * C;
+      for (int t0 = 0; t0 < nt; t0 += g.spc) tl.push_back(BatchTile{i, t0});
+      bp.st1 = cta + (int)tl.size() * C;
+      for (int mb = 0; mb < (bp.V + 31) / 32; ++mb) rt.push_back(make_int2(i, mb));
+      g.max_ntau = std::max(g.max_ntau, nt);
+    }
+    g.ntiles = (int)tl.size();
+    g.nrtiles = (int)rt.size();
+    cta += g.ntiles * C;
+    UFG_TRY(B.alloc(&g.tiles, tl.size()));
+    UFG_TRY(B.alloc(&g.rtiles, rt.size()));
+    UFG_CUDA(cudaMemcpy(g.tiles, tl.data(), tl.size() * sizeof(BatchTile), cudaMemcpyHostToDevice));
+    UFG_CUDA(cudaMemcpy(g.rtiles, rt.data(), rt.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  }
+  B.nslice_ctas = cta;
+  if (B.probs != nullptr)
+    UFG_CUDA(cudaMemcpy(B.probs, B.probs_h.data(), B.n * sizeof(BatchProb),
+                        cudaMemcpyHostToDevice));
+  return UFG_OK;
+}
+
+// Time slices per slice tile, tuned per (N_x, tau) group whose slice kernels are the
+// shared-memory ones in both precisions (no TMA shape at this N_x; the TMA kernels take one
+// slice per CTA): at N_x = 6 a one-slice tile keeps 36 of 256 threads busy in a pass.  Each
+// candidate (1, 2, 4, 8 slices within 48 KB of FP64 shared memory and the group's longest
+// N_tau) is timed on the batch's own arenas with the M apply in both precisions (zeroed
+// operands, three launches each after one), and the fastest is kept (ufg_stats.tile_slices).
+ufg_status tune_tiles(Batch& B, const ufg_problem* probs) {
+  auto tma_shape = [](int N, int prec) { return prec ? (N == 16 || N == 32) : (N == 8 || N == 16); };
+  bool changed = false, zeroed = false;
+  cudaEvent_t e0, e1;
+  UFG_CUDA(cudaEventCreate(&e0));
+  UFG_CUDA(cudaEventCreate(&e1));
+  ufg_status result = UFG_OK;
+  for (auto& g : B.groups) {
+    const int N = g.lat->nx;
+    if (tma_shape(N, 0) || tma_shape(N, 1)) continue;
+    std::vector<int> cand;
+    for (int spc : {1, 2, 4, 8}) {
+      const size_t smem = (size_t)spc * N * (N + 1) * N * sizeof(double);
+      if (spc > 1 && (smem > 48 * 1024 || spc > g.max_ntau)) break;
+      cand.push_back(spc);
+    }
+    if (cand.size() < 2) continue;
+    if (!zeroed) {
+      const size_t S = (size_t)B.S;
+      for (int prec = 0; prec < 2; ++prec) {
+        const size_t es = prec ? sizeof(float) : sizeof(double);
+        if (cudaMemsetAsync(B.ar[prec].x, 0, S * es, B.st) != cudaSuccess ||
+            cudaMemsetAsync(const_cast<void*>(fldb(B, 'w', prec)), 0, S * es, B.st) !=
+                cudaSuccess) {
+          result = cuda_fail(cudaGetLastError(), "tile tuning");
+          break;
+        }
+      }
+      zeroed = true;
+    }
+    double best = 1e30;
+    int best_spc = 1;
+    for (int spc : cand) {
+      g.spc = spc;
+      if ((result = build_slice_tiles(B, probs)) != UFG_OK) break;
+      float total = 0.0f;
+      for (int prec = 0; prec < 2 && result == UFG_OK; ++prec) {
+        SliceCall c = base_call(g.lat, FAM_KIN, prec);
+        c.in = B.ar[prec].x;
+        c.pre = fldb(B, 'w', prec);
+        c.id = c.in;
+        c.shift = -1;
+        c.out = B.ar[prec].t;
+        if ((result = slice(B, g, c, -1)) != UFG_OK) break;  // warm-up
+        cudaEventRecord(e0, B.st);
+        for (int r = 0; r < 3 && result == UFG_OK; ++r) result = slice(B, g, c, -1);
+        cudaEventRecord(e1, B.st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          result = cuda_fail(cudaGetLastError(), "tile tuning");
+          break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        total += ms;
+      }
+      if (result != UFG_OK) break;
+      if (total < best) {
+        best = total;
+        best_spc = spc;
+      }
+    }
+    if (result != UFG_OK) break;
+    g.spc = best_spc;
+    changed = true;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  UFG_TRY(result);
+  if (changed) UFG_TRY(build_slice_tiles(B, probs));
+  return UFG_OK;
+}
+
 ufg_status setup(Batch& B, int n, const ufg_problem* probs) {
   B.n = n;
   B.pr.assign(probs, probs + n);
@@ -883,36 +1002,7 @@ ufg_status setup(Batch& B, int n, const ufg_problem* probs) {
     return UFG_OOM;
   }
   UFG_TRY(B.alloc(&B.scale, 2 * (size_t)n));
-  // slice tiles per group (C CTAs per tile), recurrence tiles
-  int cta = 0;
-  for (auto& g : B.groups) {
-    std::vector<BatchTile> tl;
-    std::vector<int2> rt;
-    const int C = g.lat->C[0];  // same cluster size for both precisions below N_x = 32
-    if (g.lat->C[1] != C) g.lat->C[1] = C;
-    g.cta_base = cta;
-    for (int i : g.probs) {
-      BatchProb& bp = B.probs_h[i];
-      const int nt = probs[i].ntau;
-      bp.off = B.off[i];
-      bp.ntau = nt;
-      bp.V = probs[i].nx * probs[i].nx * probs[i].nx;
-      bp.A = std::sqrt(2.0) * std::sqrt(std::expm1(probs[i].tau * probs[i].g));
-      bp.st0 = cta + (int)tl.size() * C;
-      for (int t0 = 0; t0 < nt; ++t0) tl.push_back(BatchTile{i, t0});
-      bp.st1 = cta + (int)tl.size() * C;
-      for (int mb = 0; mb < (bp.V + 31) / 32; ++mb) rt.push_back(make_int2(i, mb));
-      g.max_ntau = std::max(g.max_ntau, nt);
-    }
-    g.ntiles = (int)tl.size();
-    g.nrtiles = (int)rt.size();
-    cta += g.ntiles * C;
-    UFG_TRY(B.alloc(&g.tiles, tl.size()));
-    UFG_TRY(B.alloc(&g.rtiles, rt.size()));
-    UFG_CUDA(cudaMemcpy(g.tiles, tl.data(), tl.size() * sizeof(BatchTile), cudaMemcpyHostToDevice));
-    UFG_CUDA(cudaMemcpy(g.rtiles, rt.data(), rt.size() * sizeof(int2), cudaMemcpyHostToDevice));
-  }
-  B.nslice_ctas = cta;
+  UFG_TRY(build_slice_tiles(B, probs));
   // vector tiles over the packed arenas, in arena order
   std::vector<int4> vt;
   for (int i : order) {
@@ -959,7 +1049,7 @@ ufg_status setup(Batch& B, int n, const ufg_problem* probs) {
   UFG_TRY(B.alloc(&B.xm64, S));
   UFG_TRY(B.alloc(&B.bm64, S));
   UFG_TRY(B.alloc(&B.d64, S));
-  return UFG_OK;
+  return tune_tiles(B, probs);
 }
 
 // Per call: potentials from each problem's sigma and its right-hand side into the arenas.
@@ -1125,6 +1215,7 @@ extern "C" ufg_status ufg_solve_batch(int n, const ufg_problem* probs, int pc_ki
       }
       s.true_residual = rel;
       s.seconds = secs;
+      s.tile_slices = B->groups[B->group_of[i]].spc;
     }
   }
   cudaEventRecord(ev, B->st);

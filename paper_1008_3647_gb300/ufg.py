@@ -58,7 +58,8 @@ class Stats(ctypes.Structure):
                 ("n_M1T", ctypes.c_longlong), ("n_M0inv", ctypes.c_longlong),
                 ("n_M0invT", ctypes.c_longlong), ("n_sca", ctypes.c_longlong),
                 ("mv_paper", ctypes.c_double), ("true_residual", ctypes.c_double),
-                ("seconds", ctypes.c_double), ("inner_tol", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("tile_slices", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
