@@ -88,6 +88,13 @@ def test_batch_96_every_problem_against_oracle(ufg, precision):
     stats = ufg.ufg_solve_batch(probs, "wce", {"order": 2}, tol=1e-10, precision=prec)
     bad = [(i, shapes[i], st) for i, st in enumerate(stats) if st["status"] != ufg.UFG_OK]
     assert not bad, bad[:3]
+    # tiles: one slice where the group has a TMA shape (N_x = 8), else a tuned count that fits
+    # 48 KB of FP64 slices and is the same for every problem of a group
+    for nx in {s[0] for s in shapes}:
+        tiles = {st["tile_slices"] for (n, _, _), st in zip(shapes, stats) if n == nx}
+        assert len(tiles) == 1, (nx, tiles)
+        k = tiles.pop()
+        assert k == 1 if nx == 8 else (k in (1, 2, 4, 8) and k * nx * nx * (nx + 1) * 8 <= 48 * 1024)
     rels = [_oracle_rel(pr) for pr in probs]
     worst = max(range(96), key=lambda i: rels[i])
     assert rels[worst] <= 1e-10, (worst, shapes[worst], rels[worst])
