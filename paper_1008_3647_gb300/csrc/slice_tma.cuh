@@ -770,11 +770,35 @@ constexpr int m1w_min_blocks() {
   return sizeof(R) == 4 ? 5 : (N <= 8 ? 4 : 2);  // DIR 1 (three boxes) fits 4 by shared memory
 }
 
-// Line passes over one swizzled slice box (all N planes in this CTA).
-template <int N, typename R, bool IN_SPEC, bool OUT_SPEC, bool MUL, class CF>
+// Row-pair permutation of the one-CTA boxes with 64-byte rows and 16 rows per plane (FP32
+// N = 16): a row's 16 words sit in banks 0-15 or 16-31 by the parity of its row index, and a
+// plane is 1 KB, so the y-pass (a warp reads the same row y of planes p and p + 1) and the
+// y-pass stores would hit the same banks twice.  Planes with odd p keep row y at position y ^ 1
+// (the swizzle phase (r >> 1) & 3 is unchanged).  The first x-pass writes its rows to the
+// permuted positions, every later pass addresses them there; the TMA boxes of multipliers and
+// epilogue operands keep the plain layout.
+template <int N, typename R>
+constexpr bool swz_perm() {
+#ifndef UFG_SWZ_PERM
+#define UFG_SWZ_PERM 1
+#endif
+  return UFG_SWZ_PERM != 0 && N == 16 && sizeof(R) == 4;
+}
+// position of row r = p N + y under the permutation
+template <int N, bool PERM>
+__device__ __forceinline__ int prow(int r) {
+  return PERM ? (r ^ ((r / N) & 1)) : r;
+}
+
+// Line passes over one swizzled slice box (all N planes in this CTA).  PERM_OUT: rows are read
+// at their plain positions and written to the permuted ones (the rows r and r ^ 1 of a plane
+// belong to one warp, which has read both before either is written).
+template <int N, typename R, bool IN_SPEC, bool OUT_SPEC, bool MUL, class CF,
+          bool PERM_OUT = false>
 __device__ __forceinline__ void swz_xpass(R* xs, const R* mul, const CF& cf) {
   using G = SwzGeom<N, R>;
   constexpr int CPR = G::RB / 16, EPC = 16 / (int)sizeof(R);
+  static_assert(!PERM_OUT || (N * N) % TMA_NT == 0, "the warp-wide exchange needs whole rows");
   for (int r = threadIdx.x; r < N * N; r += TMA_NT) {
     R v[N];
 #pragma unroll
@@ -783,19 +807,33 @@ __device__ __forceinline__ void swz_xpass(R* xs, const R* mul, const CF& cf) {
 #pragma unroll
       for (int e = 0; e < EPC; ++e) v[c * EPC + e] = MUL ? xs[o + e] * mul[o + e] : xs[o + e];
     }
-    swz_store_row<N, R>(xs, r, v, cf, IN_SPEC, OUT_SPEC);
+    if constexpr (PERM_OUT) {
+      R o[N];
+      line_op<N, R, IN_SPEC, OUT_SPEC>(v, cf, [&](int i, R val) { o[i] = val; });
+      __syncwarp();
+      const int rp = prow<N, true>(r);
+#pragma unroll
+      for (int c = 0; c < CPR; ++c) {
+        R* dst = xs + G::chunk(rp, c);
+#pragma unroll
+        for (int e = 0; e < EPC; ++e) dst[e] = o[c * EPC + e];
+      }
+    } else {
+      swz_store_row<N, R>(xs, r, v, cf, IN_SPEC, OUT_SPEC);
+    }
   }
 }
 
-template <int N, typename R, bool IN_SPEC, bool OUT_SPEC, class CF>
+template <int N, typename R, bool IN_SPEC, bool OUT_SPEC, class CF, bool PERM = false>
 __device__ __forceinline__ void swz_ypass(R* xs, const CF& cf) {
   using G = SwzGeom<N, R>;
   for (int l = threadIdx.x; l < N * N; l += TMA_NT) {
     const int p = l / N, x = l - (l / N) * N;
     R v[N];
 #pragma unroll
-    for (int y = 0; y < N; ++y) v[y] = xs[G::off(p * N + y, x)];
-    line_op<N, R, IN_SPEC, OUT_SPEC>(v, cf, [&](int i, R val) { xs[G::off(p * N + i, x)] = val; });
+    for (int y = 0; y < N; ++y) v[y] = xs[G::off(prow<N, PERM>(p * N + y), x)];
+    line_op<N, R, IN_SPEC, OUT_SPEC>(
+        v, cf, [&](int i, R val) { xs[G::off(prow<N, PERM>(p * N + i), x)] = val; });
   }
 }
 
@@ -856,20 +894,22 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
   __syncthreads();
   mbar_wait_bounded(&bar, 0u, TMA_WAIT_LIMIT, A.err);
   if (A.expire && tid == 0) mbar_expire_one_wait(&bar2, EXPIRE_LIMIT, A.err);
-  // inverse transform (spectral input); DIR 1 weights the modes by b on the way in
-  swz_xpass<N, R, true, false, DIR == 1>(xs, ks, A.ci_x);
+  // inverse transform (spectral input); DIR 1 weights the modes by b on the way in.  With PERM
+  // the slice leaves the first pass in the permuted row layout (swz_perm), the s and b boxes
+  // keep the plain one.
+  constexpr bool PERM = swz_perm<N, R>();
+  swz_xpass<N, R, true, false, DIR == 1, LineCoef<N, R>, PERM>(xs, ks, A.ci_x);
   __syncthreads();
-  swz_ypass<N, R, true, false>(xs, A.ci_y);
+  swz_ypass<N, R, true, false, LineCoef<N, R>, PERM>(xs, A.ci_y);
   __syncthreads();
   const R f1 = DIR == 1 ? sgn * R(acoef) : R(1);
   for (int q = tid; q < NN; q += TMA_NT) {  // z pass, times the site multiplier, in place
     const int y = q / N, x = q - (q / N) * N;
     R v[N];
 #pragma unroll
-    for (int z = 0; z < N; ++z) v[z] = xs[G::off(z * N + y, x)];
+    for (int z = 0; z < N; ++z) v[z] = xs[G::off(prow<N, PERM>(z * N + y), x)];
     line_op<N, R, true, false>(v, A.ci_z, [&](int zp, R val) {
-      const int o = G::off(zp * N + y, x);
-      xs[o] = (f1 * ss[o]) * val;
+      xs[G::off(prow<N, PERM>(zp * N + y), x)] = (f1 * ss[G::off(zp * N + y, x)]) * val;
     });
   }
   __syncthreads();
@@ -882,10 +922,11 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
       if (A.want_dotP) tma_load_rows(ds, &A.tm_dot, row_out, &bar);
     }
   }
-  // forward transform (spectral output)
+  // forward transform (spectral output); the x-pass works on physical rows, so the permuted
+  // layout stays
   swz_xpass<N, R, false, true, false>(xs, nullptr, A.cf_x);
   __syncthreads();
-  swz_ypass<N, R, false, true>(xs, A.cf_y);
+  swz_ypass<N, R, false, true, LineCoef<N, R>, PERM>(xs, A.cf_y);
   __syncthreads();
   const R f2 = DIR == 0 ? sgn * R(acoef) : R(1);
   R* const gout = A.out + off + (size_t)t_out * VOL;
@@ -894,7 +935,7 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
       const int y = q / N, x = q - (q / N) * N;
       R v[N];
 #pragma unroll
-      for (int z = 0; z < N; ++z) v[z] = xs[G::off(z * N + y, x)];
+      for (int z = 0; z < N; ++z) v[z] = xs[G::off(prow<N, PERM>(z * N + y), x)];
       line_op<N, R, false, true>(v, A.cf_z, [&](int zp, R val) {
         R o = f2 * val;
         if constexpr (DIR == 0) o *= __ldg(A.bk + zp * NN + q);
@@ -911,7 +952,7 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
       const int y = q / N, x = q - (q / N) * N;
       R v[N];
 #pragma unroll
-      for (int z = 0; z < N; ++z) v[z] = xs[G::off(z * N + y, x)];
+      for (int z = 0; z < N; ++z) v[z] = xs[G::off(prow<N, PERM>(z * N + y), x)];
       line_op<N, R, false, true>(v, A.cf_z, [&](int zp, R val) {
         const int g = zp * NN + q;
         const int os = G::off(zp * N + y, x);
