@@ -253,8 +253,45 @@ ufg_status wce_b(Batch& B, int prec, const void* r, void* z, bool tr,
   Arena& V = B.ar[prec];
   // in the momentum basis r is already spectral and the series accumulates straight into z
   void* const acc = B.mom ? z : V.acc;
+  // order 2 in the momentum basis: the terms y0 (V.spec) and y1 (V.acc, unused there) are kept
+  // and the last recurrence forms z = c0 y0 + c1 y1 + c2 y2 (no accumulator read-modify-write)
+  const bool keep_terms = B.mom && d == 2;
   for (auto& g : B.groups) {
     const void* bk = prec ? (const void*)g.lat->bk32 : (const void*)g.lat->bk64;
+    if (keep_terms) {
+      if (!slice_m1w_supported(g.lat->nx, prec))
+        return cuda_fail(cudaErrorInvalidValue, "momentum-basis WCE");
+      auto recb = [&](const void* in, void* out, int mode, double coef) -> ufg_status {
+        note_launches(1);
+        KTimer kt(std::string("recurrence ") + (mode == 3 ? "sum3" : "out") +
+                      (prec ? " f32" : " f64"),
+                  B.st, batch_work(B, &g.probs, 0, (prec ? 4.0 : 8.0) * (mode == 3 ? 4 : 2)));
+        cudaError_t e = launch_recurrence_batch(
+            prec, in, out, bk, g.max_ntau, tr ? 1 : 0, 1.0, mode == 3 ? z : nullptr, coef, mode, 0,
+            g.rtiles, g.nrtiles, B.probs, B.st, V.spec, V.acc, cw[0], cw[1]);
+        if (e != cudaSuccess) return cuda_fail(e, "batched recurrence");
+        return UFG_OK;
+      };
+      auto m1 = [&](const void* in) -> ufg_status {  // -A M1 (or M1^T) in momentum space
+        SliceCall m = base_call(g.lat, FAM_INV, prec);
+        m.fam = FAM_M1W;
+        m.coef2 = base_call(g.lat, FAM_FWD, prec).coef;
+        m.in = in;
+        m.pre = fldb(B, 's', prec);
+        if (tr) m.bkpre = bk; else m.bkpost = bk;
+        m.shift = tr ? +1 : -1;
+        m.a = -1.0;
+        m.scale_by_A = 1;
+        m.out = V.wr;
+        return slice(B, g, m, 0);
+      };
+      UFG_TRY(recb(r, V.spec, 0, 0.0));     // y0
+      UFG_TRY(m1(V.spec));
+      UFG_TRY(recb(V.wr, V.acc, 0, 0.0));   // y1
+      UFG_TRY(m1(V.acc));
+      UFG_TRY(recb(V.wr, nullptr, 3, cw[2]));  // z = c0 y0 + c1 y1 + c2 y2
+      continue;
+    }
     auto rec = [&](const void* in, double coef, int mode, bool write_out) -> ufg_status {
       note_launches(1);
       KTimer kt(std::string("recurrence acc") + std::to_string(mode) + (write_out ? "+out" : "") +

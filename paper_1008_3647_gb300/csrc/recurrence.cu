@@ -71,6 +71,9 @@ struct RecArgs {
   int exec_if;
   const int2* tiles;        // batched mode: (problem, 32-mode block) per CTA
   const BatchProb* probs;
+  const R* e0;              // acc_mode 3: acc = acc_coef x + c0 e0 + c1 e1
+  const R* e1;
+  double c0, c1;
 };
 
 template <typename R, int ACC, bool OUT>  // ACC = acc_mode; OUT: write out
@@ -137,13 +140,20 @@ __global__ void __launch_bounds__(32 * REC_NCH, sizeof(R) == 4 ? REC_MINB : 5) r
   R x = Is[ch][lane];
   R* out = OUT ? a.out + off + first : nullptr;
   R* acc = ACC ? a.acc + off + first : nullptr;
-  const R oscale = R(a.out_scale), acoef = R(a.acc_coef);
+  const R* e0 = ACC == 3 ? a.e0 + off + first : nullptr;
+  const R* e1 = ACC == 3 ? a.e1 + off + first : nullptr;
+  const R oscale = R(a.out_scale), acoef = R(a.acc_coef), c0 = R(a.c0), c1 = R(a.c1);
   const R* q = in;
 #pragma unroll(REC_UNROLL)
   for (int l = 0; l < n; ++l, q += step) {
     x = *q + b * x;
     if constexpr (ACC == 1) *acc = acoef * x;
     if constexpr (ACC == 2) *acc += acoef * x;
+    if constexpr (ACC == 3) {
+      *acc = acoef * x + c0 * *e0 + c1 * *e1;
+      e0 += step;
+      e1 += step;
+    }
     if constexpr (OUT) *out = oscale * x;
     if constexpr (ACC != 0) acc += step;
     if constexpr (OUT) out += step;
@@ -161,6 +171,9 @@ static cudaError_t rec_launch(const RecArgs<R>& a, unsigned grid, cudaStream_t s
     case 3: return launch_k(recurrence_kernel<R, 1, true>, dim3(grid), blk, 0, st, 1, a);
     case 4: return launch_k(recurrence_kernel<R, 2, false>, dim3(grid), blk, 0, st, 1, a);
     case 5: return launch_k(recurrence_kernel<R, 2, true>, dim3(grid), blk, 0, st, 1, a);
+    case 6:
+      if (a.e0 == nullptr || a.e1 == nullptr) return cudaErrorInvalidValue;
+      return launch_k(recurrence_kernel<R, 3, false>, dim3(grid), blk, 0, st, 1, a);
   }
   return cudaErrorInvalidValue;  // nothing to write
 }
@@ -183,16 +196,19 @@ cudaError_t launch_recurrence(int prec, const void* in, void* out, const void* b
 cudaError_t launch_recurrence_batch(int prec, const void* in, void* out, const void* bk,
                                     int max_ntau, int transpose, double out_scale, void* acc,
                                     double acc_coef, int acc_mode, int exec_if, const int2* tiles,
-                                    int ntiles, const BatchProb* probs, cudaStream_t st) {
+                                    int ntiles, const BatchProb* probs, cudaStream_t st,
+                                    const void* e0, const void* e1, double c0, double c1) {
   (void)max_ntau;  // any N_tau: the chunk length follows each problem's own N_tau
   if (ntiles <= 0) return cudaSuccess;
   if (prec == 0) {
     RecArgs<double> a{(const double*)in, (double*)out, (const double*)bk, 0, 0, transpose,
-                      out_scale, (double*)acc, acc_coef, acc_mode, nullptr, exec_if, tiles, probs};
+                      out_scale, (double*)acc, acc_coef, acc_mode, nullptr, exec_if, tiles, probs,
+                      (const double*)e0, (const double*)e1, c0, c1};
     return rec_launch(a, (unsigned)ntiles, st);
   }
   RecArgs<float> a{(const float*)in, (float*)out, (const float*)bk, 0, 0, transpose, out_scale,
-                   (float*)acc, acc_coef, acc_mode, nullptr, exec_if, tiles, probs};
+                   (float*)acc, acc_coef, acc_mode, nullptr, exec_if, tiles, probs,
+                   (const float*)e0, (const float*)e1, c0, c1};
   return rec_launch(a, (unsigned)ntiles, st);
 }
 

@@ -117,10 +117,14 @@ cudaError_t launch_recurrence(int prec, const void* in, void* out, const void* b
                               int ntau, int transpose, double out_scale, void* acc,
                               double acc_coef, int acc_mode, const int* done, cudaStream_t st);
 // Batched form: one CTA per (problem, 32-mode block) tile; max_ntau bounds every problem's N_tau.
+// acc_mode 3 (batched only): acc = acc_coef * x + c0 * e0 + c1 * e1 (the earlier terms of a
+// series, same layout as acc).
 cudaError_t launch_recurrence_batch(int prec, const void* in, void* out, const void* bk,
                                     int max_ntau, int transpose, double out_scale, void* acc,
                                     double acc_coef, int acc_mode, int exec_if, const int2* tiles,
-                                    int ntiles, const BatchProb* probs, cudaStream_t st);
+                                    int ntiles, const BatchProb* probs, cudaStream_t st,
+                                    const void* e0 = nullptr, const void* e1 = nullptr,
+                                    double c0 = 0.0, double c1 = 0.0);
 // Strong-coupling factors (per site, sequential in t) and apply.
 cudaError_t launch_sca_setup(const double* w64, long long V, int ntau, double alpha, double* L64,
                              double* Di64, float* L32, float* Di32, cudaStream_t st);
