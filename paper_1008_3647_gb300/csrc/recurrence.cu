@@ -180,16 +180,19 @@ static cudaError_t rec_launch(const RecArgs<R>& a, unsigned grid, cudaStream_t s
 
 cudaError_t launch_recurrence(int prec, const void* in, void* out, const void* bk, long long V,
                               int ntau, int transpose, double out_scale, void* acc,
-                              double acc_coef, int acc_mode, const int* done, cudaStream_t st) {
+                              double acc_coef, int acc_mode, const int* done, cudaStream_t st,
+                              const void* e0, const void* e1, double c0, double c1) {
   if (V <= 0 || ntau <= 0) return cudaErrorInvalidValue;
   const unsigned grid = (unsigned)((V + 31) / 32);
   if (prec == 0) {
     RecArgs<double> a{(const double*)in, (double*)out, (const double*)bk, V, ntau, transpose,
-                      out_scale, (double*)acc, acc_coef, acc_mode, done, 0, nullptr, nullptr};
+                      out_scale, (double*)acc, acc_coef, acc_mode, done, 0, nullptr, nullptr,
+                      (const double*)e0, (const double*)e1, c0, c1};
     return rec_launch(a, grid, st);
   }
   RecArgs<float> a{(const float*)in, (float*)out, (const float*)bk, V, ntau, transpose, out_scale,
-                   (float*)acc, acc_coef, acc_mode, done, 0, nullptr, nullptr};
+                   (float*)acc, acc_coef, acc_mode, done, 0, nullptr, nullptr,
+                   (const float*)e0, (const float*)e1, c0, c1};
   return rec_launch(a, grid, st);
 }
 

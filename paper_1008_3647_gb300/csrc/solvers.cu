@@ -374,6 +374,42 @@ ufg_status pc_wce(ufg_solver* S, const ufg_field* f, int prec, const void* r, vo
     return UFG_OK;
   };
   cudaError_t e = cudaSuccess;
+  if (S->mom && d == 2) {
+    // order 2 in the momentum basis: the terms y0 (V.spec) and y1 (V.acc, unused there) are
+    // kept and the last recurrence forms z = c0 y0 + c1 y1 + c2 y2
+    auto recm = [&](const void* in, void* out, int mode) -> ufg_status {
+      KTimer kt(std::string("recurrence ") + (mode == 3 ? "sum3" : "out") + (prec ? " f32" : " f64"),
+                S->st, solo_work(done, 0, (double)L->S * (prec ? 4.0 : 8.0) * (mode == 3 ? 4 : 2)));
+      cudaError_t er = launch_recurrence(prec, in, out, bk, L->V, L->ntau, tr ? 1 : 0, 1.0,
+                                         mode == 3 ? z : nullptr, cw[2], mode, done, S->st, V.spec,
+                                         V.acc, cw[0], cw[1]);
+      if (er != cudaSuccess) return cuda_fail(er, "recurrence kernel");
+      note_launches(1);
+      if (tr) S->counts.M0invT++; else S->counts.M0inv++;
+      return UFG_OK;
+    };
+    auto m1 = [&](const void* in) -> ufg_status {
+      SliceCall m = base_call(L, FAM_INV, prec);
+      m.fam = FAM_M1W;
+      m.coef2 = base_call(L, FAM_FWD, prec).coef;
+      m.in = in;
+      m.pre = fld(f, 's', prec);
+      if (tr) m.bkpre = bk; else m.bkpost = bk;
+      m.shift = tr ? +1 : -1;
+      m.a = -L->A;
+      m.out = V.wr;
+      m.done = done;
+      cudaError_t er = sdisp(L->nx, m, S->st);
+      if (er != cudaSuccess) return cuda_fail(er, "fused M1 term");
+      if (tr) S->counts.M1T++; else S->counts.M1++;
+      return UFG_OK;
+    };
+    UFG_TRY(recm(r, V.spec, 0));
+    UFG_TRY(m1(V.spec));
+    UFG_TRY(recm(V.wr, V.acc, 0));
+    UFG_TRY(m1(V.acc));
+    return recm(V.wr, nullptr, 3);
+  }
   if (S->mom) {
     UFG_TRY(rec(r, cw[0], 1, d > 0));
   } else {

@@ -113,12 +113,14 @@ cudaError_t launch_potentials(const double* sigma, double A, long long S, double
                               double* c64, float* w32, float* s32, float* c32, cudaStream_t st);
 // Exact M0^{-1} (transpose = 0) or M0^{-T} time recurrence per momentum mode, in place allowed.
 // out (nullable) = out_scale * x; acc_mode 0: none, 1: acc = acc_coef * x, 2: acc += acc_coef * x.
+// acc_mode 3: acc = acc_coef * x + c0 * e0 + c1 * e1 (the earlier terms of a series).
 cudaError_t launch_recurrence(int prec, const void* in, void* out, const void* bk, long long V,
                               int ntau, int transpose, double out_scale, void* acc,
-                              double acc_coef, int acc_mode, const int* done, cudaStream_t st);
+                              double acc_coef, int acc_mode, const int* done, cudaStream_t st,
+                              const void* e0 = nullptr, const void* e1 = nullptr,
+                              double c0 = 0.0, double c1 = 0.0);
 // Batched form: one CTA per (problem, 32-mode block) tile; max_ntau bounds every problem's N_tau.
-// acc_mode 3 (batched only): acc = acc_coef * x + c0 * e0 + c1 * e1 (the earlier terms of a
-// series, same layout as acc).
+// acc_mode 3 as above.
 cudaError_t launch_recurrence_batch(int prec, const void* in, void* out, const void* bk,
                                     int max_ntau, int transpose, double out_scale, void* acc,
                                     double acc_coef, int acc_mode, int exec_if, const int2* tiles,
