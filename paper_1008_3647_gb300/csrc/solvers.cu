@@ -1108,6 +1108,7 @@ double paper_mv(const ufg_solver* S, int iters, bool bicg) {
 void fill_stats(ufg_stats* st, ufg_solver* S, const SolveOut& o, double rel, double secs,
                 bool bicg, ufg_status status) {
   if (!st) return;
+  std::memset(st, 0, sizeof(*st));
   st->status = status;
   st->iterations = o.iters;
   st->outer_iterations = o.outer;
