@@ -166,17 +166,19 @@ static __device__ __noinline__ void scalar_update(int op, DevScalars* sc, const 
   }
 }
 
-// Called by every thread of a CTA of a producer that has just written its partial pair at index
-// `mine` of `part`: the CTA that completes a problem's set [i0, i1) (counted on `counter`, left at
-// 0 for the next producer) sums the set in fixed order and applies `op` to that problem's
-// scalars.  Partials reach the summing CTA through the fence before the count.
+// Called by every thread of a CTA of a producer whose thread 0 has just written the CTA's
+// partial pair into `part`: the CTA that completes a problem's set [i0, i1) (counted on
+// `counter`, left at 0 for the next producer) sums the set in fixed order and applies `op` to
+// that problem's scalars.  Partials reach the summing CTA through thread 0's fence before its
+// count (only thread 0 wrote them, so only it fences).
 template <int NT = SCAL_NT>
 static __device__ __forceinline__ void last_block_update(int op, DevScalars* sc, const double* part,
                                                         int i0, int i1, unsigned* counter) {
   __shared__ int is_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(counter, 1u) == (unsigned)(i1 - i0 - 1);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(counter, 1u) == (unsigned)(i1 - i0 - 1);
+  }
   __syncthreads();
   if (!is_last) return;
   __threadfence();
