@@ -394,7 +394,7 @@ void ufg_batch_cache_clear(void);
  * device array of 2 x 2^20 doubles (16 MiB) that every GPU loading the library holds until exit,
  * so N_x^3 N_tau must be <= 2^20 sites (UFG_INVALID_ARG otherwise, with a message).  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call overwrites the whole used
+ * current.  Every call overwrites the whole used
  * part of the array before reading it, so nothing needs clearing, but calls share the array:
  * calls that overlap on the GPU (different streams, or different host threads) race and must be
  * serialised by the caller.  It runs the shared-memory-staged slice kernels, which have no
