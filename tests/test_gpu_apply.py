@@ -14,7 +14,10 @@ pytestmark = pytest.mark.gpu
 
 TOL = {torch.float64: 1e-12, torch.float32: 2e-5}
 # (N_x, N_tau): the 4^3x16 and 8^3x64 workloads, every built N_x, odd and tiny N_tau
-SHAPES = [(4, 16), (8, 64), (6, 7), (10, 5), (12, 9), (16, 12), (32, 5), (4, 3)]
+# the long time extents give the M0^{-1} recurrence per-thread chunks (N_tau / 8 elements) of
+# several load groups plus a ragged tail
+SHAPES = [(4, 16), (8, 64), (6, 7), (10, 5), (12, 9), (16, 12), (32, 5), (4, 3), (4, 200),
+          (8, 131)]
 
 
 @pytest.fixture(scope="module")

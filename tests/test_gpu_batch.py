@@ -71,6 +71,18 @@ def test_batch_with_16_cubed(ufg, precision):
         assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(pr["b_h"])
 
 
+def test_batch_momentum_long_time_extents(ufg):
+    # mixed 16^3 batch in the momentum basis with the kept-terms order-2 series (Euler
+    # S_{2k/3,k/3}): recurrence chunks of 9 and 17 elements run load groups plus ragged tails
+    shapes = [(16, 72, 21), (16, 136, 22)]
+    probs = _problems(shapes)
+    stats = ufg.ufg_solve_batch(probs, "wce", {"order": 2, "euler": "euler23"}, tol=1e-10,
+                                precision=ufg.UFG_MIXED)
+    for pr, st in zip(probs, stats):
+        assert st["status"] == ufg.UFG_OK, st
+        assert _oracle_rel(pr) <= 1e-10
+
+
 def _oracle_rel(pr):
     olat = O.Lattice(pr["nx"], pr["ntau"])
     r = pr["b_h"] - O.apply_Q(olat, pr["sigma_h"], pr["x"].cpu().numpy())

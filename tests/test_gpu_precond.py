@@ -130,6 +130,20 @@ def test_wce_parity_shapes(ufg, nx, ntau, dtype, tol):
         assert _rel(z, fn(olat, sigma, r, 2)) < tol
 
 
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-11), (torch.float32, 1e-4)])
+@pytest.mark.parametrize("order,euler", [(2, False), (4, "euler23")])
+@pytest.mark.parametrize("nx,ntau", [(4, 200), (6, 131)])
+def test_wce_parity_long_time_extents(ufg, nx, ntau, order, euler, dtype, tol):
+    # per-thread recurrence chunks of N_tau / 8 = 17 and 25 elements: several load groups of the
+    # writing, assigning and accumulating recurrences plus a ragged tail, in both directions
+    lat, field, solver, sigma, rd, r, olat = _setup(ufg, nx, ntau, 6, dtype)
+    solver.ufg_set_preconditioner("wce", order=order, euler=euler)
+    for tr, fn in [(False, O.wce_apply), (True, O.wce_apply_T)]:
+        z = solver.ufg_apply_preconditioner(field, rd, transpose=tr).double().cpu().numpy()
+        err = _rel(z, fn(olat, sigma, r, order, euler))
+        assert err < tol, (tr, err)
+
+
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-9), (torch.float32, 2e-3)])
 @pytest.mark.parametrize("degree", [8, 16, 32])
 def test_chebyshev_parity(ufg, degree, dtype, tol):
