@@ -27,28 +27,32 @@ std::atomic<int> g_on{0};
 std::mutex& g_mu = *new std::mutex;
 std::vector<Rec>& g_recs = *new std::vector<Rec>;
 
-// Pinned host ints handed out in order; reset when recording restarts (and only then: earlier
-// snapshots may still be in flight until the next synchronisation).
+// Pinned host ints handed out in order and never reused (captured graphs may still point into
+// them).  Chunks are allocated only outside stream capture (a pinned allocation would invalidate
+// a thread-local capture): enabling the profiler reserves one, and a launch captured after the
+// current chunk has run out goes without its running-problem snapshot.
 struct PinnedPool {
   std::vector<int*> chunks;
   size_t used = 0;  // ints used in the last chunk
   static constexpr size_t CHUNK = 1 << 20;
-  int* take(size_t n) {
+  bool grow() {
+    int* p = nullptr;
+    if (cudaMallocHost(&p, CHUNK * sizeof(int)) != cudaSuccess) return false;
+    chunks.push_back(p);
+    used = 0;
+    return true;
+  }
+  int* take(size_t n, bool may_alloc) {
     if (n > CHUNK) return nullptr;
     if (chunks.empty() || used + n > CHUNK) {
-      int* p = nullptr;
-      if (cudaMallocHost(&p, CHUNK * sizeof(int)) != cudaSuccess) return nullptr;
-      chunks.push_back(p);
-      used = 0;
+      if (!may_alloc || !grow()) return nullptr;
     }
     int* r = chunks.back() + used;
     used += n;
     return r;
   }
-  void reset() {
-    for (int* p : chunks) cudaFreeHost(p);
-    chunks.clear();
-    used = 0;
+  void reserve() {  // at least half a chunk free
+    if (chunks.empty() || used > CHUNK / 2) grow();
   }
 };
 PinnedPool& g_pool = *new PinnedPool;
@@ -111,7 +115,7 @@ KTimer::KTimer(const std::string& name, cudaStream_t st, LaunchWork work) : st_(
   const bool cap = capturing(st);
   std::lock_guard<std::mutex> lk(g_mu);
   if (r.work.flag_dev != nullptr && r.work.exec_if >= 0 && !r.work.site_bytes.empty()) {
-    r.flags = g_pool.take(r.work.site_bytes.size());
+    r.flags = g_pool.take(r.work.site_bytes.size(), !cap);
     if (r.flags != nullptr &&
         cudaMemcpy2DAsync(r.flags, sizeof(int), r.work.flag_dev, r.work.stride, sizeof(int),
                           r.work.site_bytes.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -238,6 +242,7 @@ extern "C" ufg_status ufg_profile_enable(int on) {
     cudaDeviceSynchronize();
     drop_records();
     g_agg.clear();
+    g_pool.reserve();
   }
   g_on.store(on ? 1 : 0);
   return UFG_OK;

@@ -82,3 +82,29 @@ def test_profile_single_problem_solve(ufg):
     ks = ufg.ufg_profile_read()
     slices = [k for k in ks if k["name"].startswith("slice kin")]
     assert slices and all(k["bytes"] > 0 for k in slices)
+
+
+def test_profile_single_problem_wce_solve_in_momentum_basis(ufg):
+    # a mixed BiCGStab + WCE2 solve of one 16^3 lattice (momentum basis, every flagged launch
+    # inside the solver's captured graphs) runs and is recorded under the profiler
+    nx, nt = 16, 64
+    sg, b = field_and_source(nx, nt, 4)
+    lat = ufg.Lattice(nx, nt)
+    field = ufg.Field(lat, torch.from_numpy(sg).cuda())
+    solver = ufg.Solver(lat)
+    solver.ufg_set_preconditioner("wce", order=2, euler="euler23")
+    bd = torch.from_numpy(b).cuda()
+    _, st0 = solver.ufg_solve_bicgstab_two_step(field, bd, tol=1e-10, precision=ufg.UFG_MIXED)
+    ufg.ufg_profile_enable(True)
+    try:
+        x, st = solver.ufg_solve_bicgstab_two_step(field, bd, tol=1e-10,
+                                                   precision=ufg.UFG_MIXED)
+    finally:
+        ufg.ufg_profile_enable(False)
+    assert st["status"] == ufg.UFG_OK, st
+    assert st["iterations"] == st0["iterations"]
+    ks = ufg.ufg_profile_read()
+    names = {k["name"] for k in ks}
+    assert any(n.startswith("recurrence") for n in names), names
+    assert any(n.startswith("slice m1w") for n in names), names
+    assert all(k["launches"] > 0 and k["total_ms"] > 0 for k in ks)
