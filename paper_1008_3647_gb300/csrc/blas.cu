@@ -194,6 +194,8 @@ vec_kernel(long long n, DevScalars* sc, R* a, R* b, R* c, R* d, R* e, R* f, doub
     if (fop >= 0 && tiles != nullptr) {
       const int prob = tiles[blockIdx.x].x;
       last_block_update(fop, sc, part, probs[prob].vt0, probs[prob].vt1, counters + prob);
+    } else if (fop >= 0) {  // one vector: the last of the grid's CTAs takes the scalar step
+      last_block_update(fop, sc, part, 0, (int)gridDim.x, counters);
     }
   }
 }
@@ -245,6 +247,21 @@ cudaError_t launch_vec(int prec, int op, long long n, const DevScalars* sc, void
                                 (double*)e, (double*)f, part, grid, st);
   return vec_dispatch<float>(op, n, s, (float*)a, (float*)b, (float*)c, (float*)d, (float*)e,
                              (float*)f, part, grid, st);
+}
+
+cudaError_t launch_vec_fused(int prec, int op, long long n, DevScalars* sc, void* a, void* b,
+                             void* c, void* d, void* e, void* f, double* part, int* nparts,
+                             int fop, unsigned* counter, cudaStream_t st) {
+  if (sc == nullptr || part == nullptr || counter == nullptr || fop < 0)
+    return cudaErrorInvalidValue;
+  const int grid = vec_grid(n);
+  if (nparts) *nparts = grid;
+  if (prec == 0)
+    return vec_dispatch<double>(op, n, sc, (double*)a, (double*)b, (double*)c, (double*)d,
+                                (double*)e, (double*)f, part, grid, st, nullptr, 0, fop, nullptr,
+                                counter);
+  return vec_dispatch<float>(op, n, sc, (float*)a, (float*)b, (float*)c, (float*)d, (float*)e,
+                             (float*)f, part, grid, st, nullptr, 0, fop, nullptr, counter);
 }
 
 cudaError_t launch_vec_batch(int prec, int op, const int4* tiles, int ntiles, DevScalars* scs,

@@ -70,6 +70,12 @@ cudaError_t launch_vec(int prec, int op, long long n, const DevScalars* sc, void
                        void* c, void* d, void* e, void* f, double* part, int* nparts,
                        cudaStream_t st);
 int vec_grid(long long n);
+// launch_vec that also applies scalar op fop to *sc from the partials it writes: the last of its
+// CTAs sums them in the scalar kernel's order and updates *sc (counter: zero between launches,
+// left at zero), so no separate scalar launch follows.  Runs while sc->done == 0.
+cudaError_t launch_vec_fused(int prec, int op, long long n, DevScalars* sc, void* a, void* b,
+                             void* c, void* d, void* e, void* f, double* part, int* nparts,
+                             int fop, unsigned* counter, cudaStream_t st);
 // Instrumentation: "vec <op> f32|f64" and the vectors one element of the op reads plus writes
 // (V_DOT: each present pair; a: first pair present, c: second pair present).
 std::string vec_op_name(int op, int prec);

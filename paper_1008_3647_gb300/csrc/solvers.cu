@@ -54,6 +54,7 @@ struct ufg_solver {
   double* xf64 = nullptr;   // FP64 X of the force when the caller does not keep it
   double* parts = nullptr;  // NSLOT x [MAX_PARTIAL_CTAS][2]
   DevScalars* sc = nullptr;
+  unsigned* fcount = nullptr;     // CTA counter of the fused scalar steps (zero between launches)
   DevScalars* sc_host = nullptr;  // pinned
   double* red_dev = nullptr;      // scratch scalar for host-visible reductions
   double* red_host = nullptr;     // pinned
@@ -238,6 +239,17 @@ ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const v
     KTimer kt_(vec_op_name(op, prec), S->st, vec_work(S, prec, op, n, a, c, false));          \
     cudaError_t err_ = launch_vec(prec, op, n, nullptr, (void*)(a), (void*)(b), (void*)(c),   \
                                   (void*)(d), (void*)(e), (void*)(f), part, np, S->st);       \
+    if (err_ != cudaSuccess) return cuda_fail(err_, "vector kernel");                         \
+    note_launches(1);                                                                         \
+  } while (0)
+
+// VEC followed by scalar op fop, applied by the vector kernel's last CTA (no scalar launch)
+#define VEC_SCALAR(prec, op, n, a, b, c, d, e, f, part, np, fop)                               \
+  do {                                                                                        \
+    KTimer kt_(vec_op_name(op, prec), S->st, vec_work(S, prec, op, n, a, c, true));           \
+    cudaError_t err_ = launch_vec_fused(prec, op, n, S->sc, (void*)(a), (void*)(b), (void*)(c), \
+                                        (void*)(d), (void*)(e), (void*)(f), part, np, fop,    \
+                                        S->fcount, S->st);                                    \
     if (err_ != cudaSuccess) return cuda_fail(err_, "vector kernel");                         \
     note_launches(1);                                                                         \
   } while (0)
@@ -800,14 +812,15 @@ ufg_status run_bicgstab(ufg_solver* S, ufg_field* f, int prec, int op, double to
     VEC_NODONE(prec, V_ZERO, n, V.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
     VEC_NODONE(prec, V_DOT, n, V.rhat, V.r, V.r, V.r, nullptr, nullptr, slot(S, P_VEC2), &n1);
     VEC_NODONE(prec, V_DOT, n, V.rhat, V.rhat, V.rhs, V.rhs, nullptr, nullptr, slot(S, P_DOT), &n2);
-    SCALAR(OP_BI_INIT, slot(S, P_VEC2), n1, slot(S, P_DOT), n2);
+    // with the first iteration's rho (later ones come with each iteration's residual check)
+    SCALAR(OP_BI_INIT_RHO, slot(S, P_VEC2), n1, slot(S, P_DOT), n2);
     return UFG_OK;
   };
   UFG_TRY(restart(x0));
-  const int nv_grid = vec_grid(n);
+  // The residual checks ride on the vector kernels that produce their partials (their last CTA
+  // applies the scalar step); alpha and omega, from the operator's partials, take scalar launches.
   auto body = [&]() -> ufg_status {
     int nsv = 0, nst = 0, nv = 0;
-    SCALAR(OP_BI_RHO, slot(S, P_VEC2), nv_grid, nullptr, 0);
     VEC(prec, V_BI_P, n, V.p, V.r, V.v, nullptr, nullptr, nullptr, nullptr, nullptr);
     void* y = V.p;
     if (pc) {
@@ -817,8 +830,8 @@ ufg_status run_bicgstab(ufg_solver* S, ufg_field* f, int prec, int op, double to
     UFG_TRY(apply_op(S, f, prec, op, y, V.v, 1.0, nullptr, 0.0, V.rhat, false, slot(S, P_SLICE1),
                      &nsv));
     SCALAR(OP_BI_ALPHA, slot(S, P_SLICE1), nsv, nullptr, 0);
-    VEC(prec, V_BI_S, n, V.s, V.r, V.v, V.x, y, nullptr, slot(S, P_VEC1), &nv);
-    SCALAR(OP_BI_SCHECK, slot(S, P_VEC1), nv, nullptr, 0);
+    VEC_SCALAR(prec, V_BI_S, n, V.s, V.r, V.v, V.x, y, nullptr, slot(S, P_VEC1), &nv,
+               OP_BI_SCHECK);
     void* z = V.s;
     if (pc) {
       UFG_TRY(pc_apply(S, f, prec, V.s, V.z, tr));
@@ -827,8 +840,8 @@ ufg_status run_bicgstab(ufg_solver* S, ufg_field* f, int prec, int op, double to
     UFG_TRY(apply_op(S, f, prec, op, z, V.t, 1.0, nullptr, 0.0, V.s, true, slot(S, P_SLICE2),
                      &nst));
     SCALAR(OP_BI_OMEGA, slot(S, P_SLICE2), nst, nullptr, 0);
-    VEC(prec, V_BI_X, n, V.x, z, V.r, V.s, V.t, V.rhat, slot(S, P_VEC2), &nv);
-    SCALAR(OP_BI_RCHECK, slot(S, P_VEC2), nv, nullptr, 0);
+    VEC_SCALAR(prec, V_BI_X, n, V.x, z, V.r, V.s, V.t, V.rhat, slot(S, P_VEC2), &nv,
+               OP_BI_RCHECK_RHO);
     return UFG_OK;
   };
   const Counts c0 = S->counts;
@@ -1235,7 +1248,8 @@ ufg_status ufg_solver_create(const ufg_lattice* L, ufg_solver** out) {
       (L->dim == 3 && slice_m1w_supported(L->nx, 0) &&
        ((s = dev_alloc(&S->mb64, n)) || (s = dev_alloc(&S->mx64, n)))) ||
       (s = dev_alloc(&S->parts, (size_t)NSLOT * 2 * MAX_PARTIAL_CTAS)) ||
-      (s = dev_alloc(&S->sc, 1)) || (s = dev_alloc(&S->red_dev, 1)))
+      (s = dev_alloc(&S->sc, 1)) || (s = dev_alloc(&S->red_dev, 1)) ||
+      (s = dev_alloc(&S->fcount, 1)))
     return fail(s);
   if (cudaMallocHost(&S->sc_host, sizeof(DevScalars)) != cudaSuccess ||
       cudaMallocHost(&S->red_host, sizeof(double)) != cudaSuccess) {
@@ -1243,7 +1257,8 @@ ufg_status ufg_solver_create(const ufg_lattice* L, ufg_solver** out) {
     return fail(UFG_OOM);
   }
   if (cudaMemset(S->parts, 0, (size_t)NSLOT * 2 * MAX_PARTIAL_CTAS * sizeof(double)) !=
-      cudaSuccess) {
+          cudaSuccess ||
+      cudaMemset(S->fcount, 0, sizeof(unsigned)) != cudaSuccess) {
     set_error("memset failed");
     return fail(UFG_CUDA_ERROR);
   }
@@ -1278,6 +1293,7 @@ void ufg_solver_destroy(ufg_solver* S) {
   dev_free(S->mx64);
   dev_free(S->parts);
   dev_free(S->sc);
+  dev_free(S->fcount);
   dev_free(S->red_dev);
   if (S->sc_host) cudaFreeHost(S->sc_host);
   if (S->red_host) cudaFreeHost(S->red_host);
