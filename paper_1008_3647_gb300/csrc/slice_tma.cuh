@@ -990,6 +990,8 @@ slice_m1w_kernel(const __grid_constant__ M1wArgs<N, R> A) {
         const int prob = A.tiles[blockIdx.x].prob;
         last_block_update(A.fop, A.scs + prob, A.partials, A.probs[prob].st0 - A.part_base,
                           A.probs[prob].st1 - A.part_base, A.counters + prob);
+      } else if (A.fop >= 0) {  // one lattice: the grid's last CTA
+        last_block_update(A.fop, A.scs, A.partials, 0, (int)gridDim.x, A.counters);
       }
     }
   }
@@ -1027,7 +1029,8 @@ inline cudaError_t m1w_launch(const SliceCall& c, cudaStream_t st) {
   a.expire = take_expired_wait(st);
   if constexpr (FULL) {
     if ((c.want_dotP && c.dotP == nullptr) || ((c.want_dotP || c.want_self) && !c.partials) ||
-        (c.fop >= 0 && (c.tiles == nullptr || c.scs == nullptr || c.counters == nullptr)))
+        (c.fop >= 0 && (c.scs == nullptr || c.counters == nullptr ||
+                        (c.tiles == nullptr && c.part_base != 0))))
       return cudaErrorInvalidValue;
     if (c.want_dotP && encode_rows<R>(&a.tm_dot, c.dotP, nelem, N, N * N) != cudaSuccess)
       return cudaErrorNotSupported;

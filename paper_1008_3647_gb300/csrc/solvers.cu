@@ -115,9 +115,15 @@ double* slot(ufg_solver* S, int k) { return S->parts + (size_t)k * 2 * MAX_PARTI
 
 // ---- operator applications with epilogues --------------------------------------------------
 // out = a * (A in) + bU * U   with partials (out . dotP, out . out) into `part` when requested.
+// fop >= 0 (momentum basis only): the operator kernel's last CTA then applies scalar op fop to
+// the solver's scalars from those partials.
 ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const void* in, void* out,
                     double a, const void* U, double bU, const void* dotP, bool self, double* part,
-                    int* nparts) {
+                    int* nparts, int fop = -1) {
+  if (fop >= 0 && (!S->mom || part == nullptr)) {
+    set_error("fused scalar step requested outside the momentum-space operator");
+    return UFG_INTERNAL;
+  }
   const ufg_lattice* L = f->lat;
   const int* done = &S->sc->done;
   if (S->mom) {  // the fused momentum-space operator (BiCGStab only)
@@ -151,6 +157,11 @@ ufg_status apply_op(ufg_solver* S, const ufg_field* f, int prec, int op, const v
     c.want_self = self;
     c.partials = part;
     c.done = done;
+    if (fop >= 0) {
+      c.fop = fop;
+      c.scs = S->sc;
+      c.counters = S->fcount;
+    }
     int launched = 0;
     c.grid_out = &launched;
     cudaError_t e = sdisp(L->nx, c, S->st);
@@ -818,7 +829,8 @@ ufg_status run_bicgstab(ufg_solver* S, ufg_field* f, int prec, int op, double to
   };
   UFG_TRY(restart(x0));
   // The residual checks ride on the vector kernels that produce their partials (their last CTA
-  // applies the scalar step); alpha and omega, from the operator's partials, take scalar launches.
+  // applies the scalar step); alpha and omega, from the operator's partials, ride on the fused
+  // momentum-space operator and take scalar launches in the position basis.
   auto body = [&]() -> ufg_status {
     int nsv = 0, nst = 0, nv = 0;
     VEC(prec, V_BI_P, n, V.p, V.r, V.v, nullptr, nullptr, nullptr, nullptr, nullptr);
@@ -828,8 +840,8 @@ ufg_status run_bicgstab(ufg_solver* S, ufg_field* f, int prec, int op, double to
       y = V.y;
     }
     UFG_TRY(apply_op(S, f, prec, op, y, V.v, 1.0, nullptr, 0.0, V.rhat, false, slot(S, P_SLICE1),
-                     &nsv));
-    SCALAR(OP_BI_ALPHA, slot(S, P_SLICE1), nsv, nullptr, 0);
+                     &nsv, S->mom ? OP_BI_ALPHA : -1));
+    if (!S->mom) SCALAR(OP_BI_ALPHA, slot(S, P_SLICE1), nsv, nullptr, 0);
     VEC_SCALAR(prec, V_BI_S, n, V.s, V.r, V.v, V.x, y, nullptr, slot(S, P_VEC1), &nv,
                OP_BI_SCHECK);
     void* z = V.s;
@@ -838,8 +850,8 @@ ufg_status run_bicgstab(ufg_solver* S, ufg_field* f, int prec, int op, double to
       z = V.z;
     }
     UFG_TRY(apply_op(S, f, prec, op, z, V.t, 1.0, nullptr, 0.0, V.s, true, slot(S, P_SLICE2),
-                     &nst));
-    SCALAR(OP_BI_OMEGA, slot(S, P_SLICE2), nst, nullptr, 0);
+                     &nst, S->mom ? OP_BI_OMEGA : -1));
+    if (!S->mom) SCALAR(OP_BI_OMEGA, slot(S, P_SLICE2), nst, nullptr, 0);
     VEC_SCALAR(prec, V_BI_X, n, V.x, z, V.r, V.s, V.t, V.rhat, slot(S, P_VEC2), &nv,
                OP_BI_RCHECK_RHO);
     return UFG_OK;
