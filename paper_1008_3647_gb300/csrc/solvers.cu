@@ -750,12 +750,14 @@ ufg_status run_cg(ufg_solver* S, ufg_field* f, int prec, double tol, int maxit, 
     UFG_TRY(apply_op(S, f, prec, OPK_Q, V.p, V.q, 1.0, nullptr, 0.0, V.p, false, slot(S, P_SLICE1),
                      &nq));
     SCALAR(OP_CG_ALPHA, slot(S, P_SLICE1), nq, nullptr, 0);
-    VEC(prec, V_CG_UPDATE, n, V.x, V.p, V.r, V.q, nullptr, nullptr, slot(S, P_VEC1), &nv);
-    SCALAR(OP_CG_CHECK, slot(S, P_VEC1), nv, nullptr, 0);
+    // the residual check and (preconditioned) beta ride on the vector kernels that produce
+    // their partials: the last CTA applies the scalar step
+    VEC_SCALAR(prec, V_CG_UPDATE, n, V.x, V.p, V.r, V.q, nullptr, nullptr, slot(S, P_VEC1), &nv,
+               OP_CG_CHECK);
     if (pc) {
       UFG_TRY(pc_apply_q(S, f, prec, V.r, V.z));
-      VEC(prec, V_DOT, n, V.r, V.z, nullptr, nullptr, nullptr, nullptr, slot(S, P_PC), &npc);
-      SCALAR(OP_CG_BETA, slot(S, P_PC), npc, nullptr, 0);
+      VEC_SCALAR(prec, V_DOT, n, V.r, V.z, nullptr, nullptr, nullptr, nullptr, slot(S, P_PC),
+                 &npc, OP_CG_BETA);
     } else {
       SCALAR(OP_CG_BETA, nullptr, 0, slot(S, P_VEC1), nv);
     }
