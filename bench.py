@@ -22,6 +22,7 @@ path); the reference arm (--impl reference) times the FP64 CPU oracle on rank 0 
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import platform
@@ -60,8 +61,10 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms.  The sampler starts before
+    the warm-up (nvidia-smi takes a fraction of a second to begin) and the summary keeps the
+    samples whose timestamps fall inside the window marked by window_start / window_end."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -69,6 +72,8 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.path = None
+        self.t0 = None
+        self.t1 = None
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -76,11 +81,17 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
+
+    def window_start(self):
+        self.t0 = datetime.datetime.now()
+
+    def window_end(self):
+        self.t1 = datetime.datetime.now()
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -90,26 +101,52 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    @staticmethod
+    def parse(lines):
+        """[(timestamp or None, fields after the timestamp)] of the well-formed sample lines."""
         rows = []
+        for line in lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10 or not f[2].replace(".", "").isdigit():
+                continue
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                ts = None
+            rows.append((ts, f[1:]))
+        return rows
+
+    @staticmethod
+    def summarise(rows, t0, t1):
+        """Median SM clock, maximum, active throttle reasons and sample count of the rows inside
+        [t0, t1] (all rows when the window holds none or the timestamps did not parse)."""
+        inside = [f for ts, f in rows if ts is not None and t0 is not None and t1 is not None
+                  and t0 <= ts <= t1]
+        window = "timed region"
+        if not inside:
+            inside = [f for _, f in rows]
+            window = "whole run (no sample inside the timed region)"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in inside]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        power = [float(r[3]) for r in inside if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(inside[0][2]),
+                "reasons": reasons, "samples": len(inside), "window": window,
+                "power_w_max": max(power) if power else None}
+
+    def summary(self):
         try:
-            for line in open(self.path):
-                f = [x.strip() for x in line.split(",")]
-                if len(f) >= 9 and f[1].replace(".", "").isdigit():
-                    rows.append(f)
+            with open(self.path) as fh:
+                rows = self.parse(fh)
         except Exception:
-            pass
+            rows = []
         finally:
             if self.path and os.path.exists(self.path):
                 os.unlink(self.path)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in rows]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
-                "reasons": reasons, "samples": len(rows),
-                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+        return self.summarise(rows, self.t0, self.t1)
 
 
 def host_info():
@@ -334,18 +371,19 @@ def run_ufg(args, rank, world, local_rank):
             total += e0.elapsed_time(e1) / 1e3
         return max_over_ranks(total, world, dev)
 
-    # warm-up (also builds the batch workspaces and captures the CUDA graphs used below)
-    for _ in range(args.warmup):
-        step_batch(ufg.UFG_MIXED)
-    step_batch(ufg.UFG_FP64)
-    step_batch(ufg.UFG_MIXED, host=True)
-
-    launches0 = ufg.ufg_kernel_launches()
     stats_box = {}
     with ClockSampler(local_rank) as clk:
+        # warm-up (also builds the batch workspaces and captures the CUDA graphs used below)
+        for _ in range(args.warmup):
+            step_batch(ufg.UFG_MIXED)
+        step_batch(ufg.UFG_FP64)
+        step_batch(ufg.UFG_MIXED, host=True)
+        launches0 = ufg.ufg_kernel_launches()
+        clk.window_start()
         t_mixed = timed(args.steps,
                         lambda: stats_box.__setitem__("mixed", step_batch(ufg.UFG_MIXED)),
                         "step_mixed")
+        clk.window_end()
     launches = ufg.ufg_kernel_launches() - launches0
     clocks = clk.summary()
     if args.only_step:  # the headline step alone (the case a profiler's launch list covers)

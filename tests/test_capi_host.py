@@ -85,3 +85,35 @@ def test_bench_multirank_logic_gloo():
         p.join(timeout=60)
     assert [r[1] for r in res] == [2.0, 2.0]  # every rank reports the slowest rank's time
     assert not set(res[0][2]) & set(res[1][2])  # disjoint problems per rank
+
+
+def test_bench_clock_summary_keeps_the_timed_window():
+    # nvidia-smi lines (timestamp first): only samples inside the marked window count; the
+    # throttle reasons and the median clock come from those
+    import datetime
+    sys.path.insert(0, ROOT)
+    import bench
+    lines = [
+        "2026/12/03 18:11:05.100, 0, 1200, 2070, 250.5, 0x0, Not Active, Not Active, Not Active, "
+        "Not Active",
+        "2026/12/03 18:11:05.200, 0, 2070, 2070, 900.1, 0x4, Not Active, Not Active, Not Active, "
+        "Active",
+        "2026/12/03 18:11:05.300, 0, 2055, 2070, 880.0, 0x0, Not Active, Not Active, Not Active, "
+        "Not Active",
+        "2026/12/03 18:11:06.300, 0, 2070, 2070, 260.0, 0x0, Active, Not Active, Not Active, "
+        "Not Active",
+        "not a sample line",
+    ]
+    rows = bench.ClockSampler.parse(lines)
+    assert len(rows) == 4
+    t0 = datetime.datetime(2026, 12, 3, 18, 11, 5, 150000)
+    t1 = datetime.datetime(2026, 12, 3, 18, 11, 6)
+    s = bench.ClockSampler.summarise(rows, t0, t1)
+    assert s["samples"] == 2 and s["window"] == "timed region"
+    assert s["sm_mhz"] == (2070 + 2055) / 2 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["power_w_max"] == 900.1
+    # no sample inside the window: all samples, said so
+    s = bench.ClockSampler.summarise(rows, t1, t1)
+    assert s["samples"] == 4 and s["window"].startswith("whole run")
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.ClockSampler.summarise([], None, None)["reasons"] == ["unsampled"]
