@@ -52,7 +52,8 @@ cudaError_t launch_potentials(const double* sigma, double A, long long S, double
 // 8 x 16^3 x 256 sites (1024 blocks) runs as a single wave; N_tau is unbounded.
 constexpr int REC_NCH = 8;
 // Loads each thread keeps in flight (unroll depth of the streaming loops): with 4 the kernel was
-// latency-bound (long-scoreboard stalls, ~1/3 of HBM); 16 measured best of 4/8/16.
+// latency-bound (long-scoreboard stalls, ~1/3 of HBM); 16 measured best of 4/8/16/32 (8 and 32
+// again with the grouped pass 2: 18.2 and 18.0 against 17.8 us per term-only batched launch).
 constexpr int REC_UNROLL = 16;
 constexpr int REC_MINB = 7;  // 7 x 152 CTA slots still hold a batch of 1024 CTAs in one wave
 // Pass 2 stores each value it loads, and its input may alias its output, so a plain loop waits
