@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(VEC_NT)
 scalar_kernel(int op, DevScalars* sc, const double* part, int nparts, const double* part2,
               int nparts2) {
   pdl_begin();
-  if (op != OP_CG_INIT && op != OP_BI_INIT && op != OP_BI_INIT_RHO && sc->done) return;
+  if (op != OP_CG_INIT && op != OP_BI_INIT_RHO && sc->done) return;
   // every thread takes part in the block sums; thread 0 then updates the scalars
   double r[4];
   block_sums4(part, 0, nparts, part2, 0, nparts2, r);

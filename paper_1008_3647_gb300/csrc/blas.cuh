@@ -34,15 +34,14 @@ enum ScalarOp {
   OP_CG_ALPHA,      // alpha = rz / (p.q)
   OP_CG_CHECK,      // iters++, rr = r.r, converged?
   OP_CG_BETA,       // rz_new = r.z, beta = rz_new / rz
-  OP_BI_INIT,       // rhatn2 = rhat.rhat, rr = r.r, rho_old = alpha = omega = 1
-  OP_BI_RHO,        // rho = rhat.r; near-breakdown -> restart, else iters++, beta
   OP_BI_ALPHA,      // alpha = rho / (rhat.v)
   OP_BI_SCHECK,     // ss = s.s, converged?
   OP_BI_OMEGA,      // omega = (t.s) / (t.t)
-  OP_BI_RCHECK,     // rr = r.r, converged?, rho_old = rho
   OP_NORM2,         // rr = v.v only (no other state touched)
-  OP_BI_RCHECK_RHO, // OP_BI_RCHECK, then OP_BI_RHO on the same partials if still running
-  OP_BI_INIT_RHO,   // OP_BI_INIT, then OP_BI_RHO on the same partials if still running
+  OP_BI_RCHECK_RHO, // rr = r.r, converged?, rho_old = rho; then, if still running, the next
+                    // iteration's rho = rhat.r (near-breakdown -> restart, else iters++, beta)
+  OP_BI_INIT_RHO,   // rhatn2 = rhat.rhat, rr = r.r, rho_old = alpha = omega = 1; then, if still
+                    // running, the first iteration's rho as above
   OP_BI_RHO_REDO,   // after a residual replacement: rho = rhat.r, beta again (no iteration
                     // counted); done = 0, or 2 on near-breakdown
 };

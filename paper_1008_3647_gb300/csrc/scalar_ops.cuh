@@ -72,7 +72,7 @@ static __device__ __forceinline__ void bi_rcheck(DevScalars* sc, double rr, doub
 
 static __device__ __noinline__ void scalar_update(int op, DevScalars* sc, const double* part, double a0, double a1,
                               const double* part2, double b0, double b1) {
-  if ((op == OP_CG_INIT || op == OP_BI_INIT || op == OP_BI_INIT_RHO) && part2 != nullptr)
+  if ((op == OP_CG_INIT || op == OP_BI_INIT_RHO) && part2 != nullptr)
     sc->bn = sqrt(b1);  // rhs.rhs
   const double tb = sc->tol * sc->bn;
   switch (op) {
@@ -103,18 +103,8 @@ static __device__ __noinline__ void scalar_update(int op, DevScalars* sc, const 
       if (bad(sc->beta)) sc->done = 4;
       break;
     }
-    case OP_BI_INIT:  // part = (rhat.r, r.r), part2 = (rhat.rhat, rhs.rhs)
-      sc->rho = a0;
-      sc->rr = a1;
-      sc->rhatn2 = b0;
-      sc->rho_old = 1.0;
-      sc->alpha = 1.0;
-      sc->omega = 1.0;
-      sc->done = 0;
-      if (bad(a0) || bad(a1)) sc->done = 4;
-      else if (sqrt(a1) <= tb) sc->done = 1;
-      break;
-    case OP_BI_INIT_RHO:  // OP_BI_INIT, then the first iteration's rho (same partials)
+    case OP_BI_INIT_RHO:  // part = (rhat.r, r.r), part2 = (rhat.rhat, rhs.rhs); the first
+                          // iteration's rho from the same partials
       sc->rho = a0;
       sc->rr = a1;
       sc->rhatn2 = b0;
@@ -136,9 +126,6 @@ static __device__ __noinline__ void scalar_update(int op, DevScalars* sc, const 
       sc->beta = (a0 / sc->rho_old) * (sc->alpha / sc->omega);
       sc->done = bad(sc->beta) ? 4 : 0;
       break;
-    case OP_BI_RHO:  // part = (rhat.r, r.r) of the last residual update (or of the init)
-      bi_rho(sc, a0, a1);
-      break;
     case OP_BI_ALPHA:  // part = slice partials (v.rhat, -)
       sc->alpha = sc->rho / a0;
       if (bad(sc->alpha)) sc->done = 4;
@@ -156,10 +143,8 @@ static __device__ __noinline__ void scalar_update(int op, DevScalars* sc, const 
     case OP_NORM2:  // part = (-, v.v)
       sc->rr = a1;
       break;
-    case OP_BI_RCHECK:  // part = (rhat.r, r.r)
-      bi_rcheck(sc, a1, tb);
-      break;
-    case OP_BI_RCHECK_RHO:  // the iteration's check, then (still running) the next one's rho
+    case OP_BI_RCHECK_RHO:  // part = (rhat.r, r.r): the iteration's check, then (still
+                            // running) the next one's rho
       bi_rcheck(sc, a1, tb);
       if (sc->done == 0) bi_rho(sc, a0, a1);
       break;
