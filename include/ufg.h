@@ -36,7 +36,10 @@
  *   UFG_NO_FUSED_Q=1   Q = M^T M as two launches (M, then M^T) everywhere (by default one
  *                      kernel per output slice on 16^3 lattices with N_tau <= twice the SMs);
  *   UFG_NO_MOMENTUM=1  WCE-preconditioned BiCGStab stays in the position basis (by default it
- *                      iterates on F x where the lattice has the fused momentum-space operator).
+ *                      iterates on F x where the lattice has the fused momentum-space operator);
+ *   UFG_NO_PAIR=1      FP32 16^3 slices run one line per thread instead of two (packed FP32x2);
+ *   UFG_TMA_C32=4      FP32 32^3 slices run in 4-CTA clusters instead of 8;
+ *   UFG_TUNE_CACHE=f   ufg_lattice_autotune results are also kept in file f (see there).
  */
 #ifndef UFG_H
 #define UFG_H
