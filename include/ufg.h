@@ -123,6 +123,15 @@ typedef struct {
   double vw_s;
 } ufg_pc_params;
 
+/* The weights c_0..c_order (host FP64, order + 1 entries written to `weights`, caller-owned) with
+ * which the weak-coupling preconditioner of that order sums its terms, P_d r = sum_n c_n t_n,
+ * t_n = (-A M0^{-1} M1)^n M0^{-1} r (Sec. 3, Eq. WCE), under acceleration `accel` (a ufg_accel)
+ * with parameters euler_p and vw_s as in ufg_pc_params (0 selects 1/2 and 1); Sec. 3.1.  Host
+ * only: runs without a GPU.  UFG_INVALID_ARG for an order outside 0..16, an unknown accel, or
+ * parameters out of range (with a message). */
+ufg_status ufg_wce_series_weights(int order, int accel, double euler_p, double vw_s,
+                                  double* weights);
+
 /* Solve parameters.
  *   tol       : target of the true relative residual ||b - M^T M x|| / ||b|| (Sec. 5 "reduction in
  *               the norm of the residual"), recomputed in FP64 at exit.

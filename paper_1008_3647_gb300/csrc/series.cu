@@ -136,3 +136,26 @@ ufg_status normalize_pc(int kind, const ufg_pc_params* in, ufg_pc_params* out) {
 }
 
 }  // namespace ufg
+
+extern "C" ufg_status ufg_wce_series_weights(int order, int accel, double euler_p, double vw_s,
+                                             double* weights) {
+  ufg::clear_error();
+  if (weights == nullptr) {
+    ufg::set_error("wce_series_weights: weights is null");
+    return UFG_INVALID_ARG;
+  }
+  ufg_pc_params in = {}, pc = {};
+  in.order = order;
+  in.euler = accel;
+  in.euler_p = euler_p;
+  in.vw_s = vw_s;
+  const ufg_status st = ufg::normalize_pc(UFG_PC_WCE, &in, &pc);
+  if (st != UFG_OK) return st;
+  std::vector<double> c;
+  if (!ufg::wce_series_weights(pc.order, pc.euler, pc.euler_p, pc.vw_s, c)) {
+    ufg::set_error("wce_series_weights: invalid acceleration parameters");
+    return UFG_INVALID_ARG;
+  }
+  for (int n = 0; n <= pc.order; ++n) weights[n] = c[(size_t)n];
+  return UFG_OK;
+}

@@ -103,6 +103,8 @@ _SIGS = {
     "ufg_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "ufg_measure_fma_rate": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double)]),
     "ufg_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "ufg_wce_series_weights": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                              ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "ufg_lattice_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp)]),
     "ufg_lattice_create_dim": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -188,6 +190,14 @@ def ufg_measure_fma_rate(precision=UFG_FP64):
     v = ctypes.c_double(0.0)
     _check(load().ufg_measure_fma_rate(precision, _stream(), ctypes.byref(v)))
     return v.value
+
+
+def ufg_wce_series_weights(order, euler=False, p=0.0, s=0.0):
+    """The order + 1 weights of the weak-coupling series terms under acceleration `euler` (as in
+    Solver.ufg_set_preconditioner); host only, no GPU needed."""
+    w = (ctypes.c_double * (order + 1 if order >= 0 else 1))()
+    _check(load().ufg_wce_series_weights(order, ACCEL[euler], p, s, w))
+    return [w[i] for i in range(order + 1)]
 
 
 def ufg_profile_read():
