@@ -170,3 +170,34 @@ def test_batch_in_momentum_basis_matches_solo(ufg, precision):
             assert abs(ss["iterations"] - st["iterations"]) <= 2, (
                 ss["iterations_step"], st["iterations_step"])
         assert float((xs - pr["x"]).norm() / xs.norm()) < 1e-7
+
+
+def test_headline_batch_every_solution_against_oracle(ufg):
+    """The timed step of bench.py at full size and in its launch configuration: the rank's 8
+    seeded 16^3 x 256 problems in one mixed ufg_solve_batch (two-step BiCGStab, order-2 series
+    with Euler S_{2k/3,k/3}, inner tolerance 1e-5, host check every 8 iterations), then again
+    from host buffers; every solution's true residual recomputed by the oracle."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    shapes = [(bench.NX, bench.NTAU, s) for s in bench.seeds_for_rank(0)]
+    probs = _problems(shapes)
+    for pr in probs:
+        pr["tau"], pr["g"] = 0.05, 5.0
+    stats = ufg.ufg_solve_batch(probs, "wce", bench.METHOD, tol=bench.TOL,
+                                precision=ufg.UFG_MIXED, inner_tol=1e-5, check_every=8)
+    assert all(st["status"] == ufg.UFG_OK for st in stats), stats
+    rels = [_oracle_rel(pr) for pr in probs]
+    assert max(rels) <= bench.TOL, rels
+    # the end-to-end form: sigma, b and x in host memory
+    host = [{"nx": pr["nx"], "ntau": pr["ntau"], "tau": 0.05, "g": 5.0,
+             "sigma": torch.from_numpy(pr["sigma_h"]), "b": torch.from_numpy(pr["b_h"]),
+             "x": torch.zeros(pr["ntau"], pr["nx"], pr["nx"], pr["nx"], dtype=torch.float64)}
+            for pr in probs]
+    stats_h = ufg.ufg_solve_batch(host, "wce", bench.METHOD, tol=bench.TOL,
+                                  precision=ufg.UFG_MIXED, inner_tol=1e-5, check_every=8)
+    assert all(st["status"] == ufg.UFG_OK for st in stats_h), stats_h
+    for pr, hp, st, sh in zip(probs, host, stats, stats_h):
+        assert sh["iterations"] == st["iterations"]  # same arithmetic from either memory
+        assert torch.equal(hp["x"], pr["x"].cpu())
